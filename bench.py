@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the ACAT time step on GB300.
+
+Workload: 1D Euler (gamma = 1.4), ACAT P = 4 (orders up to 8), N = 16384
+cells on [0, 1], transmissive boundaries, CFL 0.4, 4000 steps, from seeded
+Riemann data with an entropy wave. One benchmark step is one full run of the
+4000 ACAT steps (each a single fused kernel, replayed from CUDA graphs, with
+the CFL dt reduced on the device) from the resident initial state.
+
+Metric: cell-updates/s (cells x ACAT steps / time), FP64. The JSON line also
+carries the roofline of the step kernel (FP64 FMA pipe, measured live), the
+end-to-end number through the host-buffer entry point, the CPU oracle as a
+baseline, and variants (P = 2; FP32 when built).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per ACAT step (P=2,4) vs roofline; batched/adjoint vs plain"
+UNIT = "cell-updates/s"
+NX, P_MAIN, ACAT_STEPS, CFL, SEED = 16384, 4, 4000, 0.4, 0
+WORKLOAD = ("1D Euler gamma=1.4, ACAT P=4 (orders up to 8), N=16384 cells on [0,1], transmissive, "
+            "CFL 0.4, 4000 steps, seeded Riemann data + entropy wave")
+PROFILE = os.path.join(ROOT, "profiles", "step1d_euler_p4_n16384.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--acat-steps", type=int, default=ACAT_STEPS,
+                    help="ACAT steps per benchmark step (profiling runs use fewer)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "samples": len(sms), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(budget_s: float = 12.0, max_steps: int = 200) -> dict:
+    """The CPU oracle as it stands, on a bounded sample of the workload:
+    consecutive oracle steps from the seeded initial state."""
+    import oracle as O
+    from paper_2007_01416_gb300 import workloads as W
+    c = W.euler1d_riemann_entropy(nx=NX, seed=SEED, P=P_MAIN, steps=ACAT_STEPS, cfl=CFL)
+    pr = O.Problem(**c.problem_kwargs())
+    u = c.u0.copy()
+    n, t0 = 0, time.perf_counter()
+    while n < max_steps and time.perf_counter() - t0 < budget_s:
+        u, _, _ = O.step_1d(pr, u)
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": NX * n / el, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"{n} consecutive FP64 oracle steps of the workload from its initial state "
+                      f"({el:.1f} s, OpenMP over interfaces)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    from paper_2007_01416_gb300 import workloads as W
+    c = W.euler1d_riemann_entropy(nx=NX, seed=SEED, P=P_MAIN, steps=ACAT_STEPS, cfl=CFL)
+    pr = O.Problem(**c.problem_kwargs())
+    per = 20  # oracle ACAT steps per benchmark step (bounded sample)
+    u = c.u0.copy()
+    for _ in range(args.warmup):
+        u, _, _ = O.step_1d(pr, u)
+    u = c.u0.copy()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per):
+            u, _, _ = O.step_1d(pr, u)
+    el = time.perf_counter() - t0
+    val = NX * per * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "P": P_MAIN,
+                       "acat_steps_per_bench_step": per, "precision": "f64"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+                             "sample": f"{per} consecutive oracle steps per benchmark step, "
+                                       f"from the workload's initial state"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def profile_traffic(kernel_src: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    got, src = None, None
+    for line in open(PROFILE):
+        if line.startswith("traffic_bytes_per_launch:"):
+            got = float(line.split(":", 1)[1])
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+    return got if src == sha else None
+
+
+def order_hist(ctx, torch, u0, steps, nx, probes=5):
+    """Order histograms at a few steps of the trajectory (outside timing)."""
+    u = u0.clone()
+    tmp = torch.empty_like(u)
+    orders = torch.zeros(nx + 1, dtype=torch.int8, device=u.device)
+    at = sorted(set([0] + [int(steps * k / (probes - 1)) - 1 for k in range(1, probes)]))
+    hists, done = [], 0
+    for s in at:
+        if s > done:
+            ctx.acat_run(u, s - done)
+            done = s
+        ctx.acat_step(u, tmp, -1.0, None, None, orders)
+        torch.cuda.synchronize()
+        hists.append(torch.bincount(orders.to(torch.int64), minlength=5).cpu().tolist())
+    return hists
+
+
+def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_clocks, dev_index):
+    c = W.euler1d_riemann_entropy(nx=nx, seed=SEED, P=P, steps=acat_steps, cfl=CFL)
+    ctx = acat.Context(**c.problem_kwargs(), precision=prec)
+    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        u.copy_(u0)
+        ctx.acat_run(u, acat_steps)
+
+    for _ in range(Wm):
+        one()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev_index) if want_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    l0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for k in range(K):
+        flush.zero_()  # evict L2 between timed runs (outside the timed events)
+        ev[k][0].record(stream)
+        one()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
+    clk = clocks.stop() if clocks else None
+    assert ctx.acat_status() == 0, "device status flags set"
+    ms = [a.elapsed_time(b) for a, b in ev]
+    hists = order_hist(ctx, torch, u0, acat_steps, nx)
+    avg = [sum(h[k] for h in hists) / len(hists) for k in range(5)]
+    fl = flops.step_flops_1d({k: avg[k] for k in range(1, 5)}, P, W.EULER1D, nx)
+    res = dict(ms=ms, launches=launches, clocks=clk, flops_per_step=fl,
+               order_mix={str(k): round(avg[k] / (nx + 1), 4) for k in range(1, 5)},
+               ctx=ctx, case=c, u0=u0)
+    return res
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2007_01416_gb300 import acat, flops
+    from paper_2007_01416_gb300 import build as B
+    from paper_2007_01416_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    B.build()
+    dev_index = torch.cuda.current_device()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    peak64 = max(acat.acat_measure_fma_peak(0) for _ in range(3))
+    peak32 = max(acat.acat_measure_fma_peak(1) for _ in range(3))
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F64, args.acat_steps, args.steps,
+                args.warmup, flush, rank == 0, dev_index)
+    tot_ms = sum(m["ms"])
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    cells_steps = NX * args.acat_steps
+    value = world * cells_steps * args.steps / (tot_ms * 1e-3)
+    ms_per_step = tot_ms / args.steps
+    kernel_ms = ms_per_step / args.acat_steps  # one step kernel per ACAT step
+    achieved = m["flops_per_step"] / (kernel_ms * 1e-3)
+
+    # end-to-end through the host-buffer entry point (pinned memory)
+    ctx, c = m["ctx"], m["case"]
+    host_in = torch.from_numpy(c.u0.copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_ms = []
+    stream = torch.cuda.current_stream()
+    for k in range(2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.acat_run_host(host_in, host_out, args.acat_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    sb = ctx.state_bytes()
+    e2e_val = cells_steps / (min(e2e_ms) * 1e-3)
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        v = measure(torch, acat, W, flops, NX, 2, acat.PREC_F64, args.acat_steps, 2, 1, flush,
+                    False, dev_index)
+        vms = sum(v["ms"]) / 2
+        variants["P2_f64"] = {
+            "value": cells_steps / (vms * 1e-3), "unit": UNIT, "ms_per_step": vms,
+            "roofline_frac": v["flops_per_step"] / (vms / args.acat_steps * 1e-3) / peak64,
+            "order_mix": v["order_mix"]}
+
+    if rank != 0:
+        return 0
+    kernel_src = os.path.join(ROOT, "paper_2007_01416_gb300", "csrc", "step1d.cu")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "P": P_MAIN, "acat_steps": args.acat_steps,
+                   "precision": "f64", "cfl": CFL, "seed": SEED,
+                   "l2": "256 MiB buffer written between timed runs; the 0.4 MB state is "
+                         "L2-resident within a run (the step is FP64-pipe bound)"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak64,
+                     "traffic": profile_traffic(kernel_src),
+                     "kernel": f"k_step1d_f64<P={P_MAIN},Euler1D>",
+                     "peak_source": "measured live: FP64 FMA-chain kernel on all SMs (best of 3)",
+                     "flops_per_launch": m["flops_per_step"], "kernel_ms": kernel_ms,
+                     "order_mix": m["order_mix"]},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb,
+                "ms_per_step": min(e2e_ms)},
+        "gpu_launches": m["launches"],
+        "clocks": m["clocks"],
+        "fma_peaks_tflops": {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12},
+        "variants": variants,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * acat.h -- C ABI of libacat, the GB300 (sm_103a) implementation of the
+ * explicit time step of the Adaptive Compact Approximate Taylor (ACAT) method
+ * of Carrillo, Macca, Pares, Russo and Zorio, "An order-adaptive compact
+ * approximation Taylor method for systems of conservation laws"
+ * (arXiv 2007.01416).
+ *
+ * One step (Sec. 3.3, Eq. 3.19; 2D: Sec. 4, Eq. 4.9) does, at every
+ * interface x_{i+1/2}:
+ *   - the smoothness indicators psi^p, p = 2..P, on the centred stencils S_p
+ *     (Eqs. 3.8-3.12; systems: minimum over components, Sec. 3.4);
+ *   - the order selection p_s = max A (Eqs. 3.2-3.3);
+ *   - the CAT2p_s flux by the local Taylor recursion (Sec. 2.2, Eq. 2.14),
+ *     or, when A is empty, the FL-CAT2 flux psi^1 F^CAT2 + (1-psi^1) F^lo with
+ *     the superbee limiter (Eqs. 3.4-3.7) and a Rusanov F^lo;
+ *   - the conservative update u_i += dt/dx (F_{i-1/2} - F_{i+1/2}) (Eq. 2.12);
+ * with dt = CFL dx / s^max (1D) or CFL/2 min(dx/s^max_x, dy/s^max_y) (2D,
+ * Sec. 5.5), s^max reduced on the device.
+ *
+ * Conventions
+ *   - Every pointer named *_dev is a device pointer on the current device; the
+ *     caller owns it. *_host pointers are host memory.
+ *   - State layout, FP64: SoA doubles, 1D u[c][i] (c < s, i < nx),
+ *     2D u[c][y][x]; s = 1 (linear, Burgers), 3 (Euler 1D), 4 (Euler 2D).
+ *   - State layout, FP32 (ACAT_PREC_F32): a compensated pair of float SoA
+ *     arrays, hi[s][...] followed by lo[s][...]; the represented value is
+ *     hi + lo.
+ *   - Interfaces, 1D: m = 0..nx, interface m between cells m-1 and m. 2D:
+ *     x-interfaces [y][m] (m = 0..nx), y-interfaces [m][x] (m = 0..ny).
+ *   - Order codes (int8): p_s in 2..P, or 1 when the FL-CAT2 flux was used.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream). All calls
+ *     except acat_create, acat_destroy and acat_status are asynchronous on it.
+ *   - Return values: ACAT_OK (0) or a negative ACAT_ERR_* code; no call
+ *     throws. Errors the device detects (non-physical states, a bad dt) are
+ *     recorded as sticky ACAT_STATUS_* bits, read by acat_status.
+ */
+#ifndef ACAT_H
+#define ACAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acat_ctx acat_ctx; /* opaque, owned by the library */
+
+enum { ACAT_FLUX_LINEAR = 0, ACAT_FLUX_BURGERS = 1, ACAT_FLUX_EULER1D = 2, ACAT_FLUX_EULER2D = 3 };
+enum { ACAT_BC_PERIODIC = 0, ACAT_BC_TRANSMISSIVE = 1 };
+enum { ACAT_PREC_F64 = 0, ACAT_PREC_F32 = 1 };
+
+enum {
+  ACAT_OK = 0,
+  ACAT_ERR_INVALID_ARG = -1,
+  ACAT_ERR_CUDA = -2,
+  ACAT_ERR_NOMEM = -3,
+  ACAT_ERR_NONPHYSICAL = -4,
+  ACAT_ERR_UNSUPPORTED = -5,
+  ACAT_ERR_TOO_LARGE = -6
+};
+
+/* sticky device status bits */
+enum {
+  ACAT_STATUS_NONPHYSICAL = 1u, /* rho <= 0, p <= 0 or a non-finite state  */
+  ACAT_STATUS_BAD_DT = 2u       /* s^max not positive and finite           */
+};
+
+/* Problem description in the terms of the paper.
+ *   flux          ACAT_FLUX_*; Euler uses gamma (Sec. 5.3, 5.5), linear
+ *                 transport uses adv[0] (x) and adv[1] (y) (Eqs. 5.1, 5.13).
+ *   P             maximal half-width 1..4 (order up to 2P); P = 1 is FL-CAT2.
+ *   nx, ny        cells; ny = 1 for 1D.
+ *   x0..y1        domain; cell centres x_i = x0 + (i + 1/2) dx.
+ *   bc            ACAT_BC_PERIODIC or ACAT_BC_TRANSMISSIVE (zero-gradient
+ *                 ghost cells, the "outflow"/"free" conditions of Sec. 5).
+ *   precision     ACAT_PREC_F64, or ACAT_PREC_F32 (float arithmetic on a
+ *                 compensated float-pair state; indicators in FP64).
+ *   cfl           CFL number of the dt rule above.
+ *   psi_tol       p is admissible when psi^p >= 1 - psi_tol (the paper's
+ *                 "psi^p ~ 1", Eq. 3.2, has no threshold; default 0.1).
+ *   eps           epsilon of the lateral weights (Eq. 3.8), default 1e-12.
+ *   tau_factorial 1 (default): tau_p = ((2p-1)! Delta^{2p-1})^2 as printed
+ *                 in Eq. 3.12; 0 drops the factorial.
+ *   limiter_form  0 (default): Roe-speed side for scalar laws (Eq. 3.6),
+ *                 min form for systems (Eq. 3.7); 1: min form everywhere. */
+typedef struct {
+  int flux;
+  int P;
+  int nx, ny;
+  int bc;
+  int precision;
+  int tau_factorial;
+  int limiter_form;
+  double gamma;
+  double adv[2];
+  double cfl;
+  double x0, x1, y0, y1;
+  double psi_tol;
+  double eps;
+} acat_params;
+
+/* Fills *p with the defaults above (gamma 1.4, CFL 0.5, psi_tol 0.1,
+ * eps 1e-12, [0,1]^2, periodic, FP64, P = 2, Burgers, nx = 64, ny = 1). */
+void acat_default_params(acat_params *p);
+
+/* Validates *p, uploads the differentiation-weight tables (Eq. 2.10; the flux
+ * weights of Eq. 2.14 are those that satisfy Eq. 2.11 at k = 1) to the
+ * current device and allocates the context's device workspace (dt/time
+ * slots, status word). Errors: INVALID_ARG (bad field, nx < 2P, P outside
+ * 1..4, 2D with P > 2 or non-Euler/linear flux), UNSUPPORTED, NOMEM, CUDA. */
+int acat_create(const acat_params *p, acat_ctx **out);
+
+/* Frees every device and host resource of ctx (synchronises first). */
+int acat_destroy(acat_ctx *ctx);
+
+/* Size in bytes of one state buffer of ctx (s * cells * 8, or 2 * s *
+ * cells * 4 in FP32). */
+int64_t acat_state_bytes(const acat_ctx *ctx);
+
+/* One ACAT step u_in -> u_out (device buffers, must not alias).
+ *   dt > 0 imposes that time step; dt <= 0 computes the CFL time step of
+ *   u_in on the device.
+ *   dt_dev (nullable): receives the dt used (one double).
+ *   orders_dev (nullable): receives the order codes, nx + 1 int8 (1D) or
+ *   ny*(nx+1) + (ny+1)*nx (2D: x-interfaces then y-interfaces). */
+int acat_step(acat_ctx *ctx, const void *u_in_dev, void *u_out_dev, double dt, void *stream,
+              double *dt_dev, int8_t *orders_dev);
+
+/* nsteps ACAT steps in place on u_dev, each with the CFL dt of its own
+ * state, reduced on the device (dt never returns to the host). With
+ * t_end > 0 the last step is clipped so that t stops at t_end and further
+ * steps do nothing. The step sequence is replayed from CUDA graphs.
+ * t_dev (nullable): receives the final time (one double). */
+int acat_run(acat_ctx *ctx, void *u_dev, int nsteps, double t_end, void *stream, double *t_dev);
+
+/* acat_run on host memory: copies u_host_in to the device, runs, copies the
+ * result to u_host_out (may equal u_host_in), all on `stream`, and
+ * synchronises it. Pinned host memory makes the copies asynchronous. */
+int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int nsteps, double t_end,
+                  void *stream, double *t_host);
+
+/* Reads and returns the sticky device status bits (synchronises ctx's
+ * work). Returns ACAT_ERR_NONPHYSICAL when any bit is set. */
+int acat_status(acat_ctx *ctx, unsigned *flags_out);
+
+/* Clears the sticky status bits. */
+int acat_clear_status(acat_ctx *ctx);
+
+/* Human-readable text of an ACAT_ERR_* code (static storage). */
+const char *acat_strerror(int code);
+
+/* Kernel launches issued by this context since creation (step kernels,
+ * dt reductions and graph-replayed kernels each count one per launch). */
+int64_t acat_launch_count(const acat_ctx *ctx);
+
+/* Measured peak of the CUDA-core FMA pipe on the current device, in
+ * FLOP/s (FMA = 2 flops): precision 0 FP64, 1 FP32. Runs a dependent-chain
+ * FMA kernel that fills every SM; used as the roofline denominator of the
+ * arithmetic-bound step. Returns a negative number on error. */
+double acat_measure_fma_peak(int precision, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACAT_H */

@@ -1,0 +1,180 @@
+"""ctypes binding of libacat (include/acat.h), with the same entry-point
+names. It only marshals arguments: every step of the ACAT path runs in the
+library's CUDA kernels. Device buffers are torch CUDA tensors (or raw device
+addresses); streams default to torch's current stream.
+
+Loading fails loudly when ``libacat.so`` is missing or cannot be loaded: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libacat.so")
+
+LINEAR, BURGERS, EULER1D, EULER2D = 0, 1, 2, 3
+PERIODIC, TRANSMISSIVE = 0, 1
+PREC_F64, PREC_F32 = 0, 1
+STATUS_NONPHYSICAL, STATUS_BAD_DT = 1, 2
+
+
+class AcatError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class acat_params(ctypes.Structure):
+    _fields_ = [
+        ("flux", ctypes.c_int), ("P", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("tau_factorial", ctypes.c_int),
+        ("limiter_form", ctypes.c_int), ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2),
+        ("cfl", ctypes.c_double), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("psi_tol", ctypes.c_double),
+        ("eps", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libacat.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        pp = ctypes.POINTER(acat_params)
+        L.acat_default_params.argtypes = [pp]
+        L.acat_default_params.restype = None
+        L.acat_create.argtypes = [pp, ctypes.POINTER(vp)]
+        L.acat_destroy.argtypes = [vp]
+        L.acat_state_bytes.argtypes = [vp]
+        L.acat_state_bytes.restype = ctypes.c_int64
+        L.acat_step.argtypes = [vp, vp, vp, d, vp, vp, vp]
+        L.acat_run.argtypes = [vp, vp, i, d, vp, vp]
+        L.acat_run_host.argtypes = [vp, vp, vp, i, d, vp, vp]
+        L.acat_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint)]
+        L.acat_clear_status.argtypes = [vp]
+        L.acat_strerror.argtypes = [i]
+        L.acat_strerror.restype = ctypes.c_char_p
+        L.acat_launch_count.argtypes = [vp]
+        L.acat_launch_count.restype = ctypes.c_int64
+        L.acat_measure_fma_peak.argtypes = [i, vp]
+        L.acat_measure_fma_peak.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().acat_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise AcatError(rc, what)
+
+
+def default_params() -> acat_params:
+    p = acat_params()
+    lib().acat_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(**kw) -> acat_params:
+    """acat_params from keyword arguments (defaults from the library)."""
+    p = default_params()
+    for k, v in kw.items():
+        if k == "adv":
+            p.adv[0], p.adv[1] = float(v[0]), float(v[1])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def acat_measure_fma_peak(precision: int, stream=None) -> float:
+    return float(lib().acat_measure_fma_peak(int(precision), _stream(stream)))
+
+
+class Context:
+    """An acat_ctx: one problem (flux, P, grid, BC, precision) on the current
+    device. Methods mirror the C entry points."""
+
+    def __init__(self, params: acat_params | None = None, **kw):
+        self.params = params if params is not None else make_params(**kw)
+        h = ctypes.c_void_p()
+        _check(lib().acat_create(ctypes.byref(self.params), ctypes.byref(h)), "acat_create")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def state_bytes(self) -> int:
+        return int(lib().acat_state_bytes(self._h))
+
+    def acat_step(self, u_in, u_out, dt: float = -1.0, stream=None, dt_out=None, orders_out=None):
+        _check(lib().acat_step(self._h, _ptr(u_in), _ptr(u_out), float(dt), _stream(stream),
+                               _ptr(dt_out), _ptr(orders_out)), "acat_step")
+
+    def acat_run(self, u, nsteps: int, t_end: float = -1.0, stream=None, t_out=None):
+        _check(lib().acat_run(self._h, _ptr(u), int(nsteps), float(t_end), _stream(stream),
+                              _ptr(t_out)), "acat_run")
+
+    def acat_run_host(self, u_host_in, u_host_out, nsteps: int, t_end: float = -1.0,
+                      stream=None) -> float:
+        t = ctypes.c_double(0.0)
+        _check(lib().acat_run_host(self._h, _ptr(u_host_in), _ptr(u_host_out), int(nsteps),
+                                   float(t_end), _stream(stream), ctypes.byref(t)),
+               "acat_run_host")
+        return t.value
+
+    def acat_status(self) -> int:
+        f = ctypes.c_uint(0)
+        rc = lib().acat_status(self._h, ctypes.byref(f))
+        if rc not in (0, -4):
+            _check(rc, "acat_status")
+        return int(f.value)
+
+    def acat_clear_status(self) -> None:
+        _check(lib().acat_clear_status(self._h), "acat_clear_status")
+
+    def launch_count(self) -> int:
+        return int(lib().acat_launch_count(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().acat_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

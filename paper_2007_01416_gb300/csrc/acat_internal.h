@@ -1,0 +1,51 @@
+// acat_internal.h -- declarations shared by the translation units of libacat.
+#pragma once
+
+#include <cstdint>
+
+#define ACAT_MAXP 4
+#define ACAT_MAXN 8
+
+// Differentiation-weight tables (built on the host in exact arithmetic by
+// weights.cpp, kept in __constant__ memory on each device). Index p is the
+// half-width, node and time-level indices r run over 0..2p-1 for the offsets
+// r - p + 1.
+struct AcatTables {
+  double g1[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];      // gamma^{1,j}_{p,r}   [p][j][r]
+  double gk[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];      // gamma^{k,0}_{p,r}   [p][k][r]
+  double gh[ACAT_MAXP + 1][ACAT_MAXN];                 // flux weights, Eq. 2.14
+  double gd[ACAT_MAXP + 1][ACAT_MAXN];                 // gamma^{2p-1,1/2}, binomial
+  double taylor[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];  // r^l / l!            [p][r][l]
+  double fact[ACAT_MAXP + 1];                          // (2p-1)!
+  double invfact[ACAT_MAXN + 1];                       // 1 / k!
+};
+
+void acat_build_tables(AcatTables *T);
+
+// Arguments of one 1D step launch (passed by value).
+struct Step1DArgs {
+  const void *u_in;           // FP64: double[s][N]; FP32: float hi[s][N], lo[s][N]
+  void *u_out;
+  int N;                      // cells
+  int bc;                     // ACAT_BC_*
+  int limiter_form;
+  int slot;                   // step index mod 3 (dt-reduction slots)
+  double dx, cfl;
+  double dt_fixed;            // > 0: imposed dt
+  double t_end;               // > 0: clip t at t_end
+  double gamma, adv, eps, thr;
+  double fact_tau[ACAT_MAXP + 1];
+  unsigned long long *smax;   // 3 slots: max wave speed as ordered double bits
+  double *tslot;              // 3 slots: simulated time (nullable)
+  int8_t *orders;             // N+1 order codes (nullable)
+  double *dt_out;             // dt used (nullable)
+  unsigned *status;           // sticky status bits
+};
+
+// Initial wave-speed reduction into smax[slot] (and t = 0 into tslot[slot]).
+int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream);
+// One 1D step; returns 0 or a cudaError_t value.
+int acat_launch_step1d(int P, int flux, int prec, const Step1DArgs &a, void *stream);
+int acat_upload_tables_current_device();
+int acat_cells_per_cta_1d(int P, int prec);
+double acat_fma_peak_run(int precision, void *stream);

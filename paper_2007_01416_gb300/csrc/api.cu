@@ -1,0 +1,354 @@
+// api.cu -- the C ABI of libacat (declared in include/acat.h): context
+// lifetime, argument checks, the step and run drivers (CUDA-graph replay of
+// the time loop with the dt reduction kept on the device), status words.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/acat.h"
+#include "acat_internal.h"
+
+struct acat_ctx {
+  acat_params p;
+  int s = 1;
+  int device = 0;
+  long cells = 0;
+  unsigned long long *d_smax = nullptr;  // 3 slots
+  double *d_t = nullptr;                 // 3 slots
+  unsigned *d_status = nullptr;
+  void *d_work = nullptr;                // second state buffer (run ping-pong)
+  void *d_host_stage = nullptr;          // device buffer for acat_run_host
+  cudaStream_t cap_stream = nullptr;     // stream used for graph capture
+  cudaGraphExec_t chain = nullptr;       // GRAPH_STEPS steps, starting at step % 6 == 0
+  void *chain_u = nullptr;
+  double chain_t_end = 0.0;
+  double fact_tau[ACAT_MAXP + 1] = {0};  // (2p-1)! or 1 (tau_factorial)
+  int64_t launches = 0;
+};
+
+namespace {
+
+constexpr int GRAPH_STEPS = 48;  // multiple of 2 (ping-pong) and 3 (dt slots)
+
+std::mutex g_tab_mu;
+bool g_tab_done[64] = {false};
+
+int nvars(int flux) {
+  switch (flux) {
+  case ACAT_FLUX_EULER1D: return 3;
+  case ACAT_FLUX_EULER2D: return 4;
+  default: return 1;
+  }
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? ACAT_OK : ACAT_ERR_CUDA; }
+
+int check_params(const acat_params *p) {
+  if (!p) return ACAT_ERR_INVALID_ARG;
+  if (p->P < 1 || p->P > ACAT_MAXP) return ACAT_ERR_INVALID_ARG;
+  if (p->flux < ACAT_FLUX_LINEAR || p->flux > ACAT_FLUX_EULER2D) return ACAT_ERR_INVALID_ARG;
+  if (p->bc != ACAT_BC_PERIODIC && p->bc != ACAT_BC_TRANSMISSIVE) return ACAT_ERR_INVALID_ARG;
+  if (p->precision != ACAT_PREC_F64 && p->precision != ACAT_PREC_F32) return ACAT_ERR_INVALID_ARG;
+  if (p->ny < 1 || p->nx < 2 * (p->P > 2 ? p->P : 2)) return ACAT_ERR_INVALID_ARG;
+  if (!(p->cfl > 0.0) || !std::isfinite(p->cfl)) return ACAT_ERR_INVALID_ARG;
+  if (!(p->x1 > p->x0) || !(p->y1 > p->y0)) return ACAT_ERR_INVALID_ARG;
+  if (!(p->psi_tol >= 0.0 && p->psi_tol < 1.0)) return ACAT_ERR_INVALID_ARG;
+  if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return ACAT_ERR_INVALID_ARG;
+  if ((p->flux == ACAT_FLUX_EULER1D || p->flux == ACAT_FLUX_EULER2D) && !(p->gamma > 1.0))
+    return ACAT_ERR_INVALID_ARG;
+  const bool is2d = p->ny > 1 || p->flux == ACAT_FLUX_EULER2D;
+  if (is2d) return ACAT_ERR_UNSUPPORTED;
+  if (p->flux == ACAT_FLUX_EULER2D) return ACAT_ERR_INVALID_ARG;
+  if (p->precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;
+  if ((long)p->nx > (1l << 30)) return ACAT_ERR_TOO_LARGE;
+  return ACAT_OK;
+}
+
+Step1DArgs base_args(acat_ctx *c) {
+  Step1DArgs a;
+  std::memset(&a, 0, sizeof a);
+  const acat_params &p = c->p;
+  a.N = p.nx;
+  a.bc = p.bc;
+  a.limiter_form = p.limiter_form;
+  a.dx = (p.x1 - p.x0) / (double)p.nx;
+  a.cfl = p.cfl;
+  a.dt_fixed = -1.0;
+  a.t_end = -1.0;
+  a.gamma = p.gamma;
+  a.adv = p.adv[0];
+  a.eps = p.eps;
+  a.thr = 1.0 - p.psi_tol;
+  for (int q = 0; q <= ACAT_MAXP; q++) a.fact_tau[q] = c->fact_tau[q];
+  a.smax = c->d_smax;
+  a.status = c->d_status;
+  return a;
+}
+
+int launch_step(acat_ctx *c, const Step1DArgs &a, cudaStream_t st) {
+  int e = acat_launch_step1d(c->p.P, c->p.flux, c->p.precision, a, st);
+  c->launches++;
+  return e ? ACAT_ERR_CUDA : ACAT_OK;
+}
+
+// Steps n..n+count-1 of a run on (u, work), dt slots n % 3.
+int issue_steps(acat_ctx *c, void *u, long n, int count, double t_end, cudaStream_t st) {
+  Step1DArgs a = base_args(c);
+  a.t_end = t_end;
+  a.tslot = c->d_t;
+  for (int k = 0; k < count; k++, n++) {
+    a.u_in = (n % 2 == 0) ? u : c->d_work;
+    a.u_out = (n % 2 == 0) ? c->d_work : u;
+    a.slot = (int)(n % 3);
+    int rc = launch_step(c, a, st);
+    if (rc) return rc;
+  }
+  return ACAT_OK;
+}
+
+int ensure_chain(acat_ctx *c, void *u, double t_end) {
+  if (c->chain && c->chain_u == u && c->chain_t_end == t_end) return ACAT_OK;
+  if (c->chain) {
+    cudaGraphExecDestroy(c->chain);
+    c->chain = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  const int64_t before = c->launches;
+  int rc = issue_steps(c, u, 0, GRAPH_STEPS, t_end, c->cap_stream);
+  c->launches = before;  // captured, not launched
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return ACAT_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&c->chain, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->chain = nullptr;
+    return ACAT_ERR_CUDA;
+  }
+  c->chain_u = u;
+  c->chain_t_end = t_end;
+  return ACAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void acat_default_params(acat_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->flux = ACAT_FLUX_BURGERS;
+  p->P = 2;
+  p->nx = 64;
+  p->ny = 1;
+  p->bc = ACAT_BC_PERIODIC;
+  p->precision = ACAT_PREC_F64;
+  p->tau_factorial = 1;
+  p->limiter_form = 0;
+  p->gamma = 1.4;
+  p->adv[0] = 1.0;
+  p->adv[1] = 1.0;
+  p->cfl = 0.5;
+  p->x0 = 0.0;
+  p->x1 = 1.0;
+  p->y0 = 0.0;
+  p->y1 = 1.0;
+  p->psi_tol = 0.1;
+  p->eps = 1e-12;
+}
+
+int acat_create(const acat_params *p, acat_ctx **out) {
+  if (!out) return ACAT_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = check_params(p);
+  if (rc) return rc;
+  acat_ctx *c = new (std::nothrow) acat_ctx();
+  if (!c) return ACAT_ERR_NOMEM;
+  c->p = *p;
+  c->s = nvars(p->flux);
+  c->cells = (long)p->nx * p->ny;
+  {
+    AcatTables T;
+    acat_build_tables(&T);
+    for (int q = 0; q <= ACAT_MAXP; q++) c->fact_tau[q] = p->tau_factorial ? T.fact[q] : 1.0;
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return ACAT_ERR_CUDA;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (c->device < 0 || c->device >= 64) {
+      delete c;
+      return ACAT_ERR_UNSUPPORTED;
+    }
+    if (!g_tab_done[c->device]) {
+      if (acat_upload_tables_current_device() != 0) {
+        delete c;
+        return ACAT_ERR_CUDA;
+      }
+      g_tab_done[c->device] = true;
+    }
+  }
+  const size_t sb = (size_t)acat_state_bytes(c);
+  cudaError_t e = cudaMalloc(&c->d_smax, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_t, 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_work, sb);
+  if (e == cudaSuccess) e = cudaMemset(c->d_smax, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_t, 0, 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    acat_destroy(c);
+    return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+  }
+  *out = c;
+  return ACAT_OK;
+}
+
+int acat_destroy(acat_ctx *c) {
+  if (!c) return ACAT_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  if (c->chain) cudaGraphExecDestroy(c->chain);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->d_smax);
+  cudaFree(c->d_t);
+  cudaFree(c->d_status);
+  cudaFree(c->d_work);
+  cudaFree(c->d_host_stage);
+  delete c;
+  return ACAT_OK;
+}
+
+int64_t acat_state_bytes(const acat_ctx *c) {
+  if (!c) return ACAT_ERR_INVALID_ARG;
+  const int64_t n = (int64_t)c->s * c->cells;
+  return c->p.precision == ACAT_PREC_F64 ? n * 8 : n * 8;  // FP32: hi + lo floats
+}
+
+int acat_step(acat_ctx *c, const void *u_in, void *u_out, double dt, void *stream, double *dt_dev,
+              int8_t *orders_dev) {
+  if (!c || !u_in || !u_out || u_in == u_out) return ACAT_ERR_INVALID_ARG;
+  if (!(dt > 0.0) && dt != dt) return ACAT_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Step1DArgs a = base_args(c);
+  a.u_in = u_in;
+  a.u_out = u_out;
+  a.slot = 0;
+  a.orders = orders_dev;
+  a.dt_out = dt_dev;
+  cudaError_t e = cudaMemsetAsync(c->d_smax, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return ACAT_ERR_CUDA;
+  if (dt > 0.0) {
+    a.dt_fixed = dt;
+  } else {
+    if (acat_launch_smax1d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+    c->launches++;
+  }
+  return launch_step(c, a, st);
+}
+
+int acat_run(acat_ctx *c, void *u, int nsteps, double t_end, void *stream, double *t_dev) {
+  if (!c || !u || nsteps < 0) return ACAT_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (t_end != t_end) return ACAT_ERR_INVALID_ARG;
+  Step1DArgs a = base_args(c);
+  a.u_in = u;
+  a.slot = 0;
+  a.tslot = c->d_t;
+  if (cudaMemsetAsync(c->d_smax, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  if (acat_launch_smax1d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+  c->launches++;
+  long n = 0;
+  const int chunks = nsteps / GRAPH_STEPS;
+  if (chunks > 0) {
+    int rc = ensure_chain(c, u, t_end);
+    if (rc) return rc;
+    for (int k = 0; k < chunks; k++) {
+      if (cudaGraphLaunch(c->chain, st) != cudaSuccess) return ACAT_ERR_CUDA;
+      c->launches += GRAPH_STEPS;
+    }
+    n = (long)chunks * GRAPH_STEPS;
+  }
+  int rc = issue_steps(c, u, n, nsteps - (int)n, t_end, st);
+  if (rc) return rc;
+  if (nsteps % 2 == 1) {
+    if (cudaMemcpyAsync(u, c->d_work, (size_t)acat_state_bytes(c), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return ACAT_ERR_CUDA;
+  }
+  if (t_dev) {
+    if (cudaMemcpyAsync(t_dev, c->d_t + (nsteps % 3), sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return ACAT_ERR_CUDA;
+  }
+  return ACAT_OK;
+}
+
+int acat_run_host(acat_ctx *c, const void *u_host_in, void *u_host_out, int nsteps, double t_end,
+                  void *stream, double *t_host) {
+  if (!c || !u_host_in || !u_host_out) return ACAT_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sb = (size_t)acat_state_bytes(c);
+  if (!c->d_host_stage) {
+    cudaError_t e = cudaMalloc(&c->d_host_stage, sb + sizeof(double));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+  }
+  double *d_tfin = reinterpret_cast<double *>(static_cast<char *>(c->d_host_stage) + sb);
+  if (cudaMemcpyAsync(c->d_host_stage, u_host_in, sb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  int rc = acat_run(c, c->d_host_stage, nsteps, t_end, stream, d_tfin);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(u_host_out, c->d_host_stage, sb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  if (t_host && cudaMemcpyAsync(t_host, d_tfin, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  return cuda_err(cudaStreamSynchronize(st));
+}
+
+int acat_status(acat_ctx *c, unsigned *flags) {
+  if (!c) return ACAT_ERR_INVALID_ARG;
+  unsigned f = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return ACAT_ERR_CUDA;
+  if (cudaMemcpy(&f, c->d_status, sizeof f, cudaMemcpyDeviceToHost) != cudaSuccess) return ACAT_ERR_CUDA;
+  if (flags) *flags = f;
+  return f ? ACAT_ERR_NONPHYSICAL : ACAT_OK;
+}
+
+int acat_clear_status(acat_ctx *c) {
+  if (!c) return ACAT_ERR_INVALID_ARG;
+  return cuda_err(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+}
+
+const char *acat_strerror(int code) {
+  switch (code) {
+  case ACAT_OK: return "ok";
+  case ACAT_ERR_INVALID_ARG: return "invalid argument";
+  case ACAT_ERR_CUDA: return "CUDA runtime error";
+  case ACAT_ERR_NOMEM: return "out of device memory";
+  case ACAT_ERR_NONPHYSICAL: return "non-physical state or bad time step detected on the device";
+  case ACAT_ERR_UNSUPPORTED: return "configuration not supported";
+  case ACAT_ERR_TOO_LARGE: return "size exceeds the supported maximum";
+  }
+  return "unknown error";
+}
+
+int64_t acat_launch_count(const acat_ctx *c) { return c ? c->launches : -1; }
+
+double acat_measure_fma_peak(int precision, void *stream) {
+  if (precision != 0 && precision != 1) return -1.0;
+  return acat_fma_peak_run(precision, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,521 @@
+// step1d.cu -- the 1D ACAT step on sm_103a CUDA cores.
+//
+// One CTA owns T consecutive cells and computes the T+1 interface fluxes
+// around them (the last one is recomputed by the next CTA). The cells
+// [i0 - GH, i0 + T + GH) are staged once in shared memory with the boundary
+// condition applied while loading. Each interface is worked by a group of 2P
+// lanes of one warp, one lane per stencil node j = -p+1..p:
+//   - lanes 0..P-2 of the group evaluate the indicators psi^{l+2}
+//     (Eqs. 3.8-3.12, minimum over components, Sec. 3.4) with explicitly
+//     rounded FP64 operations in the order of their definition, so that the
+//     order decision is bit-identical to a literal FP64 evaluation; a warp
+//     ballot then gives p_s = max A (Eqs. 3.2-3.3);
+//   - for p_s >= 2 every lane runs the local Taylor recursion of Sec. 2.2 for
+//     its node in registers, in the dt-scaled form
+//         U^(k-1)_j = -lambda sum_r gamma^{1,j}_r F^(k-2)_r     (shuffles)
+//         F^(k-1)_j = sum_r gamma^{k-1,0}_r f(u_j + sum_l r^l/l! U^(l)_j)
+//     (U^(l) = dt^l u~^(l), F^(k) = dt^k f~^(k)), keeping the Taylor sums at
+//     the 2p-1 time levels r != 0 as running values (one FMA per level and
+//     order instead of a Horner pass); the flux is sum_k 1/k! sum_j
+//     gamma^{0,1/2}_j F^(k-1)_j (Eq. 2.14) reduced across the group;
+//   - for p_s = 1 lane 0 evaluates FL-CAT2 (Eqs. 3.4-3.7).
+// The conservative update (Eq. 2.12) follows from shared memory, and its
+// epilogue reduces the wave speed of the new state for the next step's CFL
+// dt into a triple-buffered slot (atomic max on ordered double bits).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/acat.h"
+#include "acat_internal.h"
+
+__constant__ AcatTables c_tab;
+
+namespace {
+
+constexpr int NT = 256;  // threads per CTA
+
+// ---------------------------------------------------------------------------
+// Physics
+// ---------------------------------------------------------------------------
+template <int FLUX>
+struct Phys;
+
+template <>
+struct Phys<ACAT_FLUX_LINEAR> {
+  static constexpr int S = 1;
+  template <typename R>
+  __device__ static __forceinline__ void flux(const R *u, R *f, R a, R /*gm1*/) { f[0] = a * u[0]; }
+  __device__ static __forceinline__ double speed(const double *u, double a, double, bool &ok) {
+    ok = isfinite(u[0]);
+    return fabs(a);
+  }
+};
+
+template <>
+struct Phys<ACAT_FLUX_BURGERS> {
+  static constexpr int S = 1;
+  template <typename R>
+  __device__ static __forceinline__ void flux(const R *u, R *f, R, R) { f[0] = R(0.5) * u[0] * u[0]; }
+  __device__ static __forceinline__ double speed(const double *u, double, double, bool &ok) {
+    ok = isfinite(u[0]);
+    return fabs(u[0]);
+  }
+};
+
+template <>
+struct Phys<ACAT_FLUX_EULER1D> {
+  static constexpr int S = 3;
+  template <typename R>
+  __device__ static __forceinline__ void flux(const R *u, R *f, R, R gm1) {
+    const R ri = R(1) / u[0];
+    const R v = u[1] * ri;
+    const R p = gm1 * (u[2] - R(0.5) * u[1] * v);
+    f[0] = u[1];
+    f[1] = u[1] * v + p;
+    f[2] = v * (u[2] + p);
+  }
+  // |v| + c with c = sqrt(gamma p / rho), every operation rounded as written
+  // (no contraction), so that the CFL dt is reproducible bit for bit
+  __device__ static __forceinline__ double speed(const double *u, double, double gamma, bool &ok) {
+    const double v = __ddiv_rn(u[1], u[0]);
+    const double ke = __dmul_rn(__dmul_rn(__dmul_rn(0.5, u[0]), v), v);
+    const double p = __dmul_rn(__dsub_rn(gamma, 1.0), __dsub_rn(u[2], ke));
+    ok = (u[0] > 0.0) && (p > 0.0) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+    return __dadd_rn(fabs(v), __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), u[0])));
+  }
+};
+
+__device__ __forceinline__ long bc_index(long g, long N, int bc) {
+  if (bc == ACAT_BC_PERIODIC) {
+    long r = g % N;
+    return r < 0 ? r + N : r;
+  }
+  return g < 0 ? 0 : (g >= N ? N - 1 : g);
+}
+
+// ---------------------------------------------------------------------------
+// Indicators and limiter: explicit round-to-nearest operations, no FMA
+// contraction, in the order of Eqs. 3.6-3.12.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double psi_p_comp(const double *q, int p, double eps, double fact) {
+  double IL = 0.0, IR = 0.0;
+  for (int j = -p + 1; j <= -1; j++) {
+    const double d = __dsub_rn(q[1 + j], q[j]);
+    IL = __dadd_rn(IL, __dmul_rn(d, d));
+  }
+  IL = __dadd_rn(IL, eps);
+  for (int j = 1; j <= p - 1; j++) {
+    const double d = __dsub_rn(q[1 + j], q[j]);
+    IR = __dadd_rn(IR, __dmul_rn(d, d));
+  }
+  IR = __dadd_rn(IR, eps);
+  const double I = __ddiv_rn(__dmul_rn(IL, IR), __dadd_rn(IL, IR));
+  double S = 0.0;
+  for (int j = -p + 1; j <= p; j++) S = __dadd_rn(S, __dmul_rn(c_tab.gd[p][j + p - 1], q[j]));
+  const double D = __dmul_rn(fact, S);
+  const double tau = __dmul_rn(D, D);
+  return __ddiv_rn(I, __dadd_rn(I, tau));
+}
+
+__device__ __forceinline__ double lim_ratio(double upw, double loc) {
+  if (loc == 0.0) {
+    if (upw == 0.0) return 1.0;
+    return upw > 0.0 ? __longlong_as_double(0x7ff0000000000000LL)
+                     : __longlong_as_double((long long)0xfff0000000000000ULL);
+  }
+  return __ddiv_rn(upw, loc);
+}
+
+__device__ __forceinline__ double superbee(double r) {
+  const double r2 = __dmul_rn(2.0, r);
+  const double a = r2 < 1.0 ? r2 : 1.0;
+  const double b = r < 2.0 ? r : 2.0;
+  const double m = a > b ? a : b;
+  return m > 0.0 ? m : 0.0;
+}
+
+// psi^1 at the interface between q[0] (cell i) and q[1]; stride between
+// components `cs`.
+template <int FLUX>
+__device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form, double adv) {
+  constexpr int S = Phys<FLUX>::S;
+  if (S == 1 && limiter_form == 0) {
+    const double um = q[-1], u0 = q[0], u1 = q[1], u2 = q[2];
+    double a;
+    if (u0 != u1) {
+      double f0, f1;
+      if (FLUX == ACAT_FLUX_LINEAR) {
+        f0 = __dmul_rn(adv, u0);
+        f1 = __dmul_rn(adv, u1);
+      } else {
+        f0 = __dmul_rn(__dmul_rn(0.5, u0), u0);
+        f1 = __dmul_rn(__dmul_rn(0.5, u1), u1);
+      }
+      a = __ddiv_rn(__dsub_rn(f1, f0), __dsub_rn(u1, u0));
+    } else {
+      a = (FLUX == ACAT_FLUX_LINEAR) ? adv : u0;
+    }
+    const double upw = a > 0.0 ? __dsub_rn(u0, um) : __dsub_rn(u2, u1);
+    return superbee(lim_ratio(upw, __dsub_rn(u1, u0)));
+  }
+  double best = 2.0;
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const double *p = q + c * cs;
+    const double loc = __dsub_rn(p[1], p[0]);
+    const double pm = superbee(lim_ratio(__dsub_rn(p[0], p[-1]), loc));
+    const double pp = superbee(lim_ratio(__dsub_rn(p[2], p[1]), loc));
+    const double v = pp < pm ? pp : pm;
+    if (v < best) best = v;
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// CAT2p flux of one interface by a group of 2p lanes (lane l <-> node
+// j = l - p + 1). q points at cell i (left of the interface) for component 0
+// in the shared tile, components `cs` apart. Lane 0 returns the flux.
+// ---------------------------------------------------------------------------
+template <int p, int FLUX>
+__device__ __forceinline__ void cat_flux(const double *q, int cs, int l, int base, double lam,
+                                         double adv, double gm1, double *Fout) {
+  constexpr int S = Phys<FLUX>::S;
+  constexpr int n = 2 * p;
+  const unsigned mask = ((n == 32) ? 0xffffffffu : ((1u << n) - 1u)) << base;
+  const int j = l - p + 1;
+  double g1r[n];
+#pragma unroll
+  for (int r = 0; r < n; r++) g1r[r] = c_tab.g1[p][l][r];
+  double f0[S], Fsum[S], Fprev[S], arg[n][S];
+  {
+    double u[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) u[c] = q[c * cs + j];
+    Phys<FLUX>::flux(u, f0, adv, gm1);
+#pragma unroll
+    for (int rr = 0; rr < n; rr++)
+#pragma unroll
+      for (int c = 0; c < S; c++) arg[rr][c] = u[c];
+  }
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    Fsum[c] = f0[c];
+    Fprev[c] = f0[c];
+  }
+#pragma unroll
+  for (int k = 2; k <= n; k++) {
+    double U[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) U[c] = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; r++)
+#pragma unroll
+      for (int c = 0; c < S; c++) U[c] = fma(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
+    double acc[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      U[c] *= -lam;
+      acc[c] = c_tab.gk[p][k - 1][p - 1] * f0[c];
+    }
+#pragma unroll
+    for (int rr = 0; rr < n; rr++) {
+      if (rr == p - 1) continue;  // r = 0: f(u_j) itself
+      const double cr = c_tab.taylor[p][rr][k - 1];
+      double fr[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) arg[rr][c] = fma(cr, U[c], arg[rr][c]);
+      Phys<FLUX>::flux(arg[rr], fr, adv, gm1);
+#pragma unroll
+      for (int c = 0; c < S; c++) acc[c] = fma(c_tab.gk[p][k - 1][rr], fr[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      Fprev[c] = acc[c];
+      Fsum[c] = fma(c_tab.invfact[k], acc[c], Fsum[c]);
+    }
+  }
+  const double w = c_tab.gh[p][l];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const double v = w * Fsum[c];
+    double t = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; r++) t += __shfl_sync(mask, v, base + r);
+    Fout[c] = t;
+  }
+}
+
+// FL-CAT2 flux (Eq. 3.4): the CAT2 flux (p = 1 recursion, Eqs. 2.16-2.17)
+// blended with Rusanov by the limiter psi^1. Single lane.
+template <int FLUX>
+__device__ __forceinline__ void flcat2_flux(const double *q, int cs, double lam, double adv,
+                                            double gamma, int limiter_form, double *F) {
+  constexpr int S = Phys<FLUX>::S;
+  const double gm1 = gamma - 1.0;
+  double u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    u0[c] = q[c * cs];
+    u1[c] = q[c * cs + 1];
+  }
+  Phys<FLUX>::flux(u0, f0, adv, gm1);
+  Phys<FLUX>::flux(u1, f1, adv, gm1);
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const double U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
+    a0[c] = u0[c] + U;
+    a1[c] = u1[c] + U;
+  }
+  Phys<FLUX>::flux(a0, t0, adv, gm1);
+  Phys<FLUX>::flux(a1, t1, adv, gm1);
+  bool ok;
+  const double s0 = Phys<FLUX>::speed(u0, adv, gamma, ok), s1 = Phys<FLUX>::speed(u1, adv, gamma, ok);
+  const double alpha = s1 > s0 ? s1 : s0;
+  const double w = psi1<FLUX>(q, cs, limiter_form, adv);
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const double F1 = 0.5 * (f0[c] + f1[c]) + 0.25 * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
+    const double Flo = 0.5 * (f0[c] + f1[c]) - 0.5 * alpha * (u1[c] - u0[c]);
+    F[c] = w * F1 + (1.0 - w) * Flo;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
+  // non-negative doubles (and +inf, NaN with sign bit clear) order like
+  // their bit patterns
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// dt of this step from the reduced wave speed (1D CFL rule); also advances
+// the simulated time and recycles the slot two steps ahead (block 0).
+__device__ double step_dt(const Step1DArgs &a) {
+  double dt;
+  if (a.dt_fixed > 0.0) {
+    dt = a.dt_fixed;
+  } else {
+    const double smax = __longlong_as_double((long long)a.smax[a.slot]);
+    if (!(smax > 0.0) || !isfinite(smax)) {
+      if (blockIdx.x == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_BAD_DT);
+      dt = 0.0;
+    } else {
+      dt = a.cfl * a.dx / smax;
+    }
+  }
+  double t = 0.0;
+  if (a.tslot) {
+    t = a.tslot[a.slot];
+    if (a.t_end > 0.0) {
+      if (t >= a.t_end) dt = 0.0;
+      else if (dt > a.t_end - t) dt = a.t_end - t;
+    }
+  }
+  if (blockIdx.x == 0) {
+    if (a.tslot) a.tslot[(a.slot + 1) % 3] = t + dt;
+    if (a.dt_out) *a.dt_out = dt;
+    a.smax[(a.slot + 2) % 3] = 0ull;
+  }
+  return dt;
+}
+
+template <int P>
+struct Tiling {
+  static constexpr int L = 2 * P;             // lanes per interface
+  static constexpr int GPW = 32 / L;          // interface groups per warp
+  static constexpr int NI = (NT / 32) * GPW;  // interfaces per CTA
+  static constexpr int T = NI - 1;            // cells per CTA
+  static constexpr int GH = P > 2 ? P : 2;    // ghost cells each side
+  static constexpr int TW = T + 2 * GH;       // staged cells
+};
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
+  using TL = Tiling<P>;
+  constexpr int S = Phys<FLUX>::S;
+  __shared__ double tile[S][TL::TW];
+  __shared__ double Fs[TL::NI][S];
+  __shared__ double s_dt;
+  __shared__ double s_red[NT / 32];
+  const double *__restrict__ uin = static_cast<const double *>(a.u_in);
+  double *__restrict__ uout = static_cast<double *>(a.u_out);
+  const long N = a.N;
+  const long i0 = (long)blockIdx.x * TL::T;
+
+  if (threadIdx.x == 0) s_dt = step_dt(a);
+  for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
+    const int c = q / TL::TW, k = q - c * TL::TW;
+    tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
+  }
+  __syncthreads();
+  const double dt = s_dt;
+  const double lam = dt / a.dx;
+  const double gm1 = a.gamma - 1.0;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / TL::L, l = lane - grp * TL::L;
+  const bool valid = grp < TL::GPW;
+  const int il = warp * TL::GPW + grp;  // local interface
+  const long m = i0 + il;               // interface between cells m-1 and m
+  const bool active = valid && m <= N;
+  const int ic = il - 1 + TL::GH;       // tile index of cell m-1
+
+  // --- indicators and order selection -------------------------------------
+  bool adm = false;
+  if (P >= 2 && active && l < P - 1) {
+    const int p = l + 2;
+    double mn = 0.0;
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const double v = psi_p_comp(&tile[c][ic], p, a.eps, a.fact_tau[p]);
+      if (c == 0 || v < mn) mn = v;
+    }
+    adm = mn >= a.thr;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, adm);
+  int ps = 1;
+  if (valid && P >= 2) {
+    const unsigned bits = (bal >> (grp * TL::L)) & ((1u << (P - 1 > 0 ? P - 1 : 0)) - 1u);
+    ps = bits ? (32 - __clz(bits)) + 1 : 1;
+  }
+
+  // --- flux ------------------------------------------------------------------
+  double F[S];
+  const int base = grp * TL::L;
+  const double *q0 = &tile[0][ic];
+  if (active) {
+    if (ps == 4) {
+      if constexpr (P >= 4) cat_flux<4, FLUX>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+    } else if (ps == 3) {
+      if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+    } else if (ps == 2) {
+      if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+    } else if (l == 0) {
+      flcat2_flux<FLUX>(q0, TL::TW, lam, a.adv, a.gamma, a.limiter_form, F);
+    }
+    if (l == 0) {
+#pragma unroll
+      for (int c = 0; c < S; c++) Fs[il][c] = F[c];
+      if (a.orders && (il < TL::T || m == N)) a.orders[m] = (int8_t)ps;
+    }
+  }
+  __syncthreads();
+
+  // --- conservative update and wave-speed epilogue ---------------------------
+  double smax = 0.0;
+  bool bad = false;
+  for (int t = threadIdx.x; t < TL::T; t += NT) {
+    const long i = i0 + t;
+    if (i >= N) break;
+    double un[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      un[c] = tile[c][t + TL::GH] + lam * (Fs[t][c] - Fs[t + 1][c]);
+      uout[c * N + i] = un[c];
+    }
+    bool ok;
+    const double sp = Phys<FLUX>::speed(un, a.adv, a.gamma, ok);
+    bad |= !ok;
+    smax = fmax(smax, sp);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0) s_red[warp] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = s_red[0];
+    for (int w = 1; w < NT / 32; w++) v = fmax(v, s_red[w]);
+    atomic_max_pos(&a.smax[(a.slot + 1) % 3], v);
+  }
+}
+
+// Wave speed of a state into smax[slot]; block 0 also sets tslot[slot] = 0.
+template <int FLUX>
+__global__ void __launch_bounds__(NT) k_smax1d_f64(const Step1DArgs a) {
+  constexpr int S = Phys<FLUX>::S;
+  __shared__ double s_red[NT / 32];
+  const double *uin = static_cast<const double *>(a.u_in);
+  double smax = 0.0;
+  bool bad = false;
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < a.N; i += (long)gridDim.x * NT) {
+    double u[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) u[c] = uin[c * (long)a.N + i];
+    bool ok;
+    smax = fmax(smax, Phys<FLUX>::speed(u, a.adv, a.gamma, ok));
+    bad |= !ok;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0) s_red[warp] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = s_red[0];
+    for (int w = 1; w < NT / 32; w++) v = fmax(v, s_red[w]);
+    atomic_max_pos(&a.smax[a.slot], v);
+    if (blockIdx.x == 0 && a.tslot) a.tslot[a.slot] = 0.0;
+  }
+}
+
+template <int P, int FLUX>
+int launch_p_f(const Step1DArgs &a, cudaStream_t st) {
+  using TL = Tiling<P>;
+  const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
+  k_step1d_f64<P, FLUX><<<grid, NT, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <int FLUX>
+int launch_f(int P, const Step1DArgs &a, cudaStream_t st) {
+  switch (P) {
+  case 1: return launch_p_f<1, FLUX>(a, st);
+  case 2: return launch_p_f<2, FLUX>(a, st);
+  case 3: return launch_p_f<3, FLUX>(a, st);
+  case 4: return launch_p_f<4, FLUX>(a, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int acat_cells_per_cta_1d(int P, int /*prec*/) {
+  switch (P) {
+  case 1: return Tiling<1>::T;
+  case 2: return Tiling<2>::T;
+  case 3: return Tiling<3>::T;
+  case 4: return Tiling<4>::T;
+  }
+  return 0;
+}
+
+int acat_launch_step1d(int P, int flux, int prec, const Step1DArgs &a, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec != ACAT_PREC_F64) return (int)cudaErrorInvalidValue;
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: return launch_f<ACAT_FLUX_LINEAR>(P, a, st);
+  case ACAT_FLUX_BURGERS: return launch_f<ACAT_FLUX_BURGERS>(P, a, st);
+  case ACAT_FLUX_EULER1D: return launch_f<ACAT_FLUX_EULER1D>(P, a, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec != ACAT_PREC_F64) return (int)cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((a.N + NT - 1) / NT) < 1024u ? (unsigned)((a.N + NT - 1) / NT) : 1024u;
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: k_smax1d_f64<ACAT_FLUX_LINEAR><<<grid, NT, 0, st>>>(a); break;
+  case ACAT_FLUX_BURGERS: k_smax1d_f64<ACAT_FLUX_BURGERS><<<grid, NT, 0, st>>>(a); break;
+  case ACAT_FLUX_EULER1D: k_smax1d_f64<ACAT_FLUX_EULER1D><<<grid, NT, 0, st>>>(a); break;
+  default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int acat_upload_tables_current_device() {
+  AcatTables T;
+  acat_build_tables(&T);
+  return (int)cudaMemcpyToSymbol(c_tab, &T, sizeof T);
+}

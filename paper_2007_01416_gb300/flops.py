@@ -1,0 +1,62 @@
+"""Algorithmic operation counts of the ACAT step, as the CUDA kernels
+formulate it (roofline numerators).
+
+Counting convention: an FMA is 2 flops; add, multiply, divide and square root
+are 1 each. Counts are per interface for the flux work and per cell for the
+update, so a launch's work follows from the histogram of selected orders.
+
+CAT2p flux of one interface (n = 2p nodes, S components, PHI flops per flux
+evaluation), in the dt-scaled recursion with running Taylor sums:
+  f(u_j) at the n nodes                                   n PHI
+  for each of the n-1 orders k = 2..2p:
+    U^(k-1)_j = -lambda sum_r g1[j][r] F_r               2 n^2 S + n S
+    acc_j = g[k-1][0] f(u_j)                              n S
+    at the n-1 levels r != 0: Taylor update, f, acc      n (n-1) (2S + PHI + 2S)
+    F_sum += acc / k!                                     2 n S
+  sum_j gamma^{0,1/2}_j F_sum_j                           2 n S
+"""
+from __future__ import annotations
+
+# flops of one flux evaluation f(u)
+PHI = {0: 1, 1: 2, 2: 10, 3: 19}  # linear, Burgers, Euler 1D (1 divide), Euler 2D f+g pair
+NVARS = {0: 1, 1: 1, 2: 3, 3: 4}
+
+
+def cat_flux_flops(p: int, flux: int) -> int:
+    n, S, phi = 2 * p, NVARS[flux], PHI[flux]
+    per_k = 2 * n * n * S + n * S + n * S + n * (n - 1) * (4 * S + phi) + 2 * n * S
+    return n * phi + (n - 1) * per_k + 2 * n * S
+
+
+def indicator_flops(P: int, flux: int) -> int:
+    S = NVARS[flux]
+    tot = 0
+    for p in range(2, P + 1):
+        tot += S * (6 * (p - 1) + 2 + 3 + 4 * p + 2 + 2)
+    return tot
+
+
+def flcat2_flops(flux: int) -> int:
+    S, phi = NVARS[flux], PHI[flux]
+    return 4 * phi + 28 * S + 16
+
+
+def update_flops(flux: int) -> int:
+    return 3 * NVARS[flux] + 8
+
+
+def step_flops_1d(order_hist: dict, P: int, flux: int, cells: int) -> float:
+    """Flops of one 1D step: order_hist maps order code (1 = FL-CAT2) to the
+    number of interfaces that selected it."""
+    f = 0.0
+    for code, cnt in order_hist.items():
+        f += cnt * (flcat2_flops(flux) if code == 1 else cat_flux_flops(code, flux))
+    nif = sum(order_hist.values())
+    f += nif * indicator_flops(P, flux) + cells * update_flops(flux)
+    return f
+
+
+def state_bytes_1d(cells: int, flux: int, prec: int = 0) -> int:
+    """Compulsory HBM traffic of one step: read and write the state once
+    (FP64, or the FP32 hi/lo pair: 8 bytes per value either way)."""
+    return 2 * cells * NVARS[flux] * 8

@@ -139,6 +139,33 @@ int acat_run(acat_ctx *ctx, void *u_dev, int nsteps, double t_end, void *stream,
 int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int nsteps, double t_end,
                   void *stream, double *t_host);
 
+/* Largest state, in bytes, that acat_run_noalloc accepts: 8 MiB, i.e.
+ * 349525 cells of 1D Euler or 1048576 cells of a scalar law in FP64. */
+#define ACAT_NOALLOC_MAX_STATE (8u << 20)
+
+/* acat_run without a context and without any device allocation. The paper
+ * has no counterpart: this entry point exists for callers that must not call
+ * cudaMalloc, such as a host application that owns all device memory through
+ * its own pool and forbids other allocations, a plugin loaded into one, or
+ * code whose latency budget cannot absorb an allocation.
+ *   p           the problem, as for acat_create (1D, FP64 only).
+ *   u_dev       the state, advanced nsteps steps in place; its size
+ *               (s * nx * 8 bytes) must not exceed ACAT_NOALLOC_MAX_STATE,
+ *               else ACAT_ERR_TOO_LARGE is returned before any device work.
+ *   t_end, t_dev  as for acat_run.
+ *   status_dev  (nullable, device) receives the status bits of the run.
+ * Scratch (dt and time slots, status word, the ping-pong work buffer) lives
+ * in one static device array of 256 B + ACAT_NOALLOC_MAX_STATE inside the
+ * library, held by every GPU that loads the library until the process exits.
+ * The first call on a device uploads the weight tables and resolves the
+ * array's device address; make that call before any stream capture. All calls
+ * share the array, and it keeps the last call's contents (its slots are
+ * cleared at the start of each call). Calls that overlap on the GPU race on
+ * it, so issue them on one stream. Steps are launched one by one (no graph).
+ * Errors: as acat_create and acat_run, plus ACAT_ERR_TOO_LARGE. */
+int acat_run_noalloc(const acat_params *p, void *u_dev, int nsteps, double t_end, void *stream,
+                     double *t_dev, unsigned *status_dev);
+
 /* Reads and returns the sticky device status bits (synchronises ctx's
  * work). Returns ACAT_ERR_NONPHYSICAL when any bit is set. */
 int acat_status(acat_ctx *ctx, unsigned *flags_out);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libacat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["step1d.cu", "api.cu", "peak.cu", "weights.cpp"]
+SOURCES = ["step1d.cu", "api.cu", "peak.cu", "weights.cpp", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "acat_internal.h"), os.path.join(ROOT, "include", "acat.h")]
 
 

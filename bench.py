@@ -192,7 +192,8 @@ def order_hist(ctx, torch, u0, steps, nx, probes=5):
 def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_clocks, dev_index):
     c = W.euler1d_riemann_entropy(nx=nx, seed=SEED, P=P, steps=acat_steps, cfl=CFL)
     ctx = acat.Context(**c.problem_kwargs(), precision=prec)
-    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    host = acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()
+    u0 = torch.from_numpy(host).cuda()
     u = torch.empty_like(u0)
     stream = torch.cuda.current_stream()
 
@@ -291,6 +292,29 @@ def run_ours(args):
             "value": cells_steps / (vms * 1e-3), "unit": UNIT, "ms_per_step": vms,
             "roofline_frac": v["flops_per_step"] / (vms / args.acat_steps * 1e-3) / peak64,
             "order_mix": v["order_mix"]}
+        for P in (4, 2):
+            v = measure(torch, acat, W, flops, NX, P, acat.PREC_F32, args.acat_steps, 3, 1, flush,
+                        False, dev_index)
+            vms = sum(v["ms"]) / 3
+            # accuracy of the FP32 run against the FP64 run of the same workload
+            # (the FP64 path matches the oracle within 1e-12 per step)
+            u32 = v["u0"].clone()
+            v["ctx"].acat_run(u32, args.acat_steps)
+            c64 = acat.Context(**v["case"].problem_kwargs())
+            u64 = torch.from_numpy(v["case"].u0.copy()).cuda()
+            c64.acat_run(u64, args.acat_steps)
+            torch.cuda.synchronize()
+            x32 = acat.from_pair(u32)
+            diff = (x32 - u64).abs()
+            variants[f"P{P}_f32"] = {
+                "value": cells_steps / (vms * 1e-3), "unit": UNIT, "ms_per_step": vms,
+                "roofline_frac_fp32": v["flops_per_step"] / (vms / args.acat_steps * 1e-3) / peak32,
+                "speedup_vs_f64": (ms_per_step if P == P_MAIN else variants["P2_f64"]["ms_per_step"])
+                / vms,
+                "l1_rel_vs_f64": float(diff.mean() / u64.abs().mean()),
+                "linf_rel_vs_f64": float(diff.max() / u64.abs().max()),
+                "order_mix": v["order_mix"]}
+            c64.close()
 
     if rank != 0:
         return 0

@@ -112,6 +112,36 @@ def _stream(stream) -> int | None:
     return int(stream.cuda_stream)
 
 
+def to_pair(u):
+    """FP64 state -> compensated FP32 layout [hi; lo] (shape [2, ...]):
+    hi = fl32(u), lo = fl32(u - hi). Works on numpy arrays and torch tensors."""
+    try:
+        import torch
+        if isinstance(u, torch.Tensor):
+            hi = u.to(torch.float32)
+            lo = (u - hi.to(torch.float64)).to(torch.float32)
+            return torch.stack([hi, lo]).contiguous()
+    except ImportError:
+        pass
+    import numpy as np
+    u = np.asarray(u, dtype=np.float64)
+    hi = u.astype(np.float32)
+    lo = (u - hi.astype(np.float64)).astype(np.float32)
+    return np.ascontiguousarray(np.stack([hi, lo]))
+
+
+def from_pair(pair):
+    """Compensated FP32 layout [hi; lo] -> the FP64 value hi + lo (exact)."""
+    try:
+        import torch
+        if isinstance(pair, torch.Tensor):
+            return pair[0].to(torch.float64) + pair[1].to(torch.float64)
+    except ImportError:
+        pass
+    import numpy as np
+    return pair[0].astype(np.float64) + pair[1].astype(np.float64)
+
+
 def acat_measure_fma_peak(precision: int, stream=None) -> float:
     return float(lib().acat_measure_fma_peak(int(precision), _stream(stream)))
 

@@ -18,6 +18,12 @@ struct AcatTables {
   double taylor[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];  // r^l / l!            [p][r][l]
   double fact[ACAT_MAXP + 1];                          // (2p-1)!
   double invfact[ACAT_MAXN + 1];                       // 1 / k!
+  // the same weights rounded to float, for the FP32 recursion
+  float g1f[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];
+  float gkf[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];
+  float ghf[ACAT_MAXP + 1][ACAT_MAXN];
+  float taylorf[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];
+  float invfactf[ACAT_MAXN + 1];
 };
 
 void acat_build_tables(AcatTables *T);

@@ -64,7 +64,6 @@ int check_params(const acat_params *p) {
   const bool is2d = p->ny > 1 || p->flux == ACAT_FLUX_EULER2D;
   if (is2d) return ACAT_ERR_UNSUPPORTED;
   if (p->flux == ACAT_FLUX_EULER2D) return ACAT_ERR_INVALID_ARG;
-  if (p->precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;
   if ((long)p->nx > (1l << 30)) return ACAT_ERR_TOO_LARGE;
   return ACAT_OK;
 }

@@ -1,4 +1,5 @@
-// step1d.cu -- the 1D ACAT step on sm_103a CUDA cores.
+// step1d.cu -- the 1D ACAT step on sm_103a CUDA cores (FP64, and FP32 on a
+// compensated state).
 //
 // One CTA owns T consecutive cells and computes the T+1 interface fluxes
 // around them (the last one is recomputed by the next CTA). The cells
@@ -8,8 +9,8 @@
 //   - lanes 0..P-2 of the group evaluate the indicators psi^{l+2}
 //     (Eqs. 3.8-3.12, minimum over components, Sec. 3.4) with explicitly
 //     rounded FP64 operations in the order of their definition, so that the
-//     order decision is bit-identical to a literal FP64 evaluation; a warp
-//     ballot then gives p_s = max A (Eqs. 3.2-3.3);
+//     order decision is bit-identical to a literal FP64 evaluation of the same
+//     state; a warp ballot then gives p_s = max A (Eqs. 3.2-3.3);
 //   - for p_s >= 2 every lane runs the local Taylor recursion of Sec. 2.2 for
 //     its node in registers, in the dt-scaled form
 //         U^(k-1)_j = -lambda sum_r gamma^{1,j}_r F^(k-2)_r     (shuffles)
@@ -22,6 +23,12 @@
 // The conservative update (Eq. 2.12) follows from shared memory, and its
 // epilogue reduces the wave speed of the new state for the next step's CFL
 // dt into a triple-buffered slot (atomic max on ordered double bits).
+//
+// FP32 variant: the state is a compensated float pair (hi, lo). The
+// indicators, the limiter and the wave speed see the exact value hi + lo in
+// FP64; the recursion runs in float on hi; the update adds the float flux
+// difference to the pair with an error-free transformation (Knuth's TwoSum,
+// then Dekker's Fast2Sum), so rounding the state never accumulates.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,6 +41,41 @@ __constant__ AcatTables c_tab;
 namespace {
 
 constexpr int NT = 256;  // threads per CTA
+
+// ---------------------------------------------------------------------------
+// Arithmetic helpers
+// ---------------------------------------------------------------------------
+// 1/x for x > 0: the hardware approximation rcp.approx.ftz.f64 (about 23
+// correct bits) refined by two Newton-Raphson steps y <- y + y (1 - x y), each
+// doubling the number of correct bits (error within an ulp of 1/x).
+__device__ __forceinline__ double recip(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
+template <typename R>
+struct Tab;
+template <>
+struct Tab<double> {
+  __device__ static double g1(int p, int j, int r) { return c_tab.g1[p][j][r]; }
+  __device__ static double gk(int p, int k, int r) { return c_tab.gk[p][k][r]; }
+  __device__ static double gh(int p, int j) { return c_tab.gh[p][j]; }
+  __device__ static double taylor(int p, int r, int l) { return c_tab.taylor[p][r][l]; }
+  __device__ static double invfact(int k) { return c_tab.invfact[k]; }
+};
+template <>
+struct Tab<float> {
+  __device__ static float g1(int p, int j, int r) { return c_tab.g1f[p][j][r]; }
+  __device__ static float gk(int p, int k, int r) { return c_tab.gkf[p][k][r]; }
+  __device__ static float gh(int p, int j) { return c_tab.ghf[p][j]; }
+  __device__ static float taylor(int p, int r, int l) { return c_tab.taylorf[p][r][l]; }
+  __device__ static float invfact(int k) { return c_tab.invfactf[k]; }
+};
 
 // ---------------------------------------------------------------------------
 // Physics
@@ -68,7 +110,7 @@ struct Phys<ACAT_FLUX_EULER1D> {
   static constexpr int S = 3;
   template <typename R>
   __device__ static __forceinline__ void flux(const R *u, R *f, R, R gm1) {
-    const R ri = R(1) / u[0];
+    const R ri = recip(u[0]);
     const R v = u[1] * ri;
     const R p = gm1 * (u[2] - R(0.5) * u[1] * v);
     f[0] = u[1];
@@ -95,7 +137,7 @@ __device__ __forceinline__ long bc_index(long g, long N, int bc) {
 }
 
 // ---------------------------------------------------------------------------
-// Indicators and limiter: explicit round-to-nearest operations, no FMA
+// Indicators and limiter: explicit round-to-nearest FP64 operations, no FMA
 // contraction, in the order of Eqs. 3.6-3.12.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double psi_p_comp(const double *q, int p, double eps, double fact) {
@@ -175,21 +217,22 @@ __device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form
 // ---------------------------------------------------------------------------
 // CAT2p flux of one interface by a group of 2p lanes (lane l <-> node
 // j = l - p + 1). q points at cell i (left of the interface) for component 0
-// in the shared tile, components `cs` apart. Lane 0 returns the flux.
+// of the shared tile, components `cs` apart. Every lane returns the flux.
 // ---------------------------------------------------------------------------
-template <int p, int FLUX>
-__device__ __forceinline__ void cat_flux(const double *q, int cs, int l, int base, double lam,
-                                         double adv, double gm1, double *Fout) {
+template <int p, int FLUX, typename R>
+__device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R lam, R adv, R gm1,
+                                         R *Fout) {
+  using TB = Tab<R>;
   constexpr int S = Phys<FLUX>::S;
   constexpr int n = 2 * p;
-  const unsigned mask = ((n == 32) ? 0xffffffffu : ((1u << n) - 1u)) << base;
+  const unsigned mask = ((1u << n) - 1u) << base;
   const int j = l - p + 1;
-  double g1r[n];
+  R g1r[n];
 #pragma unroll
-  for (int r = 0; r < n; r++) g1r[r] = c_tab.g1[p][l][r];
-  double f0[S], Fsum[S], Fprev[S], arg[n][S];
+  for (int r = 0; r < n; r++) g1r[r] = TB::g1(p, l, r);
+  R f0[S], Fsum[S], Fprev[S], arg[n][S];
   {
-    double u[S];
+    R u[S];
 #pragma unroll
     for (int c = 0; c < S; c++) u[c] = q[c * cs + j];
     Phys<FLUX>::flux(u, f0, adv, gm1);
@@ -205,41 +248,41 @@ __device__ __forceinline__ void cat_flux(const double *q, int cs, int l, int bas
   }
 #pragma unroll
   for (int k = 2; k <= n; k++) {
-    double U[S];
+    R U[S];
 #pragma unroll
-    for (int c = 0; c < S; c++) U[c] = 0.0;
+    for (int c = 0; c < S; c++) U[c] = R(0);
 #pragma unroll
     for (int r = 0; r < n; r++)
 #pragma unroll
       for (int c = 0; c < S; c++) U[c] = fma(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
-    double acc[S];
+    R acc[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
       U[c] *= -lam;
-      acc[c] = c_tab.gk[p][k - 1][p - 1] * f0[c];
+      acc[c] = TB::gk(p, k - 1, p - 1) * f0[c];
     }
 #pragma unroll
     for (int rr = 0; rr < n; rr++) {
       if (rr == p - 1) continue;  // r = 0: f(u_j) itself
-      const double cr = c_tab.taylor[p][rr][k - 1];
-      double fr[S];
+      const R cr = TB::taylor(p, rr, k - 1);
+      R fr[S];
 #pragma unroll
       for (int c = 0; c < S; c++) arg[rr][c] = fma(cr, U[c], arg[rr][c]);
       Phys<FLUX>::flux(arg[rr], fr, adv, gm1);
 #pragma unroll
-      for (int c = 0; c < S; c++) acc[c] = fma(c_tab.gk[p][k - 1][rr], fr[c], acc[c]);
+      for (int c = 0; c < S; c++) acc[c] = fma(TB::gk(p, k - 1, rr), fr[c], acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < S; c++) {
       Fprev[c] = acc[c];
-      Fsum[c] = fma(c_tab.invfact[k], acc[c], Fsum[c]);
+      Fsum[c] = fma(TB::invfact(k), acc[c], Fsum[c]);
     }
   }
-  const double w = c_tab.gh[p][l];
+  const R w = TB::gh(p, l);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const double v = w * Fsum[c];
-    double t = 0.0;
+    const R v = w * Fsum[c];
+    R t = R(0);
 #pragma unroll
     for (int r = 0; r < n; r++) t += __shfl_sync(mask, v, base + r);
     Fout[c] = t;
@@ -247,43 +290,49 @@ __device__ __forceinline__ void cat_flux(const double *q, int cs, int l, int bas
 }
 
 // FL-CAT2 flux (Eq. 3.4): the CAT2 flux (p = 1 recursion, Eqs. 2.16-2.17)
-// blended with Rusanov by the limiter psi^1. Single lane.
-template <int FLUX>
-__device__ __forceinline__ void flcat2_flux(const double *q, int cs, double lam, double adv,
-                                            double gamma, int limiter_form, double *F) {
+// blended with Rusanov by the limiter psi^1 (taken in FP64 on q64). Single
+// lane; qR is the recursion operand (equal to q64 in FP64).
+template <int FLUX, typename R>
+__device__ __forceinline__ void flcat2_flux(const R *qR, const double *q64, int cs, R lam, R adv,
+                                            double advd, double gamma, int limiter_form, R *F) {
   constexpr int S = Phys<FLUX>::S;
-  const double gm1 = gamma - 1.0;
-  double u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
+  const R gm1 = R(gamma - 1.0);
+  R u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    u0[c] = q[c * cs];
-    u1[c] = q[c * cs + 1];
+    u0[c] = qR[c * cs];
+    u1[c] = qR[c * cs + 1];
   }
   Phys<FLUX>::flux(u0, f0, adv, gm1);
   Phys<FLUX>::flux(u1, f1, adv, gm1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const double U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
+    const R U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
     a0[c] = u0[c] + U;
     a1[c] = u1[c] + U;
   }
   Phys<FLUX>::flux(a0, t0, adv, gm1);
   Phys<FLUX>::flux(a1, t1, adv, gm1);
-  bool ok;
-  const double s0 = Phys<FLUX>::speed(u0, adv, gamma, ok), s1 = Phys<FLUX>::speed(u1, adv, gamma, ok);
-  const double alpha = s1 > s0 ? s1 : s0;
-  const double w = psi1<FLUX>(q, cs, limiter_form, adv);
+  double d0[S], d1[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const double F1 = 0.5 * (f0[c] + f1[c]) + 0.25 * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
-    const double Flo = 0.5 * (f0[c] + f1[c]) - 0.5 * alpha * (u1[c] - u0[c]);
-    F[c] = w * F1 + (1.0 - w) * Flo;
+    d0[c] = q64[c * cs];
+    d1[c] = q64[c * cs + 1];
+  }
+  bool ok;
+  const double s0 = Phys<FLUX>::speed(d0, advd, gamma, ok), s1 = Phys<FLUX>::speed(d1, advd, gamma, ok);
+  const R alpha = R(s1 > s0 ? s1 : s0);
+  const R w = R(psi1<FLUX>(q64, cs, limiter_form, advd));
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const R F1 = R(0.5) * (f0[c] + f1[c]) + R(0.25) * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
+    const R Flo = R(0.5) * (f0[c] + f1[c]) - R(0.5) * alpha * (u1[c] - u0[c]);
+    F[c] = w * F1 + (R(1) - w) * Flo;
   }
 }
 
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
-  // non-negative doubles (and +inf, NaN with sign bit clear) order like
-  // their bit patterns
+  // non-negative doubles (and +inf) order like their bit patterns
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
@@ -328,28 +377,45 @@ struct Tiling {
   static constexpr int TW = T + 2 * GH;       // staged cells
 };
 
-template <int P, int FLUX>
-__global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
+template <bool F32>
+struct Prec {
+  using R = double;
+};
+template <>
+struct Prec<true> {
+  using R = float;
+};
+
+template <int P, int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_step1d(const Step1DArgs a) {
   using TL = Tiling<P>;
+  using R = typename Prec<F32>::R;
   constexpr int S = Phys<FLUX>::S;
-  __shared__ double tile[S][TL::TW];
-  __shared__ double Fs[TL::NI][S];
+  __shared__ double tile[S][TL::TW];                          // FP64 value of the state
+  __shared__ R tileR[F32 ? S : 1][F32 ? TL::TW : 1];          // float operand (FP32)
+  __shared__ R Fs[TL::NI][S];
   __shared__ double s_dt;
   __shared__ double s_red[NT / 32];
-  const double *__restrict__ uin = static_cast<const double *>(a.u_in);
-  double *__restrict__ uout = static_cast<double *>(a.u_out);
   const long N = a.N;
   const long i0 = (long)blockIdx.x * TL::T;
 
   if (threadIdx.x == 0) s_dt = step_dt(a);
   for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
     const int c = q / TL::TW, k = q - c * TL::TW;
-    tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
+    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
+    if constexpr (F32) {
+      const float *uin = static_cast<const float *>(a.u_in);
+      const float hi = uin[c * N + g], lo = uin[(S + c) * N + g];
+      tile[c][k] = (double)hi + (double)lo;
+      tileR[c][k] = hi;
+    } else {
+      tile[c][k] = static_cast<const double *>(a.u_in)[c * N + g];
+    }
   }
   __syncthreads();
   const double dt = s_dt;
-  const double lam = dt / a.dx;
-  const double gm1 = a.gamma - 1.0;
+  const double lamd = dt / a.dx;
+  const R lam = R(lamd), adv = R(a.adv), gm1 = R(a.gamma - 1.0);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / TL::L, l = lane - grp * TL::L;
@@ -379,18 +445,20 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
   }
 
   // --- flux ------------------------------------------------------------------
-  double F[S];
+  R F[S];
   const int base = grp * TL::L;
-  const double *q0 = &tile[0][ic];
+  const R *qR;
+  if constexpr (F32) qR = &tileR[0][ic];
+  else qR = &tile[0][ic];
   if (active) {
     if (ps == 4) {
-      if constexpr (P >= 4) cat_flux<4, FLUX>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+      if constexpr (P >= 4) cat_flux<4, FLUX, R>(qR, TL::TW, l, base, lam, adv, gm1, F);
     } else if (ps == 3) {
-      if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+      if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX, R>(qR, TL::TW, l, base, lam, adv, gm1, F);
     } else if (ps == 2) {
-      if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+      if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, R>(qR, TL::TW, l, base, lam, adv, gm1, F);
     } else if (l == 0) {
-      flcat2_flux<FLUX>(q0, TL::TW, lam, a.adv, a.gamma, a.limiter_form, F);
+      flcat2_flux<FLUX, R>(qR, &tile[0][ic], TL::TW, lam, adv, a.adv, a.gamma, a.limiter_form, F);
     }
     if (l == 0) {
 #pragma unroll
@@ -407,10 +475,32 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
     const long i = i0 + t;
     if (i >= N) break;
     double un[S];
+    if constexpr (F32) {
+      const float *uin = static_cast<const float *>(a.u_in);
+      float *uout = static_cast<float *>(a.u_out);
 #pragma unroll
-    for (int c = 0; c < S; c++) {
-      un[c] = tile[c][t + TL::GH] + lam * (Fs[t][c] - Fs[t + 1][c]);
-      uout[c * N + i] = un[c];
+      for (int c = 0; c < S; c++) {
+        const float hi = tileR[c][t + TL::GH], lo = uin[(S + c) * N + i];
+        const float d = __fmul_rn(lam, __fsub_rn(Fs[t][c], Fs[t + 1][c]));
+        // TwoSum(hi, d): s + e = hi + d exactly
+        const float s = __fadd_rn(hi, d);
+        const float bp = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+        const float lo2 = __fadd_rn(lo, e);
+        // Fast2Sum(s, lo2), |s| >= |lo2|: renormalised pair
+        const float hn = __fadd_rn(s, lo2);
+        const float ln = __fsub_rn(lo2, __fsub_rn(hn, s));
+        uout[c * N + i] = hn;
+        uout[(S + c) * N + i] = ln;
+        un[c] = (double)hn + (double)ln;
+      }
+    } else {
+      double *uout = static_cast<double *>(a.u_out);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        un[c] = tile[c][t + TL::GH] + lamd * (Fs[t][c] - Fs[t + 1][c]);
+        uout[c * N + i] = un[c];
+      }
     }
     bool ok;
     const double sp = Phys<FLUX>::speed(un, a.adv, a.gamma, ok);
@@ -430,17 +520,23 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
 }
 
 // Wave speed of a state into smax[slot]; block 0 also sets tslot[slot] = 0.
-template <int FLUX>
-__global__ void __launch_bounds__(NT) k_smax1d_f64(const Step1DArgs a) {
+template <int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_smax1d(const Step1DArgs a) {
   constexpr int S = Phys<FLUX>::S;
   __shared__ double s_red[NT / 32];
-  const double *uin = static_cast<const double *>(a.u_in);
   double smax = 0.0;
   bool bad = false;
   for (long i = (long)blockIdx.x * NT + threadIdx.x; i < a.N; i += (long)gridDim.x * NT) {
     double u[S];
 #pragma unroll
-    for (int c = 0; c < S; c++) u[c] = uin[c * (long)a.N + i];
+    for (int c = 0; c < S; c++) {
+      if constexpr (F32) {
+        const float *uin = static_cast<const float *>(a.u_in);
+        u[c] = (double)uin[c * (long)a.N + i] + (double)uin[(S + c) * (long)a.N + i];
+      } else {
+        u[c] = static_cast<const double *>(a.u_in)[c * (long)a.N + i];
+      }
+    }
     bool ok;
     smax = fmax(smax, Phys<FLUX>::speed(u, a.adv, a.gamma, ok));
     bad |= !ok;
@@ -459,23 +555,46 @@ __global__ void __launch_bounds__(NT) k_smax1d_f64(const Step1DArgs a) {
   }
 }
 
-template <int P, int FLUX>
-int launch_p_f(const Step1DArgs &a, cudaStream_t st) {
+template <int P, int FLUX, bool F32>
+int launch_p(const Step1DArgs &a, cudaStream_t st) {
   using TL = Tiling<P>;
   const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
-  k_step1d_f64<P, FLUX><<<grid, NT, 0, st>>>(a);
+  k_step1d<P, FLUX, F32><<<grid, NT, 0, st>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <int FLUX>
+template <int FLUX, bool F32>
 int launch_f(int P, const Step1DArgs &a, cudaStream_t st) {
   switch (P) {
-  case 1: return launch_p_f<1, FLUX>(a, st);
-  case 2: return launch_p_f<2, FLUX>(a, st);
-  case 3: return launch_p_f<3, FLUX>(a, st);
-  case 4: return launch_p_f<4, FLUX>(a, st);
+  case 1: return launch_p<1, FLUX, F32>(a, st);
+  case 2: return launch_p<2, FLUX, F32>(a, st);
+  case 3: return launch_p<3, FLUX, F32>(a, st);
+  case 4: return launch_p<4, FLUX, F32>(a, st);
   }
   return (int)cudaErrorInvalidValue;
+}
+
+template <bool F32>
+int launch_prec(int P, int flux, const Step1DArgs &a, cudaStream_t st) {
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: return launch_f<ACAT_FLUX_LINEAR, F32>(P, a, st);
+  case ACAT_FLUX_BURGERS: return launch_f<ACAT_FLUX_BURGERS, F32>(P, a, st);
+  case ACAT_FLUX_EULER1D: return launch_f<ACAT_FLUX_EULER1D, F32>(P, a, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <bool F32>
+int launch_smax(int flux, const Step1DArgs &a, cudaStream_t st) {
+  const long blocks = (a.N + NT - 1) / NT;
+  const unsigned grid = (unsigned)(blocks < 1024 ? blocks : 1024);
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: k_smax1d<ACAT_FLUX_LINEAR, F32><<<grid, NT, 0, st>>>(a); break;
+  case ACAT_FLUX_BURGERS: k_smax1d<ACAT_FLUX_BURGERS, F32><<<grid, NT, 0, st>>>(a); break;
+  case ACAT_FLUX_EULER1D: k_smax1d<ACAT_FLUX_EULER1D, F32><<<grid, NT, 0, st>>>(a); break;
+  default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
 }
 
 }  // namespace
@@ -492,26 +611,16 @@ int acat_cells_per_cta_1d(int P, int /*prec*/) {
 
 int acat_launch_step1d(int P, int flux, int prec, const Step1DArgs &a, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (prec != ACAT_PREC_F64) return (int)cudaErrorInvalidValue;
-  switch (flux) {
-  case ACAT_FLUX_LINEAR: return launch_f<ACAT_FLUX_LINEAR>(P, a, st);
-  case ACAT_FLUX_BURGERS: return launch_f<ACAT_FLUX_BURGERS>(P, a, st);
-  case ACAT_FLUX_EULER1D: return launch_f<ACAT_FLUX_EULER1D>(P, a, st);
-  }
+  if (prec == ACAT_PREC_F64) return launch_prec<false>(P, flux, a, st);
+  if (prec == ACAT_PREC_F32) return launch_prec<true>(P, flux, a, st);
   return (int)cudaErrorInvalidValue;
 }
 
 int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (prec != ACAT_PREC_F64) return (int)cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)((a.N + NT - 1) / NT) < 1024u ? (unsigned)((a.N + NT - 1) / NT) : 1024u;
-  switch (flux) {
-  case ACAT_FLUX_LINEAR: k_smax1d_f64<ACAT_FLUX_LINEAR><<<grid, NT, 0, st>>>(a); break;
-  case ACAT_FLUX_BURGERS: k_smax1d_f64<ACAT_FLUX_BURGERS><<<grid, NT, 0, st>>>(a); break;
-  case ACAT_FLUX_EULER1D: k_smax1d_f64<ACAT_FLUX_EULER1D><<<grid, NT, 0, st>>>(a); break;
-  default: return (int)cudaErrorInvalidValue;
-  }
-  return (int)cudaGetLastError();
+  if (prec == ACAT_PREC_F64) return launch_smax<false>(flux, a, st);
+  if (prec == ACAT_PREC_F32) return launch_smax<true>(flux, a, st);
+  return (int)cudaErrorInvalidValue;
 }
 
 int acat_upload_tables_current_device() {

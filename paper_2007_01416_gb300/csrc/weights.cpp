@@ -136,4 +136,15 @@ void acat_build_tables(AcatTables *T) {
     f *= k;
     T->invfact[k] = 1.0 / (double)f;
   }
+  for (int p = 0; p <= ACAT_MAXP; p++) {
+    for (int a = 0; a < ACAT_MAXN; a++) {
+      T->ghf[p][a] = (float)T->gh[p][a];
+      for (int b = 0; b < ACAT_MAXN; b++) {
+        T->g1f[p][a][b] = (float)T->g1[p][a][b];
+        T->gkf[p][a][b] = (float)T->gk[p][a][b];
+        T->taylorf[p][a][b] = (float)T->taylor[p][a][b];
+      }
+    }
+  }
+  for (int k = 0; k <= ACAT_MAXN; k++) T->invfactf[k] = (float)T->invfact[k];
 }

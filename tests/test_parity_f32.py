@@ -1,0 +1,124 @@
+"""FP32 path (ACAT_PREC_F32): float recursion on a compensated (hi, lo) state,
+indicators and wave speed in FP64 on hi + lo.
+
+Bars (derived in the design doc from the arithmetic): the order codes of one step
+match the FP64 oracle bit for bit from the same state value hi + lo (the
+decisions are taken in FP64 on that exact value); one step agrees with the
+oracle within 2e-6 of max|u|; free runs report L1/Linf against the oracle
+and stay within 1e-5 (L1, relative) and 1e-3 (Linf, relative).
+"""
+import numpy as np
+import pytest
+
+from paper_2007_01416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+STEP_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_2007_01416_gb300 import acat, build
+    build.build()
+    O.build()
+    return torch, O, acat
+
+
+def _step32(env, ctx, pair, nx):
+    torch, O, acat = env
+    u = torch.from_numpy(np.ascontiguousarray(pair)).cuda()
+    out = torch.empty_like(u)
+    dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+    orders = torch.zeros(nx + 1, dtype=torch.int8, device="cuda")
+    ctx.acat_step(u, out, -1.0, None, dtv, orders)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), float(dtv.item()), orders.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,P,nx,bc", [("euler", 4, 16384, 1), ("euler", 3, 1001, 0),
+                                          ("euler", 2, 777, 1), ("burgers", 2, 400, 0),
+                                          ("burgers", 4, 513, 1), ("euler", 1, 64, 1)])
+def test_single_step_f32(env, kind, P, nx, bc):
+    torch, O, acat = env
+    c = W.burgers_sine(nx=nx, seed=2, P=P) if kind == "burgers" else \
+        W.euler1d_riemann_entropy(nx=nx, seed=2, P=P)
+    c.bc = bc
+    kw = c.problem_kwargs()
+    pair = acat.to_pair(c.u0)
+    x = acat.from_pair(pair)  # the exact value the GPU sees
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        out, dt, orders = _step32(env, ctx, pair, nx)
+        assert ctx.acat_status() == 0
+    pr = O.Problem(**kw)
+    assert dt == O.dt_cfl(pr, x)
+    ref, _, ord_ref = O.step_1d(pr, x, dt)
+    assert np.array_equal(orders, ord_ref)
+    err = np.abs(acat.from_pair(out) - ref).max() / max(1.0, np.abs(ref).max())
+    assert err < STEP_TOL, err
+
+
+def test_teacher_forced_f32(env):
+    torch, O, acat = env
+    c = W.euler1d_riemann_entropy(nx=2048, seed=4, P=4)
+    kw = c.problem_kwargs()
+    pr = O.Problem(**kw)
+    pair = acat.to_pair(c.u0)
+    worst = 0.0
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        for n in range(100):
+            x = acat.from_pair(pair)
+            out, dt, orders = _step32(env, ctx, pair, c.nx)
+            ref, _, ord_ref = O.step_1d(pr, x, dt)
+            assert np.array_equal(orders, ord_ref), n
+            worst = max(worst, np.abs(acat.from_pair(out) - ref).max() / np.abs(ref).max())
+            pair = out
+    assert worst < STEP_TOL, worst
+
+
+@pytest.mark.parametrize("P,nx,steps", [(4, 4096, 1000), (2, 4096, 1000)])
+def test_free_run_f32_against_oracle(env, P, nx, steps):
+    """Free-running FP32 and FP64 GPU runs of the 1D Euler workload shape
+    against the oracle run: L1 and Linf of the final state."""
+    torch, O, acat = env
+    c = W.euler1d_riemann_entropy(nx=nx, seed=0, P=P, steps=steps)
+    kw = c.problem_kwargs()
+    pr = O.Problem(**kw)
+    ref = c.u0.copy()
+    for _ in range(steps):
+        ref, _, _ = O.step_1d(pr, ref)
+    scale = np.abs(ref).max()
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
+        ctx.acat_run(u, steps)
+        torch.cuda.synchronize()
+        assert ctx.acat_status() == 0
+        got32 = acat.from_pair(u.cpu().numpy())
+    with acat.Context(**kw) as ctx:
+        u = torch.from_numpy(c.u0.copy()).cuda()
+        ctx.acat_run(u, steps)
+        torch.cuda.synchronize()
+        got64 = u.cpu().numpy()
+    l1_32 = np.abs(got32 - ref).mean() / np.abs(ref).mean()
+    li_32 = np.abs(got32 - ref).max() / scale
+    l1_64 = np.abs(got64 - ref).mean() / np.abs(ref).mean()
+    li_64 = np.abs(got64 - ref).max() / scale
+    print(f"P={P}: FP32 L1 {l1_32:.2e} Linf {li_32:.2e}; FP64 L1 {l1_64:.2e} Linf {li_64:.2e}")
+    assert l1_32 < 1e-5 and li_32 < 1e-3
+    assert li_64 < 1e-9
+
+
+def test_run_host_f32(env):
+    torch, O, acat = env
+    c = W.euler1d_riemann_entropy(nx=3000, seed=9, P=3)
+    with acat.Context(**c.problem_kwargs(), precision=acat.PREC_F32) as ctx:
+        pair = torch.from_numpy(acat.to_pair(c.u0))
+        u = pair.clone().cuda()
+        ctx.acat_run(u, 41)
+        out = torch.empty_like(pair).pin_memory()
+        ctx.acat_run_host(pair.pin_memory(), out, 41)
+        torch.cuda.synchronize()
+        assert torch.equal(out, u.cpu())

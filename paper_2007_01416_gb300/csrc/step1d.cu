@@ -26,9 +26,12 @@
 //
 // FP32 variant: the state is a compensated float pair (hi, lo). The
 // indicators, the limiter and the wave speed see the exact value hi + lo in
-// FP64; the recursion runs in float on hi; the update adds the float flux
-// difference to the pair with an error-free transformation (Knuth's TwoSum,
-// then Dekker's Fast2Sum), so rounding the state never accumulates.
+// FP64. The recursion runs in float in a delta formulation (see cat_delta):
+// every flux is carried as f(u_i) + G, G built from flux increments computed
+// in a cancellation-free form, so float rounding is relative to increments of
+// size O(dx) rather than to |f|. The update adds lambda (f(u_{i-1}) - f(u_i) +
+// G_{i-1/2} - G_{i+1/2}) to the pair with an error-free transformation
+// (Knuth's TwoSum, then Dekker's Fast2Sum).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -289,45 +292,237 @@ __device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R 
   }
 }
 
-// FL-CAT2 flux (Eq. 3.4): the CAT2 flux (p = 1 recursion, Eqs. 2.16-2.17)
-// blended with Rusanov by the limiter psi^1 (taken in FP64 on q64). Single
-// lane; qR is the recursion operand (equal to q64 in FP64).
-template <int FLUX, typename R>
-__device__ __forceinline__ void flcat2_flux(const R *qR, const double *q64, int cs, R lam, R adv,
-                                            double advd, double gamma, int limiter_form, R *F) {
+// FL-CAT2 flux (Eq. 3.4), FP64: the CAT2 flux (p = 1 recursion, Eqs.
+// 2.16-2.17) blended with Rusanov by the limiter psi^1. Single lane.
+template <int FLUX>
+__device__ __forceinline__ void flcat2_flux(const double *q, int cs, double lam, double adv,
+                                            double gamma, int limiter_form, double *F) {
   constexpr int S = Phys<FLUX>::S;
-  const R gm1 = R(gamma - 1.0);
-  R u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
+  const double gm1 = gamma - 1.0;
+  double u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    u0[c] = qR[c * cs];
-    u1[c] = qR[c * cs + 1];
+    u0[c] = q[c * cs];
+    u1[c] = q[c * cs + 1];
   }
   Phys<FLUX>::flux(u0, f0, adv, gm1);
   Phys<FLUX>::flux(u1, f1, adv, gm1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const R U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
+    const double U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
     a0[c] = u0[c] + U;
     a1[c] = u1[c] + U;
   }
   Phys<FLUX>::flux(a0, t0, adv, gm1);
   Phys<FLUX>::flux(a1, t1, adv, gm1);
-  double d0[S], d1[S];
-#pragma unroll
-  for (int c = 0; c < S; c++) {
-    d0[c] = q64[c * cs];
-    d1[c] = q64[c * cs + 1];
-  }
   bool ok;
-  const double s0 = Phys<FLUX>::speed(d0, advd, gamma, ok), s1 = Phys<FLUX>::speed(d1, advd, gamma, ok);
-  const R alpha = R(s1 > s0 ? s1 : s0);
-  const R w = R(psi1<FLUX>(q64, cs, limiter_form, advd));
+  const double s0 = Phys<FLUX>::speed(u0, adv, gamma, ok), s1 = Phys<FLUX>::speed(u1, adv, gamma, ok);
+  const double alpha = s1 > s0 ? s1 : s0;
+  const double w = psi1<FLUX>(q, cs, limiter_form, adv);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const R F1 = R(0.5) * (f0[c] + f1[c]) + R(0.25) * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
-    const R Flo = R(0.5) * (f0[c] + f1[c]) - R(0.5) * alpha * (u1[c] - u0[c]);
-    F[c] = w * F1 + (R(1) - w) * Flo;
+    const double F1 = 0.5 * (f0[c] + f1[c]) + 0.25 * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
+    const double Flo = 0.5 * (f0[c] + f1[c]) - 0.5 * alpha * (u1[c] - u0[c]);
+    F[c] = w * F1 + (1.0 - w) * Flo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 delta formulation. The flux at x_{i+1/2} is written F = f(u_i) + G and
+// every term of G is built from flux increments df(u; d) = f(u + d) - f(u)
+// evaluated in a cancellation-free algebraic form, so that float rounding is
+// relative to the (small) increments and not to |f|:
+//   - the time-derivative sums sum_r gamma^{k,0}_r f(arg_r), k >= 1, equal
+//     sum_{r != 0} gamma^{k,0}_r df(u_j; arg_r - u_j) since the weights of a
+//     derivative sum to zero;
+//   - the spatial derivative of f~^(0) equals that of df(u_i; u_j - u_i);
+//   - the k = 1 flux term sum_j gamma^{0,1/2}_j f(u_j) equals
+//     f(u_i) + sum_j gamma^{0,1/2}_j df(u_i; u_j - u_i) (weights sum to one).
+// The update u_i += lambda (F_{i-1/2} - F_{i+1/2}) then needs only
+// f(u_{i-1}) - f(u_i) = df(u_i; u_{i-1} - u_i) and the G's, all small. The
+// identities are used symbolically; nothing relies on rounded weights summing
+// to zero.
+// ---------------------------------------------------------------------------
+template <int FLUX>
+struct DPhys;
+
+template <>
+struct DPhys<ACAT_FLUX_LINEAR> {
+  static constexpr int S = 1;
+  struct Base {
+    float a;
+  };
+  __device__ static __forceinline__ Base base(const float *, float a, float) { return Base{a}; }
+  __device__ static __forceinline__ void dflux(const Base &b, const float *d, float *df) {
+    df[0] = b.a * d[0];
+  }
+  __device__ static __forceinline__ float speed(const float *, float a, float) { return fabsf(a); }
+};
+
+template <>
+struct DPhys<ACAT_FLUX_BURGERS> {
+  static constexpr int S = 1;
+  struct Base {
+    float u;
+  };
+  __device__ static __forceinline__ Base base(const float *u, float, float) { return Base{u[0]}; }
+  // (u + d)^2/2 - u^2/2 = d (u + d/2)
+  __device__ static __forceinline__ void dflux(const Base &b, const float *d, float *df) {
+    df[0] = d[0] * fmaf(0.5f, d[0], b.u);
+  }
+  __device__ static __forceinline__ float speed(const float *u, float, float) { return fabsf(u[0]); }
+};
+
+template <>
+struct DPhys<ACAT_FLUX_EULER1D> {
+  static constexpr int S = 3;
+  struct Base {
+    float rho, m, v, H, gm1;
+  };
+  __device__ static __forceinline__ Base base(const float *u, float, float gm1) {
+    Base b;
+    b.rho = u[0];
+    b.m = u[1];
+    b.v = u[1] * __frcp_rn(u[0]);
+    const float p = gm1 * fmaf(-0.5f * u[1], b.v, u[2]);
+    b.H = u[2] + p;
+    b.gm1 = gm1;
+    return b;
+  }
+  // With u = (rho, m, E), d = (a, b, c), v = m/rho, H = E + p:
+  //   dv = (b - v a) / (rho + a)          [v' - v]
+  //   d(mv) = m dv + b (v + dv)
+  //   dp = (gamma - 1)(c - d(mv)/2)
+  //   df = (b, d(mv) + dp, dv H + (v + dv)(c + dp))
+  __device__ static __forceinline__ void dflux(const Base &B, const float *d, float *df) {
+    const float dv = fmaf(-B.v, d[0], d[1]) * __frcp_rn(B.rho + d[0]);
+    const float vn = B.v + dv;
+    const float dmv = fmaf(B.m, dv, d[1] * vn);
+    const float dp = B.gm1 * fmaf(-0.5f, dmv, d[2]);
+    df[0] = d[1];
+    df[1] = dmv + dp;
+    df[2] = fmaf(dv, B.H, vn * (d[2] + dp));
+  }
+  __device__ static __forceinline__ float speed(const float *u, float, float gamma) {
+    const float v = u[1] / u[0];
+    const float p = (gamma - 1.0f) * (u[2] - 0.5f * u[1] * v);
+    return fabsf(v) + sqrtf(fmaxf(gamma * p / u[0], 0.0f));
+  }
+};
+
+// CAT2p increment G of one interface by a group of 2p lanes (lane l <-> node
+// j = l - p + 1). hi/lo point at cell i of component 0 of the compensated
+// tile, components `cs` apart. Every lane returns G.
+template <int p, int FLUX>
+__device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int cs, int l, int base,
+                                          float lam, float adv, float gm1, float *Gout) {
+  using TB = Tab<float>;
+  using DP = DPhys<FLUX>;
+  constexpr int S = DP::S;
+  constexpr int n = 2 * p;
+  const unsigned mask = ((1u << n) - 1u) << base;
+  const int j = l - p + 1;
+  float g1r[n];
+#pragma unroll
+  for (int r = 0; r < n; r++) g1r[r] = TB::g1(p, l, r);
+  float ui[S], uj[S], d0[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    ui[c] = hi[c * cs];
+    uj[c] = hi[c * cs + j];
+    d0[c] = (hi[c * cs + j] - hi[c * cs]) + (lo[c * cs + j] - lo[c * cs]);
+  }
+  float D[S], Fsum[S], Fprev[S], del[n][S];
+  DP::dflux(DP::base(ui, adv, gm1), d0, D);  // f(u_j) - f(u_i)
+  const typename DP::Base bj = DP::base(uj, adv, gm1);
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    Fsum[c] = D[c];
+    Fprev[c] = D[c];
+  }
+#pragma unroll
+  for (int rr = 0; rr < n; rr++)
+#pragma unroll
+    for (int c = 0; c < S; c++) del[rr][c] = 0.0f;
+#pragma unroll
+  for (int k = 2; k <= n; k++) {
+    float U[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) U[c] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < n; r++)
+#pragma unroll
+      for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
+    float acc[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      U[c] *= -lam;
+      acc[c] = 0.0f;
+    }
+#pragma unroll
+    for (int rr = 0; rr < n; rr++) {
+      if (rr == p - 1) continue;  // r = 0: no increment
+      const float cr = TB::taylor(p, rr, k - 1);
+      float E[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) del[rr][c] = fmaf(cr, U[c], del[rr][c]);
+      DP::dflux(bj, del[rr], E);
+#pragma unroll
+      for (int c = 0; c < S; c++) acc[c] = fmaf(TB::gk(p, k - 1, rr), E[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      Fprev[c] = acc[c];
+      Fsum[c] = fmaf(TB::invfact(k), acc[c], Fsum[c]);
+    }
+  }
+  const float w = TB::gh(p, l);
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const float v = w * Fsum[c];
+    float t = 0.0f;
+#pragma unroll
+    for (int r = 0; r < n; r++) t += __shfl_sync(mask, v, base + r);
+    Gout[c] = t;
+  }
+}
+
+// FL-CAT2 increment G (F* = f(u_i) + G), single lane. With D1 = f(u_{i+1}) -
+// f(u_i), U = -lambda D1, T0 = df(u_i; U), T1 = df(u_i; u_{i+1} - u_i + U):
+//   CAT2:    F1 - f(u_i) = (T0 + T1 + D1) / 4
+//   Rusanov: Flo - f(u_i) = D1 / 2 - alpha (u_{i+1} - u_i) / 2
+template <int FLUX>
+__device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, const double *q64,
+                                             int cs, float lam, float adv, float gamma, double advd,
+                                             double gammad, int limiter_form, float *G) {
+  using DP = DPhys<FLUX>;
+  constexpr int S = DP::S;
+  const float gm1 = gamma - 1.0f;
+  float u0[S], u1[S], du[S], D1[S], U[S], d1[S], T0[S], T1[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    u0[c] = hi[c * cs];
+    u1[c] = hi[c * cs + 1];
+    du[c] = (hi[c * cs + 1] - hi[c * cs]) + (lo[c * cs + 1] - lo[c * cs]);
+  }
+  const typename DP::Base b0 = DP::base(u0, adv, gm1);
+  DP::dflux(b0, du, D1);
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    U[c] = -lam * D1[c];
+    d1[c] = du[c] + U[c];
+  }
+  DP::dflux(b0, U, T0);
+  DP::dflux(b0, d1, T1);
+  const float s0 = DP::speed(u0, adv, gamma), s1 = DP::speed(u1, adv, gamma);
+  const float alpha = s1 > s0 ? s1 : s0;
+  const float w = (float)psi1<FLUX>(q64, cs, limiter_form, advd);
+  (void)gammad;
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const float G1 = 0.25f * (T0[c] + T1[c] + D1[c]);
+    const float Glo = 0.5f * D1[c] - 0.5f * alpha * du[c];
+    G[c] = fmaf(w, G1 - Glo, Glo);
   }
 }
 
@@ -377,45 +572,59 @@ struct Tiling {
   static constexpr int TW = T + 2 * GH;       // staged cells
 };
 
-template <bool F32>
-struct Prec {
-  using R = double;
-};
-template <>
-struct Prec<true> {
-  using R = float;
-};
-
-template <int P, int FLUX, bool F32>
-__global__ void __launch_bounds__(NT) k_step1d(const Step1DArgs a) {
+// Order selection of the interface of lane group `grp`: the (p, component)
+// pairs p = 2..P are spread over the group's lanes, each lane evaluating
+// psi^p of one component; a group OR-reduction of the rejected orders gives
+// p_s = max A (1 when A is empty). A component's psi is admissible when
+// psi >= thr; as in a literal minimum over components taken from the first
+// component, a NaN in the first component rejects p and a NaN elsewhere is
+// ignored. Must be called by all 32 lanes.
+template <int P, int S>
+__device__ __forceinline__ int select_order(const double *t0, int cs, int l, int grp, bool active,
+                                            bool valid, double eps, double thr, const double *fact) {
   using TL = Tiling<P>;
-  using R = typename Prec<F32>::R;
+  if (P < 2) return 1;
+  constexpr int NPAIR = (P - 1) * S;
+  unsigned rej = 0;
+  if (active) {
+    for (int q = l; q < NPAIR; q += TL::L) {
+      const int p = 2 + q / S, c = q - (q / S) * S;
+      const double v = psi_p_comp(t0 + c * cs, p, eps, fact[p]);
+      const bool ok = (c == 0) ? (v >= thr) : !(v < thr);
+      if (!ok) rej |= 1u << (p - 2);
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  constexpr unsigned spare = (TL::GPW * TL::L >= 32) ? 0u : (0xffffffffu << (TL::GPW * TL::L));
+  const unsigned gmask = valid ? (((1u << TL::L) - 1u) << (grp * TL::L)) : spare;
+  rej = __reduce_or_sync(gmask, rej);
+  (void)lane;
+  const unsigned accept = ~rej & ((1u << (P - 1)) - 1u);
+  return accept ? (32 - __clz(accept)) + 1 : 1;
+}
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
+  using TL = Tiling<P>;
   constexpr int S = Phys<FLUX>::S;
-  __shared__ double tile[S][TL::TW];                          // FP64 value of the state
-  __shared__ R tileR[F32 ? S : 1][F32 ? TL::TW : 1];          // float operand (FP32)
-  __shared__ R Fs[TL::NI][S];
+  __shared__ double tile[S][TL::TW];
+  __shared__ double Fs[TL::NI][S];
   __shared__ double s_dt;
   __shared__ double s_red[NT / 32];
+  const double *__restrict__ uin = static_cast<const double *>(a.u_in);
+  double *__restrict__ uout = static_cast<double *>(a.u_out);
   const long N = a.N;
   const long i0 = (long)blockIdx.x * TL::T;
 
   if (threadIdx.x == 0) s_dt = step_dt(a);
   for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
     const int c = q / TL::TW, k = q - c * TL::TW;
-    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
-    if constexpr (F32) {
-      const float *uin = static_cast<const float *>(a.u_in);
-      const float hi = uin[c * N + g], lo = uin[(S + c) * N + g];
-      tile[c][k] = (double)hi + (double)lo;
-      tileR[c][k] = hi;
-    } else {
-      tile[c][k] = static_cast<const double *>(a.u_in)[c * N + g];
-    }
+    tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
   }
   __syncthreads();
   const double dt = s_dt;
-  const double lamd = dt / a.dx;
-  const R lam = R(lamd), adv = R(a.adv), gm1 = R(a.gamma - 1.0);
+  const double lam = dt / a.dx;
+  const double gm1 = a.gamma - 1.0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / TL::L, l = lane - grp * TL::L;
@@ -425,40 +634,21 @@ __global__ void __launch_bounds__(NT) k_step1d(const Step1DArgs a) {
   const bool active = valid && m <= N;
   const int ic = il - 1 + TL::GH;       // tile index of cell m-1
 
-  // --- indicators and order selection -------------------------------------
-  bool adm = false;
-  if (P >= 2 && active && l < P - 1) {
-    const int p = l + 2;
-    double mn = 0.0;
-#pragma unroll
-    for (int c = 0; c < S; c++) {
-      const double v = psi_p_comp(&tile[c][ic], p, a.eps, a.fact_tau[p]);
-      if (c == 0 || v < mn) mn = v;
-    }
-    adm = mn >= a.thr;
-  }
-  const unsigned bal = __ballot_sync(0xffffffffu, adm);
-  int ps = 1;
-  if (valid && P >= 2) {
-    const unsigned bits = (bal >> (grp * TL::L)) & ((1u << (P - 1 > 0 ? P - 1 : 0)) - 1u);
-    ps = bits ? (32 - __clz(bits)) + 1 : 1;
-  }
+  const int ps = select_order<P, S>(&tile[0][valid ? ic : 0], TL::TW, l, grp, active, valid, a.eps,
+                                    a.thr, a.fact_tau);
 
-  // --- flux ------------------------------------------------------------------
-  R F[S];
+  double F[S];
   const int base = grp * TL::L;
-  const R *qR;
-  if constexpr (F32) qR = &tileR[0][ic];
-  else qR = &tile[0][ic];
+  const double *q0 = &tile[0][ic];
   if (active) {
     if (ps == 4) {
-      if constexpr (P >= 4) cat_flux<4, FLUX, R>(qR, TL::TW, l, base, lam, adv, gm1, F);
+      if constexpr (P >= 4) cat_flux<4, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else if (ps == 3) {
-      if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX, R>(qR, TL::TW, l, base, lam, adv, gm1, F);
+      if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else if (ps == 2) {
-      if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, R>(qR, TL::TW, l, base, lam, adv, gm1, F);
+      if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else if (l == 0) {
-      flcat2_flux<FLUX, R>(qR, &tile[0][ic], TL::TW, lam, adv, a.adv, a.gamma, a.limiter_form, F);
+      flcat2_flux<FLUX>(q0, TL::TW, lam, a.adv, a.gamma, a.limiter_form, F);
     }
     if (l == 0) {
 #pragma unroll
@@ -468,39 +658,125 @@ __global__ void __launch_bounds__(NT) k_step1d(const Step1DArgs a) {
   }
   __syncthreads();
 
-  // --- conservative update and wave-speed epilogue ---------------------------
   double smax = 0.0;
   bool bad = false;
   for (int t = threadIdx.x; t < TL::T; t += NT) {
     const long i = i0 + t;
     if (i >= N) break;
     double un[S];
-    if constexpr (F32) {
-      const float *uin = static_cast<const float *>(a.u_in);
-      float *uout = static_cast<float *>(a.u_out);
 #pragma unroll
-      for (int c = 0; c < S; c++) {
-        const float hi = tileR[c][t + TL::GH], lo = uin[(S + c) * N + i];
-        const float d = __fmul_rn(lam, __fsub_rn(Fs[t][c], Fs[t + 1][c]));
-        // TwoSum(hi, d): s + e = hi + d exactly
-        const float s = __fadd_rn(hi, d);
-        const float bp = __fsub_rn(s, hi);
-        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(d, bp));
-        const float lo2 = __fadd_rn(lo, e);
-        // Fast2Sum(s, lo2), |s| >= |lo2|: renormalised pair
-        const float hn = __fadd_rn(s, lo2);
-        const float ln = __fsub_rn(lo2, __fsub_rn(hn, s));
-        uout[c * N + i] = hn;
-        uout[(S + c) * N + i] = ln;
-        un[c] = (double)hn + (double)ln;
-      }
-    } else {
-      double *uout = static_cast<double *>(a.u_out);
+    for (int c = 0; c < S; c++) {
+      un[c] = tile[c][t + TL::GH] + lam * (Fs[t][c] - Fs[t + 1][c]);
+      uout[c * N + i] = un[c];
+    }
+    bool ok;
+    const double sp = Phys<FLUX>::speed(un, a.adv, a.gamma, ok);
+    bad |= !ok;
+    smax = fmax(smax, sp);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
 #pragma unroll
-      for (int c = 0; c < S; c++) {
-        un[c] = tile[c][t + TL::GH] + lamd * (Fs[t][c] - Fs[t + 1][c]);
-        uout[c * N + i] = un[c];
-      }
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0) s_red[warp] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = s_red[0];
+    for (int w = 1; w < NT / 32; w++) v = fmax(v, s_red[w]);
+    atomic_max_pos(&a.smax[(a.slot + 1) % 3], v);
+  }
+}
+
+// FP32 step on the compensated state [hi(s x N); lo(s x N)].
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
+  using TL = Tiling<P>;
+  using DP = DPhys<FLUX>;
+  constexpr int S = DP::S;
+  __shared__ double tile[S][TL::TW];  // hi + lo, exact
+  __shared__ float thi[S][TL::TW], tlo[S][TL::TW];
+  __shared__ float Gs[TL::NI][S];
+  __shared__ double s_dt;
+  __shared__ double s_red[NT / 32];
+  const float *__restrict__ uin = static_cast<const float *>(a.u_in);
+  float *__restrict__ uout = static_cast<float *>(a.u_out);
+  const long N = a.N;
+  const long i0 = (long)blockIdx.x * TL::T;
+
+  if (threadIdx.x == 0) s_dt = step_dt(a);
+  for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
+    const int c = q / TL::TW, k = q - c * TL::TW;
+    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
+    const float h = uin[c * N + g], w = uin[(S + c) * N + g];
+    thi[c][k] = h;
+    tlo[c][k] = w;
+    tile[c][k] = (double)h + (double)w;
+  }
+  __syncthreads();
+  const double dt = s_dt;
+  const float lam = (float)(dt / a.dx), adv = (float)a.adv, gam = (float)a.gamma;
+  const float gm1 = (float)(a.gamma - 1.0);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / TL::L, l = lane - grp * TL::L;
+  const bool valid = grp < TL::GPW;
+  const int il = warp * TL::GPW + grp;
+  const long m = i0 + il;
+  const bool active = valid && m <= N;
+  const int ic = il - 1 + TL::GH;
+
+  const int ps = select_order<P, S>(&tile[0][valid ? ic : 0], TL::TW, l, grp, active, valid, a.eps,
+                                    a.thr, a.fact_tau);
+
+  float G[S];
+  const int base = grp * TL::L;
+  if (active) {
+    const float *h0 = &thi[0][ic], *l0 = &tlo[0][ic];
+    if (ps == 4) {
+      if constexpr (P >= 4) cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+    } else if (ps == 3) {
+      if constexpr (P >= 3) if (l < 6) cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+    } else if (ps == 2) {
+      if constexpr (P >= 2) if (l < 4) cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+    } else if (l == 0) {
+      flcat2_delta<FLUX>(h0, l0, &tile[0][ic], TL::TW, lam, adv, gam, a.adv, a.gamma, a.limiter_form, G);
+    }
+    if (l == 0) {
+#pragma unroll
+      for (int c = 0; c < S; c++) Gs[il][c] = G[c];
+      if (a.orders && (il < TL::T || m == N)) a.orders[m] = (int8_t)ps;
+    }
+  }
+  __syncthreads();
+
+  double smax = 0.0;
+  bool bad = false;
+  for (int t = threadIdx.x; t < TL::T; t += NT) {
+    const long i = i0 + t;
+    if (i >= N) break;
+    const int k = t + TL::GH;
+    float ui[S], dl[S], B[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      ui[c] = thi[c][k];
+      dl[c] = (thi[c][k - 1] - thi[c][k]) + (tlo[c][k - 1] - tlo[c][k]);
+    }
+    DP::dflux(DP::base(ui, adv, gm1), dl, B);  // f(u_{i-1}) - f(u_i)
+    double un[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const float d = __fmul_rn(lam, __fadd_rn(B[c], __fsub_rn(Gs[t][c], Gs[t + 1][c])));
+      const float h = thi[c][k], w = tlo[c][k];
+      // TwoSum(h, d): s + e = h + d exactly
+      const float s = __fadd_rn(h, d);
+      const float bp = __fsub_rn(s, h);
+      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+      const float w2 = __fadd_rn(w, e);
+      // Fast2Sum(s, w2), |s| >= |w2|: renormalised pair
+      const float hn = __fadd_rn(s, w2);
+      const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
+      uout[c * N + i] = hn;
+      uout[(S + c) * N + i] = ln;
+      un[c] = (double)hn + (double)ln;
     }
     bool ok;
     const double sp = Phys<FLUX>::speed(un, a.adv, a.gamma, ok);
@@ -559,7 +835,8 @@ template <int P, int FLUX, bool F32>
 int launch_p(const Step1DArgs &a, cudaStream_t st) {
   using TL = Tiling<P>;
   const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
-  k_step1d<P, FLUX, F32><<<grid, NT, 0, st>>>(a);
+  if constexpr (F32) k_step1d_f32<P, FLUX><<<grid, NT, 0, st>>>(a);
+  else k_step1d_f64<P, FLUX><<<grid, NT, 0, st>>>(a);
   return (int)cudaGetLastError();
 }
 

@@ -48,6 +48,31 @@ struct Step1DArgs {
   unsigned *status;           // sticky status bits
 };
 
+// Arguments of one 2D step launch (passed by value). State u[c][y][x].
+struct Step2DArgs {
+  const void *u_in;
+  void *u_out;
+  int NX, NY;
+  int bc;
+  int limiter_form;
+  int slot;                   // step index mod 3
+  double dx, dy, cfl;
+  double dt_fixed, t_end;
+  double gamma, adv[2], eps, thr;
+  double fact_tau[ACAT_MAXP + 1];
+  unsigned long long *smax;   // 3 slots x 2 directions: [slot][dir]
+  double *tslot;              // 3 slots (nullable)
+  int8_t *ord_x;              // NY x (NX+1) (nullable)
+  int8_t *ord_y;              // (NY+1) x NX (nullable)
+  double *dt_out;
+  unsigned *status;
+};
+
+int acat_launch_step2d(int P, int flux, int prec, const Step2DArgs &a, void *stream);
+int acat_launch_smax2d(int flux, int prec, const Step2DArgs &a, void *stream);
+int acat_upload_tables_1d(const AcatTables *T);
+int acat_upload_tables_2d(const AcatTables *T);
+
 // Initial wave-speed reduction into smax[slot] (and t = 0 into tslot[slot]).
 int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream);
 // One 1D step; returns 0 or a cudaError_t value.

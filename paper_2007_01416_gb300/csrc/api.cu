@@ -16,6 +16,7 @@
 struct acat_ctx {
   acat_params p;
   int s = 1;
+  int dim = 1;
   int device = 0;
   long cells = 0;
   unsigned long long *d_smax = nullptr;  // 3 slots
@@ -62,8 +63,13 @@ int check_params(const acat_params *p) {
   if ((p->flux == ACAT_FLUX_EULER1D || p->flux == ACAT_FLUX_EULER2D) && !(p->gamma > 1.0))
     return ACAT_ERR_INVALID_ARG;
   const bool is2d = p->ny > 1 || p->flux == ACAT_FLUX_EULER2D;
-  if (is2d) return ACAT_ERR_UNSUPPORTED;
-  if (p->flux == ACAT_FLUX_EULER2D) return ACAT_ERR_INVALID_ARG;
+  if (is2d) {
+    if (p->ny < 2 * (p->P > 2 ? p->P : 2)) return ACAT_ERR_INVALID_ARG;
+    if (p->flux != ACAT_FLUX_EULER2D && p->flux != ACAT_FLUX_LINEAR) return ACAT_ERR_UNSUPPORTED;
+    if (p->P > 2) return ACAT_ERR_UNSUPPORTED;  // 2D kernels cover P <= 2
+    if ((long)p->nx * (long)p->ny > (1l << 31)) return ACAT_ERR_TOO_LARGE;
+    return ACAT_OK;
+  }
   if ((long)p->nx > (1l << 30)) return ACAT_ERR_TOO_LARGE;
   return ACAT_OK;
 }
@@ -89,6 +95,30 @@ Step1DArgs base_args(acat_ctx *c) {
   return a;
 }
 
+Step2DArgs base_args2(acat_ctx *c) {
+  Step2DArgs a;
+  std::memset(&a, 0, sizeof a);
+  const acat_params &p = c->p;
+  a.NX = p.nx;
+  a.NY = p.ny;
+  a.bc = p.bc;
+  a.limiter_form = p.limiter_form;
+  a.dx = (p.x1 - p.x0) / (double)p.nx;
+  a.dy = (p.y1 - p.y0) / (double)p.ny;
+  a.cfl = p.cfl;
+  a.dt_fixed = -1.0;
+  a.t_end = -1.0;
+  a.gamma = p.gamma;
+  a.adv[0] = p.adv[0];
+  a.adv[1] = p.adv[1];
+  a.eps = p.eps;
+  a.thr = 1.0 - p.psi_tol;
+  for (int q = 0; q <= ACAT_MAXP; q++) a.fact_tau[q] = c->fact_tau[q];
+  a.smax = c->d_smax;
+  a.status = c->d_status;
+  return a;
+}
+
 int launch_step(acat_ctx *c, const Step1DArgs &a, cudaStream_t st) {
   int e = acat_launch_step1d(c->p.P, c->p.flux, c->p.precision, a, st);
   c->launches++;
@@ -97,6 +127,20 @@ int launch_step(acat_ctx *c, const Step1DArgs &a, cudaStream_t st) {
 
 // Steps n..n+count-1 of a run on (u, work), dt slots n % 3.
 int issue_steps(acat_ctx *c, void *u, long n, int count, double t_end, cudaStream_t st) {
+  if (c->dim == 2) {
+    Step2DArgs a = base_args2(c);
+    a.t_end = t_end;
+    a.tslot = c->d_t;
+    for (int k = 0; k < count; k++, n++) {
+      a.u_in = (n % 2 == 0) ? u : c->d_work;
+      a.u_out = (n % 2 == 0) ? c->d_work : u;
+      a.slot = (int)(n % 3);
+      int e = acat_launch_step2d(c->p.P, c->p.flux, c->p.precision, a, st);
+      c->launches++;
+      if (e) return ACAT_ERR_CUDA;
+    }
+    return ACAT_OK;
+  }
   Step1DArgs a = base_args(c);
   a.t_end = t_end;
   a.tslot = c->d_t;
@@ -175,6 +219,7 @@ int acat_create(const acat_params *p, acat_ctx **out) {
   c->p = *p;
   c->s = nvars(p->flux);
   c->cells = (long)p->nx * p->ny;
+  c->dim = (p->ny > 1 || p->flux == ACAT_FLUX_EULER2D) ? 2 : 1;
   {
     AcatTables T;
     acat_build_tables(&T);
@@ -199,11 +244,11 @@ int acat_create(const acat_params *p, acat_ctx **out) {
     }
   }
   const size_t sb = (size_t)acat_state_bytes(c);
-  cudaError_t e = cudaMalloc(&c->d_smax, 3 * sizeof(unsigned long long));
+  cudaError_t e = cudaMalloc(&c->d_smax, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_t, 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_work, sb);
-  if (e == cudaSuccess) e = cudaMemset(c->d_smax, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_smax, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_t, 0, 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -240,13 +285,35 @@ int acat_step(acat_ctx *c, const void *u_in, void *u_out, double dt, void *strea
   if (!c || !u_in || !u_out || u_in == u_out) return ACAT_ERR_INVALID_ARG;
   if (!(dt > 0.0) && dt != dt) return ACAT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->dim == 2) {
+    Step2DArgs a = base_args2(c);
+    a.u_in = u_in;
+    a.u_out = u_out;
+    a.slot = 0;
+    a.dt_out = dt_dev;
+    if (orders_dev) {
+      a.ord_x = orders_dev;
+      a.ord_y = orders_dev + (long)c->p.ny * (c->p.nx + 1);
+    }
+    if (cudaMemsetAsync(c->d_smax, 0, 6 * sizeof(unsigned long long), st) != cudaSuccess)
+      return ACAT_ERR_CUDA;
+    if (dt > 0.0) {
+      a.dt_fixed = dt;
+    } else {
+      if (acat_launch_smax2d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+      c->launches++;
+    }
+    int e2 = acat_launch_step2d(c->p.P, c->p.flux, c->p.precision, a, st);
+    c->launches++;
+    return e2 ? ACAT_ERR_CUDA : ACAT_OK;
+  }
   Step1DArgs a = base_args(c);
   a.u_in = u_in;
   a.u_out = u_out;
   a.slot = 0;
   a.orders = orders_dev;
   a.dt_out = dt_dev;
-  cudaError_t e = cudaMemsetAsync(c->d_smax, 0, 3 * sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(c->d_smax, 0, 6 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return ACAT_ERR_CUDA;
   if (dt > 0.0) {
     a.dt_fixed = dt;
@@ -261,13 +328,21 @@ int acat_run(acat_ctx *c, void *u, int nsteps, double t_end, void *stream, doubl
   if (!c || !u || nsteps < 0) return ACAT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (t_end != t_end) return ACAT_ERR_INVALID_ARG;
-  Step1DArgs a = base_args(c);
-  a.u_in = u;
-  a.slot = 0;
-  a.tslot = c->d_t;
-  if (cudaMemsetAsync(c->d_smax, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess)
+  if (cudaMemsetAsync(c->d_smax, 0, 6 * sizeof(unsigned long long), st) != cudaSuccess)
     return ACAT_ERR_CUDA;
-  if (acat_launch_smax1d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+  if (c->dim == 2) {
+    Step2DArgs a = base_args2(c);
+    a.u_in = u;
+    a.slot = 0;
+    a.tslot = c->d_t;
+    if (acat_launch_smax2d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+  } else {
+    Step1DArgs a = base_args(c);
+    a.u_in = u;
+    a.slot = 0;
+    a.tslot = c->d_t;
+    if (acat_launch_smax1d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+  }
   c->launches++;
   long n = 0;
   const int chunks = nsteps / GRAPH_STEPS;

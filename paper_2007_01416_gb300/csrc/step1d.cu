@@ -32,53 +32,9 @@
 // size O(dx) rather than to |f|. The update adds lambda (f(u_{i-1}) - f(u_i) +
 // G_{i-1/2} - G_{i+1/2}) to the pair with an error-free transformation
 // (Knuth's TwoSum, then Dekker's Fast2Sum).
-#include <cuda_runtime.h>
-
-#include <cstdint>
-
-#include "../../include/acat.h"
-#include "acat_internal.h"
-
-__constant__ AcatTables c_tab;
+#include "device_common.cuh"
 
 namespace {
-
-constexpr int NT = 256;  // threads per CTA
-
-// ---------------------------------------------------------------------------
-// Arithmetic helpers
-// ---------------------------------------------------------------------------
-// 1/x for x > 0: the hardware approximation rcp.approx.ftz.f64 (about 23
-// correct bits) refined by two Newton-Raphson steps y <- y + y (1 - x y), each
-// doubling the number of correct bits (error within an ulp of 1/x).
-__device__ __forceinline__ double recip(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-
-template <typename R>
-struct Tab;
-template <>
-struct Tab<double> {
-  __device__ static double g1(int p, int j, int r) { return c_tab.g1[p][j][r]; }
-  __device__ static double gk(int p, int k, int r) { return c_tab.gk[p][k][r]; }
-  __device__ static double gh(int p, int j) { return c_tab.gh[p][j]; }
-  __device__ static double taylor(int p, int r, int l) { return c_tab.taylor[p][r][l]; }
-  __device__ static double invfact(int k) { return c_tab.invfact[k]; }
-};
-template <>
-struct Tab<float> {
-  __device__ static float g1(int p, int j, int r) { return c_tab.g1f[p][j][r]; }
-  __device__ static float gk(int p, int k, int r) { return c_tab.gkf[p][k][r]; }
-  __device__ static float gh(int p, int j) { return c_tab.ghf[p][j]; }
-  __device__ static float taylor(int p, int r, int l) { return c_tab.taylorf[p][r][l]; }
-  __device__ static float invfact(int k) { return c_tab.invfactf[k]; }
-};
 
 // ---------------------------------------------------------------------------
 // Physics
@@ -131,90 +87,10 @@ struct Phys<ACAT_FLUX_EULER1D> {
   }
 };
 
-__device__ __forceinline__ long bc_index(long g, long N, int bc) {
-  if (bc == ACAT_BC_PERIODIC) {
-    long r = g % N;
-    return r < 0 ? r + N : r;
-  }
-  return g < 0 ? 0 : (g >= N ? N - 1 : g);
-}
-
-// ---------------------------------------------------------------------------
-// Indicators and limiter: explicit round-to-nearest FP64 operations, no FMA
-// contraction, in the order of Eqs. 3.6-3.12.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double psi_p_comp(const double *q, int p, double eps, double fact) {
-  double IL = 0.0, IR = 0.0;
-  for (int j = -p + 1; j <= -1; j++) {
-    const double d = __dsub_rn(q[1 + j], q[j]);
-    IL = __dadd_rn(IL, __dmul_rn(d, d));
-  }
-  IL = __dadd_rn(IL, eps);
-  for (int j = 1; j <= p - 1; j++) {
-    const double d = __dsub_rn(q[1 + j], q[j]);
-    IR = __dadd_rn(IR, __dmul_rn(d, d));
-  }
-  IR = __dadd_rn(IR, eps);
-  const double I = __ddiv_rn(__dmul_rn(IL, IR), __dadd_rn(IL, IR));
-  double S = 0.0;
-  for (int j = -p + 1; j <= p; j++) S = __dadd_rn(S, __dmul_rn(c_tab.gd[p][j + p - 1], q[j]));
-  const double D = __dmul_rn(fact, S);
-  const double tau = __dmul_rn(D, D);
-  return __ddiv_rn(I, __dadd_rn(I, tau));
-}
-
-__device__ __forceinline__ double lim_ratio(double upw, double loc) {
-  if (loc == 0.0) {
-    if (upw == 0.0) return 1.0;
-    return upw > 0.0 ? __longlong_as_double(0x7ff0000000000000LL)
-                     : __longlong_as_double((long long)0xfff0000000000000ULL);
-  }
-  return __ddiv_rn(upw, loc);
-}
-
-__device__ __forceinline__ double superbee(double r) {
-  const double r2 = __dmul_rn(2.0, r);
-  const double a = r2 < 1.0 ? r2 : 1.0;
-  const double b = r < 2.0 ? r : 2.0;
-  const double m = a > b ? a : b;
-  return m > 0.0 ? m : 0.0;
-}
-
-// psi^1 at the interface between q[0] (cell i) and q[1]; stride between
-// components `cs`.
+// psi^1 of a 1D interface (cells consecutive in the tile).
 template <int FLUX>
 __device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form, double adv) {
-  constexpr int S = Phys<FLUX>::S;
-  if (S == 1 && limiter_form == 0) {
-    const double um = q[-1], u0 = q[0], u1 = q[1], u2 = q[2];
-    double a;
-    if (u0 != u1) {
-      double f0, f1;
-      if (FLUX == ACAT_FLUX_LINEAR) {
-        f0 = __dmul_rn(adv, u0);
-        f1 = __dmul_rn(adv, u1);
-      } else {
-        f0 = __dmul_rn(__dmul_rn(0.5, u0), u0);
-        f1 = __dmul_rn(__dmul_rn(0.5, u1), u1);
-      }
-      a = __ddiv_rn(__dsub_rn(f1, f0), __dsub_rn(u1, u0));
-    } else {
-      a = (FLUX == ACAT_FLUX_LINEAR) ? adv : u0;
-    }
-    const double upw = a > 0.0 ? __dsub_rn(u0, um) : __dsub_rn(u2, u1);
-    return superbee(lim_ratio(upw, __dsub_rn(u1, u0)));
-  }
-  double best = 2.0;
-#pragma unroll
-  for (int c = 0; c < S; c++) {
-    const double *p = q + c * cs;
-    const double loc = __dsub_rn(p[1], p[0]);
-    const double pm = superbee(lim_ratio(__dsub_rn(p[0], p[-1]), loc));
-    const double pp = superbee(lim_ratio(__dsub_rn(p[2], p[1]), loc));
-    const double v = pp < pm ? pp : pm;
-    if (v < best) best = v;
-  }
-  return best;
+  return psi1_line<Phys<FLUX>::S>(q, cs, 1, FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, adv);
 }
 
 // ---------------------------------------------------------------------------
@@ -526,11 +402,6 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, c
   }
 }
 
-__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
-  // non-negative doubles (and +inf) order like their bit patterns
-  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
-}
-
 // dt of this step from the reduced wave speed (1D CFL rule); also advances
 // the simulated time and recycles the slot two steps ahead (block 0).
 __device__ double step_dt(const Step1DArgs &a) {
@@ -589,7 +460,7 @@ __device__ __forceinline__ int select_order(const double *t0, int cs, int l, int
   if (active) {
     for (int q = l; q < NPAIR; q += TL::L) {
       const int p = 2 + q / S, c = q - (q / S) * S;
-      const double v = psi_p_comp(t0 + c * cs, p, eps, fact[p]);
+      const double v = psi_p_comp(t0 + c * cs, 1, p, eps, fact[p]);
       const bool ok = (c == 0) ? (v >= thr) : !(v < thr);
       if (!ok) rej |= 1u << (p - 2);
     }
@@ -900,8 +771,12 @@ int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream) {
   return (int)cudaErrorInvalidValue;
 }
 
+int acat_upload_tables_1d(const AcatTables *T) { return (int)cudaMemcpyToSymbol(c_tab, T, sizeof *T); }
+
 int acat_upload_tables_current_device() {
   AcatTables T;
   acat_build_tables(&T);
-  return (int)cudaMemcpyToSymbol(c_tab, &T, sizeof T);
+  int e = acat_upload_tables_1d(&T);
+  if (e == 0) e = acat_upload_tables_2d(&T);
+  return e;
 }

@@ -1,0 +1,782 @@
+// step2d.cu -- the 2D ACAT step (Sec. 4) on sm_103a CUDA cores, for the 2D
+// Euler equations and 2D linear transport, P <= 2.
+//
+// A CTA owns a 15 x 15 tile of cells and the 16 x 16 corner anchors
+// (x, y), x0-1 <= x < x0+15, y0-1 <= y < y0+15, that carry the x-flux F at
+// (x+1/2, y) and the y-flux G at (x, y+1/2) around its cells (Eq. 4.9). The
+// cells the anchors' stencils reach (a halo of max(P, 2)) are staged once in
+// shared memory with the boundary condition applied. Each anchor is worked by
+// a group of 16 lanes, one lane per node of the 4 x 4 block S_2:
+//   - the indicators are taken dimension by dimension (p_1 from the row
+//     through the anchor, p_2 from its column; Sec. 4, admissible sets A_1,
+//     A_2), one (direction, component) pair per lane, in explicitly rounded
+//     FP64 as in 1D;
+//   - when a direction selects p = 2, the group runs the block recursion of
+//     Sec. 4 (Eqs. 4.5-4.6): u~^(k-1) at every node from the x-derivative of
+//     f~ along its row and the y-derivative of g~ along its column (lane
+//     shuffles), f and g at the 2p - 1 other time levels, and F from row 0,
+//     G from column 0. One block serves both directions when both select it;
+//   - a direction that selects nothing uses FL-CAT2 (Eqs. 4.3-4.4 blended as
+//     Eqs. 4.7-4.8) on one lane.
+// The update and the dt epilogue (both directions' maximal speeds, Sec. 5.5
+// CFL rule) follow as in 1D. The FP32 variant uses the delta formulation of
+// the 1D kernel: F = f(u_a) + G_F, G = g(u_a) + G_G about the anchor state.
+#include <type_traits>
+
+#include "device_common.cuh"
+
+namespace {
+
+constexpr int TXY = 15;       // cells per CTA side
+constexpr int NA = TXY + 1;   // anchors per CTA side
+constexpr int GH2 = 2;        // ghost width (P <= 2)
+constexpr int TW2 = TXY + 2 * GH2;
+
+template <int FLUX>
+struct Phys2;
+
+template <>
+struct Phys2<ACAT_FLUX_LINEAR> {
+  static constexpr int S = 1;
+  template <typename R>
+  __device__ static __forceinline__ void flux2(const R *u, R *f, R *g, R ax, R ay, R) {
+    f[0] = ax * u[0];
+    g[0] = ay * u[0];
+  }
+  __device__ static __forceinline__ void speed2(const double *u, double ax, double ay, double,
+                                                double &sx, double &sy, bool &ok) {
+    sx = fabs(ax);
+    sy = fabs(ay);
+    ok = isfinite(u[0]);
+  }
+  struct Base {
+    float ax, ay;
+  };
+  __device__ static __forceinline__ Base base(const float *, float ax, float ay, float) {
+    return Base{ax, ay};
+  }
+  __device__ static __forceinline__ void dflux2(const Base &B, const float *d, float *df, float *dg) {
+    df[0] = B.ax * d[0];
+    dg[0] = B.ay * d[0];
+  }
+  __device__ static __forceinline__ float fspeed(const float *, float ax, float ay, float, int dir) {
+    return dir == 0 ? fabsf(ax) : fabsf(ay);
+  }
+};
+
+template <>
+struct Phys2<ACAT_FLUX_EULER2D> {
+  static constexpr int S = 4;
+  template <typename R>
+  __device__ static __forceinline__ void flux2(const R *u, R *f, R *g, R, R, R gm1) {
+    const R ri = recip(u[0]);
+    const R v = u[1] * ri, w = u[2] * ri;
+    const R p = gm1 * (u[3] - R(0.5) * (u[1] * v + u[2] * w));
+    const R H = u[3] + p;
+    f[0] = u[1];
+    f[1] = u[1] * v + p;
+    f[2] = u[1] * w;
+    f[3] = v * H;
+    g[0] = u[2];
+    g[1] = u[2] * v;
+    g[2] = u[2] * w + p;
+    g[3] = w * H;
+  }
+  // |v| + c and |w| + c, every operation rounded as written (bit-exact dt)
+  __device__ static __forceinline__ void speed2(const double *u, double, double, double gamma,
+                                                double &sx, double &sy, bool &ok) {
+    const double v = __ddiv_rn(u[1], u[0]), w = __ddiv_rn(u[2], u[0]);
+    const double ke = __dmul_rn(__dmul_rn(0.5, u[0]), __dadd_rn(__dmul_rn(v, v), __dmul_rn(w, w)));
+    const double p = __dmul_rn(__dsub_rn(gamma, 1.0), __dsub_rn(u[3], ke));
+    const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), u[0]));
+    sx = __dadd_rn(fabs(v), c);
+    sy = __dadd_rn(fabs(w), c);
+    ok = (u[0] > 0.0) && (p > 0.0) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) &&
+         isfinite(u[3]);
+  }
+  struct Base {
+    float mx, my, v, w, H, rho, gm1;
+  };
+  __device__ static __forceinline__ Base base(const float *u, float, float, float gm1) {
+    Base b;
+    b.rho = u[0];
+    b.mx = u[1];
+    b.my = u[2];
+    const float ri = __frcp_rn(u[0]);
+    b.v = u[1] * ri;
+    b.w = u[2] * ri;
+    const float p = gm1 * (u[3] - 0.5f * fmaf(u[1], b.v, u[2] * b.w));
+    b.H = u[3] + p;
+    b.gm1 = gm1;
+    return b;
+  }
+  // Increments of f and g for u -> u + d, d = (a, bx, by, c):
+  //   dv = (bx - v a)/(rho + a), dw = (by - w a)/(rho + a)
+  //   d(mx v) = mx dv + bx (v + dv), d(my w) = my dw + by (w + dw),
+  //   d(mx w) = mx dw + bx (w + dw), dp = (gamma - 1)(c - (d(mx v) + d(my w))/2)
+  __device__ static __forceinline__ void dflux2(const Base &B, const float *d, float *df, float *dg) {
+    const float ri = __frcp_rn(B.rho + d[0]);
+    const float dv = fmaf(-B.v, d[0], d[1]) * ri, dw = fmaf(-B.w, d[0], d[2]) * ri;
+    const float vn = B.v + dv, wn = B.w + dw;
+    const float dmv = fmaf(B.mx, dv, d[1] * vn), dmw = fmaf(B.my, dw, d[2] * wn);
+    const float dxy = fmaf(B.mx, dw, d[1] * wn);
+    const float dp = B.gm1 * fmaf(-0.5f, dmv + dmw, d[3]);
+    const float dH = d[3] + dp;
+    df[0] = d[1];
+    df[1] = dmv + dp;
+    df[2] = dxy;
+    df[3] = fmaf(dv, B.H, vn * dH);
+    dg[0] = d[2];
+    dg[1] = dxy;
+    dg[2] = dmw + dp;
+    dg[3] = fmaf(dw, B.H, wn * dH);
+  }
+  __device__ static __forceinline__ float fspeed(const float *u, float, float, float gamma, int dir) {
+    const float v = u[1] / u[0], w = u[2] / u[0];
+    const float p = (gamma - 1.0f) * (u[3] - 0.5f * (u[1] * v + u[2] * w));
+    return fabsf(dir == 0 ? v : w) + sqrtf(fmaxf(gamma * p / u[0], 0.0f));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// FP64 block recursion (Eqs. 4.5-4.6) by 16 lanes; lane l <-> node
+// (a1, b1) = (l % n, l / n). q points at the anchor for component 0; `cs`
+// between components, `rs` between rows. Every lane returns F and G.
+// ---------------------------------------------------------------------------
+template <int p, int FLUX>
+__device__ __forceinline__ void cat2d_f64(const double *q, int cs, int rs, int l, int base,
+                                          double lx, double ly, double ax, double ay, double gm1,
+                                          double *Fo, double *Go) {
+  using TB = Tab<double>;
+  constexpr int S = Phys2<FLUX>::S;
+  constexpr int n = 2 * p;
+  const unsigned mask = ((1u << (n * n)) - 1u) << base;
+  const int a1 = l % n, b1 = l / n;
+  double gx[n], gy[n];
+#pragma unroll
+  for (int r = 0; r < n; r++) {
+    gx[r] = TB::g1(p, a1, r);
+    gy[r] = TB::g1(p, b1, r);
+  }
+  double f0[S], g0[S], Ff[S], Fg[S], Pf[S], Pg[S], arg[n][S];
+  {
+    double u[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) u[c] = q[c * cs + (b1 - p + 1) * rs + (a1 - p + 1)];
+    Phys2<FLUX>::flux2(u, f0, g0, ax, ay, gm1);
+#pragma unroll
+    for (int rr = 0; rr < n; rr++)
+#pragma unroll
+      for (int c = 0; c < S; c++) arg[rr][c] = u[c];
+  }
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    Ff[c] = Pf[c] = f0[c];
+    Fg[c] = Pg[c] = g0[c];
+  }
+#pragma unroll
+  for (int k = 2; k <= n; k++) {
+    double Ux[S], Uy[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; r++)
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Ux[c] = fma(gx[r], __shfl_sync(mask, Pf[c], base + b1 * n + r), Ux[c]);
+        Uy[c] = fma(gy[r], __shfl_sync(mask, Pg[c], base + r * n + a1), Uy[c]);
+      }
+    double U[S], af[S], ag[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      U[c] = -(lx * Ux[c]) - ly * Uy[c];
+      af[c] = TB::gk(p, k - 1, p - 1) * f0[c];
+      ag[c] = TB::gk(p, k - 1, p - 1) * g0[c];
+    }
+#pragma unroll
+    for (int rr = 0; rr < n; rr++) {
+      if (rr == p - 1) continue;
+      const double cr = TB::taylor(p, rr, k - 1), wk = TB::gk(p, k - 1, rr);
+      double fr[S], gr[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) arg[rr][c] = fma(cr, U[c], arg[rr][c]);
+      Phys2<FLUX>::flux2(arg[rr], fr, gr, ax, ay, gm1);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        af[c] = fma(wk, fr[c], af[c]);
+        ag[c] = fma(wk, gr[c], ag[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      Pf[c] = af[c];
+      Pg[c] = ag[c];
+      Ff[c] = fma(TB::invfact(k), af[c], Ff[c]);
+      Fg[c] = fma(TB::invfact(k), ag[c], Fg[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const double vF = TB::gh(p, a1) * Ff[c], vG = TB::gh(p, b1) * Fg[c];
+    double tF = 0.0, tG = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; r++) {
+      tF += __shfl_sync(mask, vF, base + (p - 1) * n + r);
+      tG += __shfl_sync(mask, vG, base + r * n + (p - 1));
+    }
+    Fo[c] = tF;
+    Go[c] = tG;
+  }
+}
+
+// FP32 block recursion in the delta formulation about the anchor state u_a:
+// returns G_F = F - f(u_a) and G_G = G - g(u_a).
+template <int p, int FLUX>
+__device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int cs, int rs, int l,
+                                          int base, float lx, float ly, float ax, float ay, float gm1,
+                                          float *GFo, float *GGo) {
+  using TB = Tab<float>;
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  constexpr int n = 2 * p;
+  const unsigned mask = ((1u << (n * n)) - 1u) << base;
+  const int a1 = l % n, b1 = l / n;
+  const int off = (b1 - p + 1) * rs + (a1 - p + 1);
+  float gx[n], gy[n];
+#pragma unroll
+  for (int r = 0; r < n; r++) {
+    gx[r] = TB::g1(p, a1, r);
+    gy[r] = TB::g1(p, b1, r);
+  }
+  float ua[S], uj[S], d0[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    ua[c] = hi[c * cs];
+    uj[c] = hi[c * cs + off];
+    d0[c] = (hi[c * cs + off] - hi[c * cs]) + (lo[c * cs + off] - lo[c * cs]);
+  }
+  float Df[S], Dg[S];
+  PH::dflux2(PH::base(ua, ax, ay, gm1), d0, Df, Dg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
+  const typename PH::Base bj = PH::base(uj, ax, ay, gm1);
+  float Ff[S], Fg[S], Pf[S], Pg[S], del[n][S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    Ff[c] = Pf[c] = Df[c];
+    Fg[c] = Pg[c] = Dg[c];
+  }
+#pragma unroll
+  for (int rr = 0; rr < n; rr++)
+#pragma unroll
+    for (int c = 0; c < S; c++) del[rr][c] = 0.0f;
+#pragma unroll
+  for (int k = 2; k <= n; k++) {
+    float Ux[S], Uy[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < n; r++)
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Ux[c] = fmaf(gx[r], __shfl_sync(mask, Pf[c], base + b1 * n + r), Ux[c]);
+        Uy[c] = fmaf(gy[r], __shfl_sync(mask, Pg[c], base + r * n + a1), Uy[c]);
+      }
+    float U[S], af[S], ag[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      U[c] = -(lx * Ux[c]) - ly * Uy[c];
+      af[c] = ag[c] = 0.0f;
+    }
+#pragma unroll
+    for (int rr = 0; rr < n; rr++) {
+      if (rr == p - 1) continue;
+      const float cr = TB::taylor(p, rr, k - 1), wk = TB::gk(p, k - 1, rr);
+      float ef[S], eg[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) del[rr][c] = fmaf(cr, U[c], del[rr][c]);
+      PH::dflux2(bj, del[rr], ef, eg);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        af[c] = fmaf(wk, ef[c], af[c]);
+        ag[c] = fmaf(wk, eg[c], ag[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      Pf[c] = af[c];
+      Pg[c] = ag[c];
+      Ff[c] = fmaf(TB::invfact(k), af[c], Ff[c]);
+      Fg[c] = fmaf(TB::invfact(k), ag[c], Fg[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const float vF = TB::gh(p, a1) * Ff[c], vG = TB::gh(p, b1) * Fg[c];
+    float tF = 0.0f, tG = 0.0f;
+#pragma unroll
+    for (int r = 0; r < n; r++) {
+      tF += __shfl_sync(mask, vF, base + (p - 1) * n + r);
+      tG += __shfl_sync(mask, vG, base + r * n + (p - 1));
+    }
+    GFo[c] = tF;
+    GGo[c] = tG;
+  }
+}
+
+// FP64 FL-CAT2 in 2D (one lane): the 2D CAT2 fluxes of Eqs. 4.3-4.4 on the
+// 2 x 2 block at the anchor, blended with Rusanov by psi^1 of the row (F) or
+// the column (G) as in Eqs. 4.7-4.8.
+template <int FLUX>
+__device__ __forceinline__ void flcat2_2d_f64(const double *q, int cs, int rs, bool wantF, bool wantG,
+                                              double lx, double ly, double ax, double ay,
+                                              double gamma, int limiter_form, double *F, double *G) {
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  const double gm1 = gamma - 1.0;
+  double u00[S], u10[S], u01[S], u11[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    u00[c] = q[c * cs];
+    u10[c] = q[c * cs + 1];
+    u01[c] = q[c * cs + rs];
+    u11[c] = q[c * cs + rs + 1];
+  }
+  double f00[S], g00[S], f10[S], g10[S], f01[S], g01[S], f11[S], g11[S];
+  PH::flux2(u00, f00, g00, ax, ay, gm1);
+  PH::flux2(u10, f10, g10, ax, ay, gm1);
+  PH::flux2(u01, f01, g01, ax, ay, gm1);
+  PH::flux2(u11, f11, g11, ax, ay, gm1);
+  const int kind = 0;  // 2D scalar law here is linear transport
+  if (wantF) {
+    double a0[S], a1[S], t0[S], t1[S], tg[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      a0[c] = u00[c] + (-lx * (f10[c] - f00[c]) - ly * (g01[c] - g00[c]));
+      a1[c] = u10[c] + (-lx * (f10[c] - f00[c]) - ly * (g11[c] - g10[c]));
+    }
+    PH::flux2(a0, t0, tg, ax, ay, gm1);
+    PH::flux2(a1, t1, tg, ax, ay, gm1);
+    double sx0, sy0, sx1, sy1;
+    bool ok;
+    PH::speed2(u00, ax, ay, gamma, sx0, sy0, ok);
+    PH::speed2(u10, ax, ay, gamma, sx1, sy1, ok);
+    const double alpha = sx1 > sx0 ? sx1 : sx0;
+    const double w = psi1_line<S>(q, cs, 1, kind, limiter_form, ax);
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const double F1 = 0.25 * (t0[c] + t1[c] + f00[c] + f10[c]);
+      const double Flo = 0.5 * (f00[c] + f10[c]) - 0.5 * alpha * (u10[c] - u00[c]);
+      F[c] = w * F1 + (1.0 - w) * Flo;
+    }
+  }
+  if (wantG) {
+    double a0[S], a1[S], t0[S], t1[S], tf[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      a0[c] = u00[c] + (-lx * (f10[c] - f00[c]) - ly * (g01[c] - g00[c]));
+      a1[c] = u01[c] + (-lx * (f11[c] - f01[c]) - ly * (g01[c] - g00[c]));
+    }
+    PH::flux2(a0, tf, t0, ax, ay, gm1);
+    PH::flux2(a1, tf, t1, ax, ay, gm1);
+    double sx0, sy0, sx1, sy1;
+    bool ok;
+    PH::speed2(u00, ax, ay, gamma, sx0, sy0, ok);
+    PH::speed2(u01, ax, ay, gamma, sx1, sy1, ok);
+    const double alpha = sy1 > sy0 ? sy1 : sy0;
+    const double w = psi1_line<S>(q, cs, rs, kind, limiter_form, ay);
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const double G1 = 0.25 * (t0[c] + t1[c] + g00[c] + g01[c]);
+      const double Glo = 0.5 * (g00[c] + g01[c]) - 0.5 * alpha * (u01[c] - u00[c]);
+      G[c] = w * G1 + (1.0 - w) * Glo;
+    }
+  }
+}
+
+// FP32 FL-CAT2 in 2D, delta form about the anchor state a (one lane).
+template <int FLUX>
+__device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, const double *q64,
+                                              int cs, int rs, bool wantF, bool wantG, float lx,
+                                              float ly, float ax, float ay, float gamma, double axd,
+                                              double ayd, int limiter_form, float *GF, float *GG) {
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  const float gm1 = gamma - 1.0f;
+  float ua[S], d10[S], d01[S], d11[S], u10[S], u01[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const int o = c * cs;
+    ua[c] = hi[o];
+    u10[c] = hi[o + 1];
+    u01[c] = hi[o + rs];
+    d10[c] = (hi[o + 1] - hi[o]) + (lo[o + 1] - lo[o]);
+    d01[c] = (hi[o + rs] - hi[o]) + (lo[o + rs] - lo[o]);
+    d11[c] = (hi[o + rs + 1] - hi[o]) + (lo[o + rs + 1] - lo[o]);
+  }
+  const typename PH::Base B = PH::base(ua, ax, ay, gm1);
+  float Df10[S], Dg10[S], Df01[S], Dg01[S], Df11[S], Dg11[S];
+  PH::dflux2(B, d10, Df10, Dg10);
+  PH::dflux2(B, d01, Df01, Dg01);
+  PH::dflux2(B, d11, Df11, Dg11);
+  float U00[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) U00[c] = -lx * Df10[c] - ly * Dg01[c];
+  float e00f[S], e00g[S];
+  PH::dflux2(B, U00, e00f, e00g);
+  const int kind = 0;
+  if (wantF) {
+    float x1[S], ef[S], eg[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) x1[c] = d10[c] + (-lx * Df10[c] - ly * (Dg11[c] - Dg10[c]));
+    PH::dflux2(B, x1, ef, eg);  // f(u10 + U10) - f(u_a)
+    const float s0 = PH::fspeed(ua, ax, ay, gamma, 0), s1 = PH::fspeed(u10, ax, ay, gamma, 0);
+    const float alpha = s1 > s0 ? s1 : s0;
+    const float w = (float)psi1_line<S>(q64, cs, 1, kind, limiter_form, axd);
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      // F1 - f(a) = Df10/2 + (e00 + (ef - Df10))/4 ; Flo - f(a) = Df10/2 - alpha d10/2
+      const float G1 = 0.5f * Df10[c] + 0.25f * (e00f[c] + ef[c] - Df10[c]);
+      const float Glo = 0.5f * Df10[c] - 0.5f * alpha * d10[c];
+      GF[c] = fmaf(w, G1 - Glo, Glo);
+    }
+  }
+  if (wantG) {
+    float x1[S], ef[S], eg[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) x1[c] = d01[c] + (-lx * (Df11[c] - Df01[c]) - ly * Dg01[c]);
+    PH::dflux2(B, x1, ef, eg);  // g(u01 + U01) - g(u_a)
+    const float s0 = PH::fspeed(ua, ax, ay, gamma, 1), s1 = PH::fspeed(u01, ax, ay, gamma, 1);
+    const float alpha = s1 > s0 ? s1 : s0;
+    const float w = (float)psi1_line<S>(q64, cs, rs, kind, limiter_form, ayd);
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const float G1 = 0.5f * Dg01[c] + 0.25f * (e00g[c] + eg[c] - Dg01[c]);
+      const float Glo = 0.5f * Dg01[c] - 0.5f * alpha * d01[c];
+      GG[c] = fmaf(w, G1 - Glo, Glo);
+    }
+  }
+}
+
+// dt of a 2D step: CFL/2 min(dx / s^max_x, dy / s^max_y) (Sec. 5.5).
+__device__ double step_dt2(const Step2DArgs &a) {
+  double dt;
+  if (a.dt_fixed > 0.0) {
+    dt = a.dt_fixed;
+  } else {
+    const double sx = __longlong_as_double((long long)a.smax[a.slot * 2 + 0]);
+    const double sy = __longlong_as_double((long long)a.smax[a.slot * 2 + 1]);
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    if (!isfinite(sx) || !isfinite(sy) || !(sx > 0.0 || sy > 0.0)) {
+      if (blockIdx.x == 0 && blockIdx.y == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_BAD_DT);
+      dt = 0.0;
+    } else {
+      const double tx = sx > 0.0 ? __ddiv_rn(a.dx, sx) : inf;
+      const double ty = sy > 0.0 ? __ddiv_rn(a.dy, sy) : inf;
+      dt = __dmul_rn(a.cfl / 2.0, tx < ty ? tx : ty);
+    }
+  }
+  double t = 0.0;
+  if (a.tslot) {
+    t = a.tslot[a.slot];
+    if (a.t_end > 0.0) {
+      if (t >= a.t_end) dt = 0.0;
+      else if (dt > a.t_end - t) dt = a.t_end - t;
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    if (a.tslot) a.tslot[(a.slot + 1) % 3] = t + dt;
+    if (a.dt_out) *a.dt_out = dt;
+    const int z = (a.slot + 2) % 3;
+    a.smax[z * 2 + 0] = 0ull;
+    a.smax[z * 2 + 1] = 0ull;
+  }
+  return dt;
+}
+
+__device__ __forceinline__ long bc2(long g, long n, int bc) { return bc_index(g, n, bc); }
+
+template <int P, int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  using R = typename std::conditional<F32, float, double>::type;
+  __shared__ double tile[S][TW2][TW2];
+  __shared__ float thi[F32 ? S : 1][F32 ? TW2 : 1][F32 ? TW2 : 1];
+  __shared__ float tlo[F32 ? S : 1][F32 ? TW2 : 1][F32 ? TW2 : 1];
+  __shared__ R Fx[TXY][TXY + 1][S];
+  __shared__ R Gy[TXY + 1][TXY][S];
+  __shared__ double s_dt;
+  __shared__ double s_red[2][NT / 32];
+  const long NXl = a.NX, NYl = a.NY;
+  const long x0 = (long)blockIdx.x * TXY, y0 = (long)blockIdx.y * TXY;
+
+  if (threadIdx.x == 0) s_dt = step_dt2(a);
+  constexpr int CELLS = TW2 * TW2;
+  for (int q = threadIdx.x; q < S * CELLS; q += NT) {
+    const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW2, xx = rem - yy * TW2;
+    const long gx = bc2(x0 - GH2 + xx, NXl, a.bc), gy = bc2(y0 - GH2 + yy, NYl, a.bc);
+    const long gi = ((long)c * NYl + gy) * NXl + gx;
+    if constexpr (F32) {
+      const float *u = static_cast<const float *>(a.u_in);
+      const float h = u[gi], w = u[(long)S * NYl * NXl + gi];
+      thi[c][yy][xx] = h;
+      tlo[c][yy][xx] = w;
+      tile[c][yy][xx] = (double)h + (double)w;
+    } else {
+      tile[c][yy][xx] = static_cast<const double *>(a.u_in)[gi];
+    }
+  }
+  __syncthreads();
+  const double dt = s_dt;
+  const double lxd = dt / a.dx, lyd = dt / a.dy;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane >> 4, l = lane & 15, base = grp * 16;
+  const unsigned gmask = 0xffffu << base;
+  constexpr int CS = TW2 * TW2, RS = TW2;
+  constexpr int NPAIR = 2 * (P - 1) * S;
+
+  for (int round = 0; round < NA * NA / 16; round++) {
+    const int an = round * 16 + warp * 2 + grp;
+    const int ax = an % NA - 1, ay = an / NA - 1;  // anchor relative to (x0, y0)
+    const long gxa = x0 + ax, gya = y0 + ay;
+    const bool inside = gxa < NXl && gya < NYl;
+    const bool needF = inside && ay >= 0;
+    const bool needG = inside && ax >= 0;
+    const int tx = ax + GH2, ty = ay + GH2;
+    const double *q64 = &tile[0][ty][tx];
+    // --- dimension-by-dimension order selection -------------------------------
+    unsigned rej = 0;
+    if (P >= 2) {
+      for (int qq = l; qq < NPAIR; qq += 16) {
+        const int dir = qq / ((P - 1) * S), rem = qq - dir * ((P - 1) * S);
+        const int p = 2 + rem / S, c = rem - (rem / S) * S;
+        if (dir == 0 ? !needF : !needG) continue;
+        const double v = psi_p_comp(q64 + c * CS, dir == 0 ? 1 : RS, p, a.eps, a.fact_tau[p]);
+        const bool ok = (c == 0) ? (v >= a.thr) : !(v < a.thr);
+        if (!ok) rej |= 1u << (dir * (P - 1) + (p - 2));
+      }
+      rej = __reduce_or_sync(gmask, rej);
+    }
+    int px = 1, py = 1;
+    if (P >= 2) {
+      const unsigned all = (1u << (P - 1)) - 1u;
+      const unsigned accx = ~rej & all, accy = ~(rej >> (P - 1)) & all;
+      px = accx ? (32 - __clz(accx)) + 1 : 1;
+      py = accy ? (32 - __clz(accy)) + 1 : 1;
+    }
+    const bool blkF = needF && px >= 2, blkG = needG && py >= 2;
+    R F[S], G[S];
+    if (P >= 2 && (blkF || blkG)) {
+      if constexpr (P >= 2) {
+        if constexpr (F32) {
+          cat2d_f32<2, FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, l, base, (float)lxd,
+                             (float)lyd, (float)a.adv[0], (float)a.adv[1], (float)(a.gamma - 1.0), F, G);
+        } else {
+          cat2d_f64<2, FLUX>(q64, CS, RS, l, base, lxd, lyd, a.adv[0], a.adv[1], a.gamma - 1.0, F, G);
+        }
+      }
+    }
+    const bool flF = needF && !blkF, flG = needG && !blkG;
+    if (l == 0 && (flF || flG)) {
+      R F1[S], G1[S];
+      if constexpr (F32) {
+        flcat2_2d_f32<FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], q64, CS, RS, flF, flG, (float)lxd,
+                            (float)lyd, (float)a.adv[0], (float)a.adv[1], (float)a.gamma, a.adv[0],
+                            a.adv[1], a.limiter_form, F1, G1);
+      } else {
+        flcat2_2d_f64<FLUX>(q64, CS, RS, flF, flG, lxd, lyd, a.adv[0], a.adv[1], a.gamma,
+                            a.limiter_form, F1, G1);
+      }
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if (flF) F[c] = F1[c];
+        if (flG) G[c] = G1[c];
+      }
+    }
+    if (l == 0) {
+      if (needF) {
+#pragma unroll
+        for (int c = 0; c < S; c++) Fx[ay][ax + 1][c] = F[c];
+        if (a.ord_x && (ax >= 0 || gxa == -1)) a.ord_x[gya * (NXl + 1) + (gxa + 1)] = (int8_t)px;
+      }
+      if (needG) {
+#pragma unroll
+        for (int c = 0; c < S; c++) Gy[ay + 1][ax][c] = G[c];
+        if (a.ord_y && (ay >= 0 || gya == -1)) a.ord_y[(gya + 1) * NXl + gxa] = (int8_t)py;
+      }
+    }
+  }
+  __syncthreads();
+
+  // --- update and wave-speed epilogue ------------------------------------------
+  double mx = 0.0, my = 0.0;
+  bool bad = false;
+  for (int t = threadIdx.x; t < TXY * TXY; t += NT) {
+    const int cy = t / TXY, cx = t - cy * TXY;
+    const long gx = x0 + cx, gy = y0 + cy;
+    if (gx >= NXl || gy >= NYl) continue;
+    const int tx = cx + GH2, ty = cy + GH2;
+    double un[S];
+    if constexpr (F32) {
+      float uc[S], dlx[S], dly[S], Bx[S], By[S], junk[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        uc[c] = thi[c][ty][tx];
+        dlx[c] = (thi[c][ty][tx - 1] - thi[c][ty][tx]) + (tlo[c][ty][tx - 1] - tlo[c][ty][tx]);
+        dly[c] = (thi[c][ty - 1][tx] - thi[c][ty][tx]) + (tlo[c][ty - 1][tx] - tlo[c][ty][tx]);
+      }
+      const typename PH::Base B =
+          PH::base(uc, (float)a.adv[0], (float)a.adv[1], (float)(a.gamma - 1.0));
+      PH::dflux2(B, dlx, Bx, junk);  // f(u_{x-1,y}) - f(u)
+      PH::dflux2(B, dly, junk, By);  // g(u_{x,y-1}) - g(u)
+      float *uo = static_cast<float *>(a.u_out);
+      const float lx = (float)lxd, ly = (float)lyd;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        const float dx_ = __fmul_rn(lx, __fadd_rn(Bx[c], __fsub_rn(Fx[cy][cx][c], Fx[cy][cx + 1][c])));
+        const float dy_ = __fmul_rn(ly, __fadd_rn(By[c], __fsub_rn(Gy[cy][cx][c], Gy[cy + 1][cx][c])));
+        const float d = __fadd_rn(dx_, dy_);
+        const float h = thi[c][ty][tx], w = tlo[c][ty][tx];
+        const float s = __fadd_rn(h, d);
+        const float bp = __fsub_rn(s, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+        const float w2 = __fadd_rn(w, e);
+        const float hn = __fadd_rn(s, w2);
+        const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
+        const long gi = ((long)c * NYl + gy) * NXl + gx;
+        uo[gi] = hn;
+        uo[(long)S * NYl * NXl + gi] = ln;
+        un[c] = (double)hn + (double)ln;
+      }
+    } else {
+      double *uo = static_cast<double *>(a.u_out);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        un[c] = tile[c][ty][tx] + lxd * (Fx[cy][cx][c] - Fx[cy][cx + 1][c]) +
+                lyd * (Gy[cy][cx][c] - Gy[cy + 1][cx][c]);
+        uo[((long)c * NYl + gy) * NXl + gx] = un[c];
+      }
+    }
+    double sx, sy;
+    bool ok;
+    PH::speed2(un, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
+    bad |= !ok;
+    mx = fmax(mx, sx);
+    my = fmax(my, sy);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  if (lane == 0) {
+    s_red[0][warp] = mx;
+    s_red[1][warp] = my;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double vx = s_red[0][0], vy = s_red[1][0];
+    for (int w = 1; w < NT / 32; w++) {
+      vx = fmax(vx, s_red[0][w]);
+      vy = fmax(vy, s_red[1][w]);
+    }
+    const int z = (a.slot + 1) % 3;
+    atomic_max_pos(&a.smax[z * 2 + 0], vx);
+    atomic_max_pos(&a.smax[z * 2 + 1], vy);
+  }
+}
+
+template <int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_smax2d(const Step2DArgs a) {
+  constexpr int S = Phys2<FLUX>::S;
+  __shared__ double s_red[2][NT / 32];
+  const long NC = (long)a.NX * a.NY;
+  double mx = 0.0, my = 0.0;
+  bool bad = false;
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < NC; i += (long)gridDim.x * NT) {
+    double u[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      if constexpr (F32) {
+        const float *p = static_cast<const float *>(a.u_in);
+        u[c] = (double)p[c * NC + i] + (double)p[(S + c) * NC + i];
+      } else {
+        u[c] = static_cast<const double *>(a.u_in)[c * NC + i];
+      }
+    }
+    double sx, sy;
+    bool ok;
+    Phys2<FLUX>::speed2(u, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
+    mx = fmax(mx, sx);
+    my = fmax(my, sy);
+    bad |= !ok;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  if (lane == 0) {
+    s_red[0][warp] = mx;
+    s_red[1][warp] = my;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double vx = s_red[0][0], vy = s_red[1][0];
+    for (int w = 1; w < NT / 32; w++) {
+      vx = fmax(vx, s_red[0][w]);
+      vy = fmax(vy, s_red[1][w]);
+    }
+    atomic_max_pos(&a.smax[a.slot * 2 + 0], vx);
+    atomic_max_pos(&a.smax[a.slot * 2 + 1], vy);
+    if (blockIdx.x == 0 && a.tslot) a.tslot[a.slot] = 0.0;
+  }
+}
+
+template <int P, int FLUX, bool F32>
+int launch2(const Step2DArgs &a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.NX + TXY - 1) / TXY), (unsigned)((a.NY + TXY - 1) / TXY));
+  k_step2d<P, FLUX, F32><<<grid, NT, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <int FLUX, bool F32>
+int launch2_p(int P, const Step2DArgs &a, cudaStream_t st) {
+  if (P == 1) return launch2<1, FLUX, F32>(a, st);
+  if (P == 2) return launch2<2, FLUX, F32>(a, st);
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int acat_launch_step2d(int P, int flux, int prec, const Step2DArgs &a, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool f32 = prec == ACAT_PREC_F32;
+  if (flux == ACAT_FLUX_EULER2D)
+    return f32 ? launch2_p<ACAT_FLUX_EULER2D, true>(P, a, st) : launch2_p<ACAT_FLUX_EULER2D, false>(P, a, st);
+  if (flux == ACAT_FLUX_LINEAR)
+    return f32 ? launch2_p<ACAT_FLUX_LINEAR, true>(P, a, st) : launch2_p<ACAT_FLUX_LINEAR, false>(P, a, st);
+  return (int)cudaErrorInvalidValue;
+}
+
+int acat_launch_smax2d(int flux, int prec, const Step2DArgs &a, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long NC = (long)a.NX * a.NY;
+  const long blocks = (NC + NT - 1) / NT;
+  const unsigned grid = (unsigned)(blocks < 2048 ? blocks : 2048);
+  const bool f32 = prec == ACAT_PREC_F32;
+  if (flux == ACAT_FLUX_EULER2D) {
+    if (f32) k_smax2d<ACAT_FLUX_EULER2D, true><<<grid, NT, 0, st>>>(a);
+    else k_smax2d<ACAT_FLUX_EULER2D, false><<<grid, NT, 0, st>>>(a);
+  } else if (flux == ACAT_FLUX_LINEAR) {
+    if (f32) k_smax2d<ACAT_FLUX_LINEAR, true><<<grid, NT, 0, st>>>(a);
+    else k_smax2d<ACAT_FLUX_LINEAR, false><<<grid, NT, 0, st>>>(a);
+  } else {
+    return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int acat_upload_tables_2d(const AcatTables *T) { return (int)cudaMemcpyToSymbol(c_tab, T, sizeof *T); }

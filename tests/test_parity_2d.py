@@ -1,0 +1,173 @@
+"""Parity of the CUDA 2D step (Sec. 4) with the CPU oracle.
+
+FP64: order codes of both directions bit-exact, states within 1e-12 of
+max|u| per step (teacher-forced over several steps). FP32 (delta form on the
+compensated state): same order codes from the same state value, states within
+1e-7 of max|u| per step.
+"""
+import numpy as np
+import pytest
+
+from paper_2007_01416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_2007_01416_gb300 import acat, build
+    build.build()
+    O.build()
+    return torch, O, acat
+
+
+def _step2(env, ctx, u_np, nx, ny, dt=-1.0):
+    torch, O, acat = env
+    u = torch.from_numpy(np.ascontiguousarray(u_np)).cuda()
+    out = torch.empty_like(u)
+    dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+    orders = torch.zeros(ny * (nx + 1) + (ny + 1) * nx, dtype=torch.int8, device="cuda")
+    ctx.acat_step(u, out, dt, None, dtv, orders)
+    torch.cuda.synchronize()
+    o = orders.cpu().numpy()
+    ox = o[:ny * (nx + 1)].reshape(ny, nx + 1)
+    oy = o[ny * (nx + 1):].reshape(ny + 1, nx)
+    return out.cpu().numpy(), float(dtv.item()), ox, oy
+
+
+def _transport(nx, ny, P, bc):
+    x = W.centres(nx, 0, 1)[None, :]
+    y = W.centres(ny, 0, 1)[:, None]
+    u = (np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.5 * (x + 0 * y > 0.55))[None]
+    c = W.Case("transport2d", W.LINEAR, P, nx, ny, bc, 0.5, 0, 1, 0, 1, u, 1, adv=(0.7, -0.4))
+    return c
+
+
+CASES = [
+    ("lax_liu_4", 2, 33, 30, 1), ("lax_liu_6", 2, 40, 16, 1), ("lax_liu_8", 1, 31, 31, 1),
+    ("quadrants", 2, 47, 44, 1), ("quadrants", 2, 32, 32, 0), ("quadrants", 1, 20, 23, 0),
+    ("transport", 2, 45, 38, 0), ("transport", 1, 30, 17, 1), ("quadrants", 2, 8, 9, 1),
+]
+
+
+def _case(kind, P, nx, ny, bc, seed=0):
+    if kind.startswith("lax_liu"):
+        c = W.lax_liu(int(kind.split("_")[-1]), nx, P)
+        if ny != nx:
+            c = W._quadrants(c.name, W.LAX_LIU[int(kind.split("_")[-1])], nx, ny, P, 1, c.cfl)
+    elif kind == "quadrants":
+        c = W.euler2d_quadrants(n=nx, ny=ny, seed=seed, P=P)
+    else:
+        c = _transport(nx, ny, P, bc)
+    c.bc = bc
+    return c
+
+
+@pytest.mark.parametrize("kind,P,nx,ny,bc", CASES)
+def test_single_step_2d(env, kind, P, nx, ny, bc):
+    torch, O, acat = env
+    c = _case(kind, P, nx, ny, bc)
+    kw = c.problem_kwargs()
+    with acat.Context(**kw) as ctx:
+        out, dt, ox, oy = _step2(env, ctx, c.u0, nx, ny)
+        assert ctx.acat_status() == 0
+    pr = O.Problem(**kw)
+    assert dt == O.dt_cfl(pr, c.u0)
+    ref, _, rox, roy = O.step_2d(pr, c.u0, dt)
+    assert np.array_equal(ox, rox), np.argwhere(ox != rox)[:5]
+    assert np.array_equal(oy, roy), np.argwhere(oy != roy)[:5]
+    err = np.abs(out - ref).max() / max(1.0, np.abs(ref).max())
+    assert err < 1e-12, err
+
+
+def test_teacher_forced_2d(env):
+    torch, O, acat = env
+    c = W.euler2d_quadrants(n=40, ny=36, seed=3, P=2)
+    kw = c.problem_kwargs()
+    pr = O.Problem(**kw)
+    u = c.u0.copy()
+    worst = 0.0
+    with acat.Context(**kw) as ctx:
+        for n in range(25):
+            out, dt, ox, oy = _step2(env, ctx, u, c.nx, c.ny)
+            ref, _, rox, roy = O.step_2d(pr, u, dt)
+            assert np.array_equal(ox, rox) and np.array_equal(oy, roy), n
+            worst = max(worst, np.abs(out - ref).max() / np.abs(ref).max())
+            u = out
+    assert worst < 1e-12, worst
+
+
+def test_run_2d_matches_steps_and_conserves(env):
+    torch, O, acat = env
+    c = _transport(64, 48, 2, 0)
+    kw = c.problem_kwargs()
+    with acat.Context(**kw) as ctx:
+        u = torch.from_numpy(c.u0.copy()).cuda()
+        ctx.acat_run(u, 53)
+        v = torch.from_numpy(c.u0.copy()).cuda()
+        w = torch.empty_like(v)
+        for _ in range(53):
+            ctx.acat_step(v, w)
+            v, w = w, v
+        torch.cuda.synchronize()
+        assert torch.equal(u, v)
+        s0, s1 = float(c.u0.sum()), float(u.sum().item())
+        assert abs(s1 - s0) < 1e-11 * np.abs(c.u0).sum()
+
+
+@pytest.mark.parametrize("kind,P,nx,ny,bc", [("quadrants", 2, 47, 44, 1), ("lax_liu_8", 2, 40, 40, 1),
+                                             ("transport", 2, 45, 38, 0), ("quadrants", 1, 20, 23, 0)])
+def test_single_step_2d_f32(env, kind, P, nx, ny, bc):
+    torch, O, acat = env
+    c = _case(kind, P, nx, ny, bc, seed=5)
+    kw = c.problem_kwargs()
+    pair = acat.to_pair(c.u0)
+    xval = acat.from_pair(pair)
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        out, dt, ox, oy = _step2(env, ctx, pair, nx, ny)
+        assert ctx.acat_status() == 0
+    pr = O.Problem(**kw)
+    assert dt == O.dt_cfl(pr, xval)
+    ref, _, rox, roy = O.step_2d(pr, xval, dt)
+    assert np.array_equal(ox, rox) and np.array_equal(oy, roy)
+    err = np.abs(acat.from_pair(out) - ref).max() / max(1.0, np.abs(ref).max())
+    assert err < 1e-7, err
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_size_2d_sampled(env, prec):
+    """2D Euler P=2, 4096 x 4096, transmissive, CFL 0.4, in the launch
+    configuration of the benchmark: after 3 GPU steps, one more GPU step is
+    compared with the oracle's update of 256 sampled cells (and the four
+    corners) from the same state and dt."""
+    torch, O, acat = env
+    c = W.euler2d_quadrants(n=4096, seed=0, P=2)
+    kw = c.problem_kwargs()
+    pr = O.Problem(**kw)
+    f32 = prec == "f32"
+    with acat.Context(**kw, precision=acat.PREC_F32 if f32 else acat.PREC_F64) as ctx:
+        host = acat.to_pair(c.u0) if f32 else c.u0
+        u = torch.from_numpy(host).cuda()
+        ctx.acat_run(u, 3)
+        out = torch.empty_like(u)
+        dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.acat_step(u, out, -1.0, None, dtv, None)
+        torch.cuda.synchronize()
+        assert ctx.acat_status() == 0
+        un = u.cpu().numpy()
+        got = out.cpu().numpy()
+    if f32:
+        un, got = acat.from_pair(un), acat.from_pair(got)
+    dt = float(dtv.item())
+    assert dt == O.dt_cfl(pr, un)
+    rng = np.random.default_rng(1)
+    cx = np.r_[0, 4095, 0, 4095, 2047, 2048, rng.integers(0, 4096, 250)]
+    cy = np.r_[0, 0, 4095, 4095, 2047, 2048, rng.integers(0, 4096, 250)]
+    ref = O.step_2d_cells(pr, un, dt, cx, cy)
+    gpu = got[:, cy, cx].T
+    err = np.abs(gpu - ref).max() / np.abs(un).max()
+    assert err < (1e-7 if f32 else 1e-12), err

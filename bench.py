@@ -230,6 +230,47 @@ def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_c
     return res
 
 
+def measure_2d(torch, acat, W, flops, n, prec, steps, K, flush, peak):
+    """2D Euler four-quadrant workload (P = 2, transmissive, CFL 0.4)."""
+    c = W.euler2d_quadrants(n=n, seed=SEED, P=2, steps=steps, cfl=CFL)
+    ctx = acat.Context(**c.problem_kwargs(), precision=prec)
+    host = acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0
+    u0 = torch.from_numpy(host).cuda()
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    u.copy_(u0)
+    ctx.acat_run(u, min(steps, 6))  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        e0.record(stream)
+        ctx.acat_run(u, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    assert ctx.acat_status() == 0
+    # order mix at the end of the run (outside timing)
+    orders = torch.zeros(n * (n + 1) * 2, dtype=torch.int8, device="cuda")
+    tmp = torch.empty_like(u)
+    ctx.acat_step(u, tmp, -1.0, None, None, orders)
+    torch.cuda.synchronize()
+    o = orders.cpu().numpy()
+    ox = o[:n * (n + 1)].reshape(n, n + 1)
+    oy = o[n * (n + 1):].reshape(n + 1, n)
+    blk = int(((ox[:, 1:] == 2) | (oy[1:, :] == 2)).sum())
+    flc = int((ox == 1).sum() + (oy == 1).sum())
+    fl = flops.step_flops_2d(blk, flc, (n + 1) * (n + 1), 2, W.EULER2D, n * n)
+    t = sum(ms) / K
+    ctx.close()
+    return {"value": n * n * steps / (t * 1e-3), "unit": UNIT, "ms_per_run": t, "steps": steps,
+            "n": n, "roofline_frac": fl / (t / steps * 1e-3) / peak,
+            "anchors_with_block": round(blk / (n * n), 4),
+            "flcat2_directions": round(flc / (2 * n * (n + 1)), 4)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -315,6 +356,15 @@ def run_ours(args):
                 "linf_rel_vs_f64": float(diff.max() / u64.abs().max()),
                 "order_mix": v["order_mix"]}
             c64.close()
+        # 2D Euler, P = 2: 4096^2 x 500 steps in FP32 (the 2D configuration), and the
+        # plain FP64 step at 1024^2 x 20 steps for the FP32 / FP64 ratio
+        v32 = measure_2d(torch, acat, W, flops, 4096, acat.PREC_F32, 500, 2, flush, peak32)
+        v64 = measure_2d(torch, acat, W, flops, 1024, acat.PREC_F64, 20, 2, flush, peak64)
+        v32["roofline_peak"] = "fp32"
+        v64["roofline_peak"] = "fp64"
+        v32["speedup_vs_f64_per_cell_update"] = v32["value"] / v64["value"]
+        variants["2d_euler_P2_4096_f32"] = v32
+        variants["2d_euler_P2_1024_f64"] = v64
 
     if rank != 0:
         return 0

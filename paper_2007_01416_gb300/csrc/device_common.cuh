@@ -100,6 +100,128 @@ __device__ __forceinline__ double superbee(double r) {
   return m > 0.0 ? m : 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// Filtered order decision. psi^p >= thr (thr < 1) holds exactly when
+// I (1 - thr) >= thr tau, i.e. I >= r tau with r = thr / (1 - thr). The test is
+// first evaluated in float from the first differences d_k = u_{k+1} - u_k,
+// k = -p+1..p-1, each with an absolute error bound e_k:
+//   I_L, I_R, I from the d_k (relative error below 4e-6),
+//   Delta^{2p-1} u = Delta^{2p-2} d by repeated differencing, its bound
+//   propagated as e' = e_{k+1} + e_k + 2^-24 |t'|,
+// and the decision is returned only when the bounds leave no doubt (with a
+// further relative margin of 1e-5, far above the rounding of a literal FP64
+// evaluation). Otherwise the caller evaluates psi^p literally in FP64. Returns
+// 1 (accept), 0 (reject) or -1 (undecided). The same decision as the literal
+// FP64 evaluation results in every case.
+// ---------------------------------------------------------------------------
+template <int p>
+__device__ __forceinline__ int psi_filter(const float *d, const float *e, float eps, float r,
+                                          float fact) {
+  constexpr int n = 2 * p - 1;
+  float IL = 0.0f, IR = 0.0f;
+#pragma unroll
+  for (int k = 0; k < p - 1; k++) IL = fmaf(d[k], d[k], IL);
+#pragma unroll
+  for (int k = p; k < n; k++) IR = fmaf(d[k], d[k], IR);
+  IL += eps;
+  IR += eps;
+  if (!(IL > 1e-30f && IR > 1e-30f) || !(IL < 1e30f && IR < 1e30f)) return -1;
+  const float I = IL * IR / (IL + IR);
+  float t[n], b[n];
+#pragma unroll
+  for (int k = 0; k < n; k++) {
+    t[k] = d[k];
+    b[k] = e[k];
+  }
+#pragma unroll
+  for (int lev = 1; lev < n; lev++)
+#pragma unroll
+    for (int k = 0; k < n - lev; k++) {
+      t[k] = t[k + 1] - t[k];
+      b[k] = (b[k + 1] + b[k]) + 5.97e-8f * fabsf(t[k]) + 1e-44f;
+    }
+  const float S = fabsf(t[0]), eS = 1.01f * b[0];
+  const float Dhi = (S + eS) * fact * 1.0000005f;
+  const float Dlo = fmaxf(S - eS, 0.0f) * fact * 0.9999995f;
+  const float lo = I * (1.0f - 4e-6f), hi = I * (1.0f + 4e-6f);
+  if (lo > r * (Dhi * Dhi) * 1.00001f) return 1;
+  if (hi < r * (Dlo * Dlo) * 0.99999f) return 0;
+  return -1;
+}
+
+// Float constants of the filter.
+struct FiltConst {
+  float eps, r;
+  float fact[ACAT_MAXP + 1];
+};
+__device__ __forceinline__ FiltConst filt_const(double eps, double thr, const double *fact) {
+  FiltConst f;
+  f.eps = (float)eps;
+  f.r = (float)(thr / (1.0 - thr));
+#pragma unroll
+  for (int q = 0; q <= ACAT_MAXP; q++) f.fact[q] = (float)fact[q];
+  return f;
+}
+
+// Admissibility of order p for one component of an FP64 state; values at
+// q[j*st], j = -p+1..p. `first`: the first component (a NaN there rejects, a
+// NaN in a later component is ignored, as in a minimum taken from the first
+// component).
+template <int p>
+__device__ __forceinline__ bool admit64(const double *q, int st, bool first, const FiltConst &F,
+                                        double eps, double thr, double fact) {
+  float d[2 * p - 1], e[2 * p - 1];
+#pragma unroll
+  for (int k = 0; k < 2 * p - 1; k++) {
+    const int j = k - p + 1;
+    d[k] = (float)__dsub_rn(q[(j + 1) * st], q[j * st]);
+    e[k] = 6.0e-8f * fabsf(d[k]) + 1e-44f;
+  }
+  const int dec = psi_filter<p>(d, e, F.eps, F.r, F.fact[p]);
+  if (dec >= 0) return dec == 1;
+  const double v = psi_p_comp(q, st, p, eps, fact);
+  return first ? (v >= thr) : !(v < thr);
+}
+
+// The same for a compensated float state hi + lo (q64 holds hi + lo in FP64
+// for the literal fallback).
+template <int p>
+__device__ __forceinline__ bool admit32(const float *hi, const float *lo, const double *q64, int st,
+                                        bool first, const FiltConst &F, double eps, double thr,
+                                        double fact) {
+  float d[2 * p - 1], e[2 * p - 1];
+#pragma unroll
+  for (int k = 0; k < 2 * p - 1; k++) {
+    const int j = k - p + 1;
+    const float h1 = hi[(j + 1) * st], h0 = hi[j * st];
+    d[k] = (h1 - h0) + (lo[(j + 1) * st] - lo[j * st]);
+    e[k] = 1.2e-7f * fabsf(d[k]) + 1.5e-14f * (fabsf(h1) + fabsf(h0)) + 1e-44f;
+  }
+  const int dec = psi_filter<p>(d, e, F.eps, F.r, F.fact[p]);
+  if (dec >= 0) return dec == 1;
+  const double v = psi_p_comp(q64, st, p, eps, fact);
+  return first ? (v >= thr) : !(v < thr);
+}
+
+// Dispatch on a runtime p in 2..4 (lanes of one warp may hold different p).
+__device__ __forceinline__ bool admit64_p(int p, const double *q, int st, bool first,
+                                          const FiltConst &F, double eps, double thr, double fact) {
+  switch (p) {
+  case 2: return admit64<2>(q, st, first, F, eps, thr, fact);
+  case 3: return admit64<3>(q, st, first, F, eps, thr, fact);
+  default: return admit64<4>(q, st, first, F, eps, thr, fact);
+  }
+}
+__device__ __forceinline__ bool admit32_p(int p, const float *hi, const float *lo, const double *q64,
+                                          int st, bool first, const FiltConst &F, double eps,
+                                          double thr, double fact) {
+  switch (p) {
+  case 2: return admit32<2>(hi, lo, q64, st, first, F, eps, thr, fact);
+  case 3: return admit32<3>(hi, lo, q64, st, first, F, eps, thr, fact);
+  default: return admit32<4>(hi, lo, q64, st, first, F, eps, thr, fact);
+  }
+}
+
 // psi^1 (Eqs. 3.5-3.7, superbee) at the interface between q[0] (cell i) and
 // q[st]: components `cs` apart, cells `st` apart. Scalar laws (S == 1; kind
 // 0: linear transport with speed `adv`, kind 1: Burgers) use the Roe-speed

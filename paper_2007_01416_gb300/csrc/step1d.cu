@@ -450,9 +450,11 @@ struct Tiling {
 // psi >= thr; as in a literal minimum over components taken from the first
 // component, a NaN in the first component rejects p and a NaN elsewhere is
 // ignored. Must be called by all 32 lanes.
-template <int P, int S>
-__device__ __forceinline__ int select_order(const double *t0, int cs, int l, int grp, bool active,
-                                            bool valid, double eps, double thr, const double *fact) {
+template <int P, int S, bool F32>
+__device__ __forceinline__ int select_order(const double *t0, const float *h0, const float *l0, int cs,
+                                            int l, int grp, bool active, bool valid,
+                                            const FiltConst &FC, double eps, double thr,
+                                            const double *fact) {
   using TL = Tiling<P>;
   if (P < 2) return 1;
   constexpr int NPAIR = (P - 1) * S;
@@ -460,16 +462,17 @@ __device__ __forceinline__ int select_order(const double *t0, int cs, int l, int
   if (active) {
     for (int q = l; q < NPAIR; q += TL::L) {
       const int p = 2 + q / S, c = q - (q / S) * S;
-      const double v = psi_p_comp(t0 + c * cs, 1, p, eps, fact[p]);
-      const bool ok = (c == 0) ? (v >= thr) : !(v < thr);
+      bool ok;
+      if constexpr (F32)
+        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
+      else
+        ok = admit64_p(p, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
       if (!ok) rej |= 1u << (p - 2);
     }
   }
-  const int lane = threadIdx.x & 31;
   constexpr unsigned spare = (TL::GPW * TL::L >= 32) ? 0u : (0xffffffffu << (TL::GPW * TL::L));
   const unsigned gmask = valid ? (((1u << TL::L) - 1u) << (grp * TL::L)) : spare;
   rej = __reduce_or_sync(gmask, rej);
-  (void)lane;
   const unsigned accept = ~rej & ((1u << (P - 1)) - 1u);
   return accept ? (32 - __clz(accept)) + 1 : 1;
 }
@@ -505,8 +508,9 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
   const bool active = valid && m <= N;
   const int ic = il - 1 + TL::GH;       // tile index of cell m-1
 
-  const int ps = select_order<P, S>(&tile[0][valid ? ic : 0], TL::TW, l, grp, active, valid, a.eps,
-                                    a.thr, a.fact_tau);
+  const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
+  const int ps = select_order<P, S, false>(&tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l, grp,
+                                           active, valid, FC, a.eps, a.thr, a.fact_tau);
 
   double F[S];
   const int base = grp * TL::L;
@@ -595,8 +599,10 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
   const bool active = valid && m <= N;
   const int ic = il - 1 + TL::GH;
 
-  const int ps = select_order<P, S>(&tile[0][valid ? ic : 0], TL::TW, l, grp, active, valid, a.eps,
-                                    a.thr, a.fact_tau);
+  const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
+  const int icv = valid ? ic : 0;
+  const int ps = select_order<P, S, true>(&tile[0][icv], &thi[0][icv], &tlo[0][icv], TL::TW, l, grp,
+                                          active, valid, FC, a.eps, a.thr, a.fact_tau);
 
   float G[S];
   const int base = grp * TL::L;

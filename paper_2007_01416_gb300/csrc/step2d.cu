@@ -533,6 +533,7 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
   const unsigned gmask = 0xffffu << base;
   constexpr int CS = TW2 * TW2, RS = TW2;
   constexpr int NPAIR = 2 * (P - 1) * S;
+  const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
 
   for (int round = 0; round < NA * NA / 16; round++) {
     const int an = round * 16 + warp * 2 + grp;
@@ -550,8 +551,12 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
         const int dir = qq / ((P - 1) * S), rem = qq - dir * ((P - 1) * S);
         const int p = 2 + rem / S, c = rem - (rem / S) * S;
         if (dir == 0 ? !needF : !needG) continue;
-        const double v = psi_p_comp(q64 + c * CS, dir == 0 ? 1 : RS, p, a.eps, a.fact_tau[p]);
-        const bool ok = (c == 0) ? (v >= a.thr) : !(v < a.thr);
+        bool ok;
+        if constexpr (F32)
+          ok = admit32_p(p, &thi[c][ty][tx], &tlo[c][ty][tx], q64 + c * CS, dir == 0 ? 1 : RS, c == 0,
+                         FC, a.eps, a.thr, a.fact_tau[p]);
+        else
+          ok = admit64_p(p, q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau[p]);
         if (!ok) rej |= 1u << (dir * (P - 1) + (p - 2));
       }
       rej = __reduce_or_sync(gmask, rej);

@@ -56,6 +56,32 @@ def step_flops_1d(order_hist: dict, P: int, flux: int, cells: int) -> float:
     return f
 
 
+def cat2d_flops(p: int, flux: int) -> int:
+    """2D block recursion on the 2p x 2p block (Eqs. 4.5-4.6), F and G
+    together: per node the x- and y-derivative sums (n terms each), the
+    Taylor update, the f/g pair at the n-1 levels r != 0 and both time sums."""
+    n, S, phi = 2 * p, NVARS[flux], PHI[3] if flux == 3 else 2 * PHI[0]
+    nodes = n * n
+    per_k = nodes * (2 * 2 * n * S + 2 * S) + nodes * 2 * S \
+        + nodes * (n - 1) * (2 * S + phi + 4 * S) + nodes * 4 * S
+    return nodes * phi + (n - 1) * per_k + 2 * 2 * n * S
+
+
+def flcat2_2d_flops(flux: int) -> int:
+    S, phi = NVARS[flux], PHI[3] if flux == 3 else 2 * PHI[0]
+    return 6 * phi + 40 * S + 30
+
+
+def step_flops_2d(blocks: int, flcat: int, anchors: int, P: int, flux: int, cells: int) -> float:
+    """blocks: block recursions run (one per anchor whose directions select
+    p = 2; two only when both select different p >= 2), flcat: directions
+    on FL-CAT2, anchors: both indicator lines per anchor."""
+    S = NVARS[flux]
+    ind = 2 * sum(S * (6 * (p - 1) + 2 + 3 + 4 * p + 2 + 2) for p in range(2, P + 1))
+    return blocks * cat2d_flops(P, flux) + flcat * flcat2_2d_flops(flux) + anchors * ind \
+        + cells * (5 * S + 14)
+
+
 def state_bytes_1d(cells: int, flux: int, prec: int = 0) -> int:
     """Compulsory HBM traffic of one step: read and write the state once
     (FP64, or the FP32 hi/lo pair: 8 bytes per value either way)."""

@@ -110,6 +110,19 @@ void acat_default_params(acat_params *p);
  * 1..4, 2D with P > 2 or non-Euler/linear flux), UNSUPPORTED, NOMEM, CUDA. */
 int acat_create(const acat_params *p, acat_ctx **out);
 
+/* A batch of n_inst independent 1D problems of ragged sizes n_per_inst[b]
+ * (host array; each >= 2 max(P, 2)), all with the parameters *p (p->nx is
+ * ignored) and each on the whole domain [x0, x1] with its own dx. The state
+ * is the concatenation along the cell index, u[c][M] with M = sum n_b and
+ * instance b at cells off_b = n_0 + ... + n_{b-1} (FP32: hi[c][M] then
+ * lo[c][M]). Every step advances all instances in one persistent launch,
+ * each with its own CFL dt reduced on the device (Eq. 2.12 per instance).
+ * With a batched ctx: acat_step's dt_dev receives n_inst values and
+ * orders_dev M + n_inst codes (instance b at off_b + b); acat_run's t_dev and
+ * acat_run_host's t_host receive n_inst times. Errors as acat_create, plus
+ * INVALID_ARG for a 2D problem or a too small instance. */
+int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_inst, acat_ctx **out);
+
 /* Frees every device and host resource of ctx (synchronises first). */
 int acat_destroy(acat_ctx *ctx);
 

@@ -51,12 +51,13 @@ def lib() -> ctypes.CDLL:
         L.acat_default_params.argtypes = [pp]
         L.acat_default_params.restype = None
         L.acat_create.argtypes = [pp, ctypes.POINTER(vp)]
+        L.acat_create_batched.argtypes = [pp, i, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vp)]
         L.acat_destroy.argtypes = [vp]
         L.acat_state_bytes.argtypes = [vp]
         L.acat_state_bytes.restype = ctypes.c_int64
         L.acat_step.argtypes = [vp, vp, vp, d, vp, vp, vp]
         L.acat_run.argtypes = [vp, vp, i, d, vp, vp]
-        L.acat_run_host.argtypes = [vp, vp, vp, i, d, vp, vp]
+        L.acat_run_host.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(ctypes.c_double)]
         L.acat_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint)]
         L.acat_clear_status.argtypes = [vp]
         L.acat_strerror.argtypes = [i]
@@ -150,10 +151,19 @@ class Context:
     """An acat_ctx: one problem (flux, P, grid, BC, precision) on the current
     device. Methods mirror the C entry points."""
 
-    def __init__(self, params: acat_params | None = None, **kw):
+    def __init__(self, params: acat_params | None = None, sizes=None, **kw):
+        """sizes: instance sizes for a batch of independent 1D problems
+        (acat_create_batched); None for a single problem (acat_create)."""
         self.params = params if params is not None else make_params(**kw)
         h = ctypes.c_void_p()
-        _check(lib().acat_create(ctypes.byref(self.params), ctypes.byref(h)), "acat_create")
+        self.n_inst = 0
+        if sizes is None:
+            _check(lib().acat_create(ctypes.byref(self.params), ctypes.byref(h)), "acat_create")
+        else:
+            arr = (ctypes.c_int32 * len(sizes))(*[int(v) for v in sizes])
+            _check(lib().acat_create_batched(ctypes.byref(self.params), len(sizes), arr,
+                                             ctypes.byref(h)), "acat_create_batched")
+            self.n_inst = len(sizes)
         self._h = h
 
     @property
@@ -173,11 +183,11 @@ class Context:
 
     def acat_run_host(self, u_host_in, u_host_out, nsteps: int, t_end: float = -1.0,
                       stream=None) -> float:
-        t = ctypes.c_double(0.0)
+        t = (ctypes.c_double * max(1, self.n_inst))()
         _check(lib().acat_run_host(self._h, _ptr(u_host_in), _ptr(u_host_out), int(nsteps),
-                                   float(t_end), _stream(stream), ctypes.byref(t)),
+                                   float(t_end), _stream(stream), t),
                "acat_run_host")
-        return t.value
+        return list(t) if self.n_inst else t[0]
 
     def acat_status(self) -> int:
         f = ctypes.c_uint(0)

@@ -48,6 +48,30 @@ struct Step1DArgs {
   unsigned *status;           // sticky status bits
 };
 
+// Work description of a batch of independent 1D instances (ragged sizes),
+// concatenated along the cell index: u[c][M] with instance b at cells
+// offs[b]..offs[b+1]-1.
+struct TileRef {
+  int b;     // instance
+  int tile;  // tile index within the instance (first cell tile * T)
+};
+struct BatchArgs {
+  const long long *offs;      // B+1 cell offsets
+  const TileRef *tiles;       // work list
+  long long ntiles;
+  int B;
+  long long M;                // total cells (component stride)
+  double xlen;                // x1 - x0 (each instance spans the domain)
+  unsigned long long *smax;   // 3 x B wave-speed slots
+  double *t;                  // 3 x B time slots
+  double *dt_out;             // B (nullable)
+  int8_t *orders;             // M + B order codes (nullable), instance b at offs[b] + b
+};
+
+int acat_launch_batch1d(int P, int flux, int prec, const Step1DArgs &a, const BatchArgs &bt,
+                        void *stream);
+int acat_launch_smax_batch(int flux, int prec, const Step1DArgs &a, const BatchArgs &bt, void *stream);
+
 // Arguments of one 2D step launch (passed by value). State u[c][y][x].
 struct Step2DArgs {
   const void *u_in;

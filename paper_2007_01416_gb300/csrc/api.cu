@@ -30,6 +30,14 @@ struct acat_ctx {
   double chain_t_end = 0.0;
   double fact_tau[ACAT_MAXP + 1] = {0};  // (2p-1)! or 1 (tau_factorial)
   int64_t launches = 0;
+  // batch of independent 1D instances (acat_create_batched)
+  int batched = 0;
+  int B = 0;
+  long long *d_offs = nullptr;
+  TileRef *d_tiles = nullptr;
+  long long ntiles = 0;
+  unsigned long long *d_smaxb = nullptr;  // 3 x B
+  double *d_tb = nullptr;                 // 3 x B
 };
 
 namespace {
@@ -125,8 +133,36 @@ int launch_step(acat_ctx *c, const Step1DArgs &a, cudaStream_t st) {
   return e ? ACAT_ERR_CUDA : ACAT_OK;
 }
 
+BatchArgs batch_args(acat_ctx *c) {
+  BatchArgs bt;
+  std::memset(&bt, 0, sizeof bt);
+  bt.offs = c->d_offs;
+  bt.tiles = c->d_tiles;
+  bt.ntiles = c->ntiles;
+  bt.B = c->B;
+  bt.M = c->cells;
+  bt.xlen = c->p.x1 - c->p.x0;
+  bt.smax = c->d_smaxb;
+  bt.t = c->d_tb;
+  return bt;
+}
+
 // Steps n..n+count-1 of a run on (u, work), dt slots n % 3.
 int issue_steps(acat_ctx *c, void *u, long n, int count, double t_end, cudaStream_t st) {
+  if (c->batched) {
+    Step1DArgs a = base_args(c);
+    a.t_end = t_end;
+    BatchArgs bt = batch_args(c);
+    for (int k = 0; k < count; k++, n++) {
+      a.u_in = (n % 2 == 0) ? u : c->d_work;
+      a.u_out = (n % 2 == 0) ? c->d_work : u;
+      a.slot = (int)(n % 3);
+      int e = acat_launch_batch1d(c->p.P, c->p.flux, c->p.precision, a, bt, st);
+      c->launches++;
+      if (e) return ACAT_ERR_CUDA;
+    }
+    return ACAT_OK;
+  }
   if (c->dim == 2) {
     Step2DArgs a = base_args2(c);
     a.t_end = t_end;
@@ -260,6 +296,68 @@ int acat_create(const acat_params *p, acat_ctx **out) {
   return ACAT_OK;
 }
 
+int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_inst, acat_ctx **out) {
+  if (!out || !p || n_inst < 1 || !n_per_inst) return ACAT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (p->ny != 1 || p->flux == ACAT_FLUX_EULER2D) return ACAT_ERR_INVALID_ARG;
+  const int gh = p->P > 2 ? p->P : 2;
+  long long M = 0, ntiles = 0;
+  const int T = acat_cells_per_cta_1d(p->P, p->precision);
+  if (T <= 0) return ACAT_ERR_INVALID_ARG;
+  for (int b = 0; b < n_inst; b++) {
+    if (n_per_inst[b] < 2 * gh) return ACAT_ERR_INVALID_ARG;
+    M += n_per_inst[b];
+    ntiles += (n_per_inst[b] + T - 1) / T;
+  }
+  if (M > (1ll << 31) || ntiles > (1ll << 31)) return ACAT_ERR_TOO_LARGE;
+  acat_params q = *p;
+  q.nx = n_per_inst[0];
+  acat_ctx *c = nullptr;
+  int rc = acat_create(&q, &c);
+  if (rc) return rc;
+  // replace the single-instance workspace by the batch's
+  cudaFree(c->d_work);
+  c->d_work = nullptr;
+  c->batched = 1;
+  c->B = n_inst;
+  c->cells = M;
+  c->ntiles = ntiles;
+  long long *offs = (long long *)std::malloc(sizeof(long long) * (size_t)(n_inst + 1));
+  TileRef *tiles = (TileRef *)std::malloc(sizeof(TileRef) * (size_t)ntiles);
+  if (!offs || !tiles) {
+    std::free(offs);
+    std::free(tiles);
+    acat_destroy(c);
+    return ACAT_ERR_NOMEM;
+  }
+  offs[0] = 0;
+  long long w = 0;
+  for (int b = 0; b < n_inst; b++) {
+    offs[b + 1] = offs[b] + n_per_inst[b];
+    const int nt = (n_per_inst[b] + T - 1) / T;
+    for (int k = 0; k < nt; k++) tiles[w++] = TileRef{b, k};
+  }
+  cudaError_t e = cudaMalloc(&c->d_work, (size_t)acat_state_bytes(c));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_offs, sizeof(long long) * (size_t)(n_inst + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_tiles, sizeof(TileRef) * (size_t)ntiles);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_smaxb, 3 * sizeof(unsigned long long) * (size_t)n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_tb, 3 * sizeof(double) * (size_t)n_inst);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_offs, offs, sizeof(long long) * (size_t)(n_inst + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_tiles, tiles, sizeof(TileRef) * (size_t)ntiles, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_smaxb, 0, 3 * sizeof(unsigned long long) * (size_t)n_inst);
+  if (e == cudaSuccess) e = cudaMemset(c->d_tb, 0, 3 * sizeof(double) * (size_t)n_inst);
+  std::free(offs);
+  std::free(tiles);
+  if (e != cudaSuccess) {
+    acat_destroy(c);
+    return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+  }
+  *out = c;
+  return ACAT_OK;
+}
+
 int acat_destroy(acat_ctx *c) {
   if (!c) return ACAT_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
@@ -270,6 +368,10 @@ int acat_destroy(acat_ctx *c) {
   cudaFree(c->d_status);
   cudaFree(c->d_work);
   cudaFree(c->d_host_stage);
+  cudaFree(c->d_offs);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_smaxb);
+  cudaFree(c->d_tb);
   delete c;
   return ACAT_OK;
 }
@@ -285,6 +387,28 @@ int acat_step(acat_ctx *c, const void *u_in, void *u_out, double dt, void *strea
   if (!c || !u_in || !u_out || u_in == u_out) return ACAT_ERR_INVALID_ARG;
   if (!(dt > 0.0) && dt != dt) return ACAT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->batched) {
+    Step1DArgs a = base_args(c);
+    a.u_in = u_in;
+    a.u_out = u_out;
+    a.slot = 0;
+    BatchArgs bt = batch_args(c);
+    bt.dt_out = dt_dev;
+    bt.orders = orders_dev;
+    if (cudaMemsetAsync(c->d_smaxb, 0, 3 * (size_t)c->B * sizeof(unsigned long long), st) != cudaSuccess)
+      return ACAT_ERR_CUDA;
+    if (dt > 0.0) {
+      a.dt_fixed = dt;
+      if (cudaMemsetAsync(c->d_tb, 0, 3 * (size_t)c->B * sizeof(double), st) != cudaSuccess)
+        return ACAT_ERR_CUDA;
+    } else {
+      if (acat_launch_smax_batch(c->p.flux, c->p.precision, a, bt, st)) return ACAT_ERR_CUDA;
+      c->launches++;
+    }
+    int e3 = acat_launch_batch1d(c->p.P, c->p.flux, c->p.precision, a, bt, st);
+    c->launches++;
+    return e3 ? ACAT_ERR_CUDA : ACAT_OK;
+  }
   if (c->dim == 2) {
     Step2DArgs a = base_args2(c);
     a.u_in = u_in;
@@ -330,7 +454,15 @@ int acat_run(acat_ctx *c, void *u, int nsteps, double t_end, void *stream, doubl
   if (t_end != t_end) return ACAT_ERR_INVALID_ARG;
   if (cudaMemsetAsync(c->d_smax, 0, 6 * sizeof(unsigned long long), st) != cudaSuccess)
     return ACAT_ERR_CUDA;
-  if (c->dim == 2) {
+  if (c->batched) {
+    Step1DArgs a = base_args(c);
+    a.u_in = u;
+    a.slot = 0;
+    BatchArgs bt = batch_args(c);
+    if (cudaMemsetAsync(c->d_smaxb, 0, 3 * (size_t)c->B * sizeof(unsigned long long), st) != cudaSuccess)
+      return ACAT_ERR_CUDA;
+    if (acat_launch_smax_batch(c->p.flux, c->p.precision, a, bt, st)) return ACAT_ERR_CUDA;
+  } else if (c->dim == 2) {
     Step2DArgs a = base_args2(c);
     a.u_in = u;
     a.slot = 0;
@@ -363,8 +495,9 @@ int acat_run(acat_ctx *c, void *u, int nsteps, double t_end, void *stream, doubl
       return ACAT_ERR_CUDA;
   }
   if (t_dev) {
-    if (cudaMemcpyAsync(t_dev, c->d_t + (nsteps % 3), sizeof(double), cudaMemcpyDeviceToDevice, st) !=
-        cudaSuccess)
+    const double *src = c->batched ? c->d_tb + (size_t)(nsteps % 3) * c->B : c->d_t + (nsteps % 3);
+    const size_t nb = (c->batched ? (size_t)c->B : 1) * sizeof(double);
+    if (cudaMemcpyAsync(t_dev, src, nb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return ACAT_ERR_CUDA;
   }
   return ACAT_OK;
@@ -375,8 +508,9 @@ int acat_run_host(acat_ctx *c, const void *u_host_in, void *u_host_out, int nste
   if (!c || !u_host_in || !u_host_out) return ACAT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t sb = (size_t)acat_state_bytes(c);
+  const size_t nt = c->batched ? (size_t)c->B : 1;  // time values returned
   if (!c->d_host_stage) {
-    cudaError_t e = cudaMalloc(&c->d_host_stage, sb + sizeof(double));
+    cudaError_t e = cudaMalloc(&c->d_host_stage, sb + nt * sizeof(double));
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
   }
   double *d_tfin = reinterpret_cast<double *>(static_cast<char *>(c->d_host_stage) + sb);
@@ -386,7 +520,7 @@ int acat_run_host(acat_ctx *c, const void *u_host_in, void *u_host_out, int nste
   if (rc) return rc;
   if (cudaMemcpyAsync(u_host_out, c->d_host_stage, sb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return ACAT_ERR_CUDA;
-  if (t_host && cudaMemcpyAsync(t_host, d_tfin, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (t_host && cudaMemcpyAsync(t_host, d_tfin, nt * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return ACAT_ERR_CUDA;
   return cuda_err(cudaStreamSynchronize(st));
 }

@@ -32,6 +32,8 @@
 // size O(dx) rather than to |f|. The update adds lambda (f(u_{i-1}) - f(u_i) +
 // G_{i-1/2} - G_{i+1/2}) to the pair with an error-free transformation
 // (Knuth's TwoSum, then Dekker's Fast2Sum).
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace {
@@ -477,27 +479,51 @@ __device__ __forceinline__ int select_order(const double *t0, const float *h0, c
   return accept ? (32 - __clz(accept)) + 1 : 1;
 }
 
+// Shared-memory workspace of one 1D tile.
+template <int P, int S>
+struct Smem64 {
+  double tile[S][Tiling<P>::TW];
+  double Fs[Tiling<P>::NI][S];
+  double red[NT / 32];
+};
+template <int P, int S>
+struct Smem32 {
+  double tile[S][Tiling<P>::TW];  // hi + lo, exact
+  float thi[S][Tiling<P>::TW], tlo[S][Tiling<P>::TW];
+  float Gs[Tiling<P>::NI][S];
+  double red[NT / 32];
+};
+
+// Block-wide maximum of `v` (thread 0 returns it).
+__device__ __forceinline__ double block_max(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = red[0];
+  if (threadIdx.x == 0)
+    for (int w = 1; w < NT / 32; w++) r = fmax(r, red[w]);
+  return r;
+}
+
+// One FP64 tile: cells [i0, i0 + T) of an instance of N cells whose state
+// starts at cell `off` of arrays with component stride M; orders (nullable)
+// points at the instance's interface 0; the tile's maximal wave speed goes to
+// *smax_out.
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
+__device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLUX>::S> &sm,
+                                         const double *__restrict__ uin, double *__restrict__ uout,
+                                         long off, long M, long N, long i0, double dt, double dx,
+                                         int8_t *orders, unsigned long long *smax_out) {
   using TL = Tiling<P>;
   constexpr int S = Phys<FLUX>::S;
-  __shared__ double tile[S][TL::TW];
-  __shared__ double Fs[TL::NI][S];
-  __shared__ double s_dt;
-  __shared__ double s_red[NT / 32];
-  const double *__restrict__ uin = static_cast<const double *>(a.u_in);
-  double *__restrict__ uout = static_cast<double *>(a.u_out);
-  const long N = a.N;
-  const long i0 = (long)blockIdx.x * TL::T;
-
-  if (threadIdx.x == 0) s_dt = step_dt(a);
   for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
     const int c = q / TL::TW, k = q - c * TL::TW;
-    tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
+    sm.tile[c][k] = uin[c * M + off + bc_index(i0 - TL::GH + k, N, a.bc)];
   }
   __syncthreads();
-  const double dt = s_dt;
-  const double lam = dt / a.dx;
+  const double lam = dt / dx;
   const double gm1 = a.gamma - 1.0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -509,12 +535,12 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
   const int ic = il - 1 + TL::GH;       // tile index of cell m-1
 
   const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
-  const int ps = select_order<P, S, false>(&tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l, grp,
-                                           active, valid, FC, a.eps, a.thr, a.fact_tau);
+  const int ps = select_order<P, S, false>(&sm.tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l,
+                                           grp, active, valid, FC, a.eps, a.thr, a.fact_tau);
 
   double F[S];
   const int base = grp * TL::L;
-  const double *q0 = &tile[0][ic];
+  const double *q0 = &sm.tile[0][ic];
   if (active) {
     if (ps == 4) {
       if constexpr (P >= 4) cat_flux<4, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
@@ -527,8 +553,8 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
     }
     if (l == 0) {
 #pragma unroll
-      for (int c = 0; c < S; c++) Fs[il][c] = F[c];
-      if (a.orders && (il < TL::T || m == N)) a.orders[m] = (int8_t)ps;
+      for (int c = 0; c < S; c++) sm.Fs[il][c] = F[c];
+      if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
     }
   }
   __syncthreads();
@@ -541,8 +567,8 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
     double un[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      un[c] = tile[c][t + TL::GH] + lam * (Fs[t][c] - Fs[t + 1][c]);
-      uout[c * N + i] = un[c];
+      un[c] = sm.tile[c][t + TL::GH] + lam * (sm.Fs[t][c] - sm.Fs[t + 1][c]);
+      uout[c * M + off + i] = un[c];
     }
     bool ok;
     const double sp = Phys<FLUX>::speed(un, a.adv, a.gamma, ok);
@@ -550,45 +576,30 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
     smax = fmax(smax, sp);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  if (lane == 0) s_red[warp] = smax;
+  const double v = block_max(smax, sm.red);
+  if (threadIdx.x == 0) atomic_max_pos(smax_out, v);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = s_red[0];
-    for (int w = 1; w < NT / 32; w++) v = fmax(v, s_red[w]);
-    atomic_max_pos(&a.smax[(a.slot + 1) % 3], v);
-  }
 }
 
-// FP32 step on the compensated state [hi(s x N); lo(s x N)].
+// One FP32 tile on the compensated state [hi(s x M); lo(s x M)].
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
+__device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FLUX>::S> &sm,
+                                         const float *__restrict__ uin, float *__restrict__ uout,
+                                         long off, long M, long N, long i0, double dt, double dx,
+                                         int8_t *orders, unsigned long long *smax_out) {
   using TL = Tiling<P>;
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
-  __shared__ double tile[S][TL::TW];  // hi + lo, exact
-  __shared__ float thi[S][TL::TW], tlo[S][TL::TW];
-  __shared__ float Gs[TL::NI][S];
-  __shared__ double s_dt;
-  __shared__ double s_red[NT / 32];
-  const float *__restrict__ uin = static_cast<const float *>(a.u_in);
-  float *__restrict__ uout = static_cast<float *>(a.u_out);
-  const long N = a.N;
-  const long i0 = (long)blockIdx.x * TL::T;
-
-  if (threadIdx.x == 0) s_dt = step_dt(a);
   for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
     const int c = q / TL::TW, k = q - c * TL::TW;
-    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
-    const float h = uin[c * N + g], w = uin[(S + c) * N + g];
-    thi[c][k] = h;
-    tlo[c][k] = w;
-    tile[c][k] = (double)h + (double)w;
+    const long g = off + bc_index(i0 - TL::GH + k, N, a.bc);
+    const float h = uin[c * M + g], w = uin[(S + c) * M + g];
+    sm.thi[c][k] = h;
+    sm.tlo[c][k] = w;
+    sm.tile[c][k] = (double)h + (double)w;
   }
   __syncthreads();
-  const double dt = s_dt;
-  const float lam = (float)(dt / a.dx), adv = (float)a.adv, gam = (float)a.gamma;
+  const float lam = (float)(dt / dx), adv = (float)a.adv, gam = (float)a.gamma;
   const float gm1 = (float)(a.gamma - 1.0);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -601,13 +612,13 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
 
   const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
   const int icv = valid ? ic : 0;
-  const int ps = select_order<P, S, true>(&tile[0][icv], &thi[0][icv], &tlo[0][icv], TL::TW, l, grp,
-                                          active, valid, FC, a.eps, a.thr, a.fact_tau);
+  const int ps = select_order<P, S, true>(&sm.tile[0][icv], &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW,
+                                          l, grp, active, valid, FC, a.eps, a.thr, a.fact_tau);
 
   float G[S];
   const int base = grp * TL::L;
   if (active) {
-    const float *h0 = &thi[0][ic], *l0 = &tlo[0][ic];
+    const float *h0 = &sm.thi[0][ic], *l0 = &sm.tlo[0][ic];
     if (ps == 4) {
       if constexpr (P >= 4) cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
     } else if (ps == 3) {
@@ -615,12 +626,13 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
     } else if (ps == 2) {
       if constexpr (P >= 2) if (l < 4) cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
     } else if (l == 0) {
-      flcat2_delta<FLUX>(h0, l0, &tile[0][ic], TL::TW, lam, adv, gam, a.adv, a.gamma, a.limiter_form, G);
+      flcat2_delta<FLUX>(h0, l0, &sm.tile[0][ic], TL::TW, lam, adv, gam, a.adv, a.gamma,
+                         a.limiter_form, G);
     }
     if (l == 0) {
 #pragma unroll
-      for (int c = 0; c < S; c++) Gs[il][c] = G[c];
-      if (a.orders && (il < TL::T || m == N)) a.orders[m] = (int8_t)ps;
+      for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];
+      if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
     }
   }
   __syncthreads();
@@ -634,15 +646,15 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
     float ui[S], dl[S], B[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      ui[c] = thi[c][k];
-      dl[c] = (thi[c][k - 1] - thi[c][k]) + (tlo[c][k - 1] - tlo[c][k]);
+      ui[c] = sm.thi[c][k];
+      dl[c] = (sm.thi[c][k - 1] - sm.thi[c][k]) + (sm.tlo[c][k - 1] - sm.tlo[c][k]);
     }
     DP::dflux(DP::base(ui, adv, gm1), dl, B);  // f(u_{i-1}) - f(u_i)
     double un[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      const float d = __fmul_rn(lam, __fadd_rn(B[c], __fsub_rn(Gs[t][c], Gs[t + 1][c])));
-      const float h = thi[c][k], w = tlo[c][k];
+      const float d = __fmul_rn(lam, __fadd_rn(B[c], __fsub_rn(sm.Gs[t][c], sm.Gs[t + 1][c])));
+      const float h = sm.thi[c][k], w = sm.tlo[c][k];
       // TwoSum(h, d): s + e = h + d exactly
       const float s = __fadd_rn(h, d);
       const float bp = __fsub_rn(s, h);
@@ -651,8 +663,8 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
       // Fast2Sum(s, w2), |s| >= |w2|: renormalised pair
       const float hn = __fadd_rn(s, w2);
       const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
-      uout[c * N + i] = hn;
-      uout[(S + c) * N + i] = ln;
+      uout[c * M + off + i] = hn;
+      uout[(S + c) * M + off + i] = ln;
       un[c] = (double)hn + (double)ln;
     }
     bool ok;
@@ -661,14 +673,121 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
     smax = fmax(smax, sp);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  if (lane == 0) s_red[warp] = smax;
+  const double v = block_max(smax, sm.red);
+  if (threadIdx.x == 0) atomic_max_pos(smax_out, v);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = s_red[0];
-    for (int w = 1; w < NT / 32; w++) v = fmax(v, s_red[w]);
-    atomic_max_pos(&a.smax[(a.slot + 1) % 3], v);
+}
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
+  __shared__ Smem64<P, Phys<FLUX>::S> sm;
+  __shared__ double s_dt;
+  if (threadIdx.x == 0) s_dt = step_dt(a);
+  __syncthreads();
+  tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out), 0,
+                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_dt, a.dx, a.orders,
+                    &a.smax[(a.slot + 1) % 3]);
+}
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
+  __shared__ Smem32<P, DPhys<FLUX>::S> sm;
+  __shared__ double s_dt;
+  if (threadIdx.x == 0) s_dt = step_dt(a);
+  __syncthreads();
+  tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0,
+                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_dt, a.dx, a.orders,
+                    &a.smax[(a.slot + 1) % 3]);
+}
+
+// dt of instance b of a batch (1D CFL rule on the instance's own wave speed
+// and grid); the instance's first tile advances its time and recycles its
+// slot two steps ahead.
+__device__ double batch_dt(const Step1DArgs &a, const BatchArgs &bt, int b, bool leader, double dx) {
+  const long B = bt.B;
+  double dt;
+  if (a.dt_fixed > 0.0) {
+    dt = a.dt_fixed;
+  } else {
+    const double smax = __longlong_as_double((long long)bt.smax[a.slot * B + b]);
+    if (!(smax > 0.0) || !isfinite(smax)) {
+      if (leader) atomicOr(a.status, (unsigned)ACAT_STATUS_BAD_DT);
+      dt = 0.0;
+    } else {
+      dt = a.cfl * dx / smax;
+    }
+  }
+  const double t = bt.t[a.slot * B + b];
+  if (a.t_end > 0.0) {
+    if (t >= a.t_end) dt = 0.0;
+    else if (dt > a.t_end - t) dt = a.t_end - t;
+  }
+  if (leader) {
+    bt.t[((a.slot + 1) % 3) * B + b] = t + dt;
+    bt.smax[((a.slot + 2) % 3) * B + b] = 0ull;
+    if (bt.dt_out) bt.dt_out[b] = dt;
+  }
+  return dt;
+}
+
+// Persistent batched step: the CTAs stride over the (instance, first cell)
+// work list; every instance is advanced with its own dt.
+template <int P, int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_batch1d(const Step1DArgs a, const BatchArgs bt) {
+  using SM = typename std::conditional<F32, Smem32<P, Phys<FLUX>::S>, Smem64<P, Phys<FLUX>::S>>::type;
+  __shared__ SM sm;
+  __shared__ double s_dt;
+  for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
+    const int b = bt.tiles[w].b;
+    const long i0 = (long)bt.tiles[w].tile * Tiling<P>::T;
+    const long off = bt.offs[b], N = bt.offs[b + 1] - off;
+    const double dx = bt.xlen / (double)N;
+    if (threadIdx.x == 0) s_dt = batch_dt(a, bt, b, i0 == 0, dx);
+    __syncthreads();
+    int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
+    unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
+    if constexpr (F32)
+      tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), off,
+                        bt.M, N, i0, s_dt, dx, ord, so);
+    else
+      tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
+                        off, bt.M, N, i0, s_dt, dx, ord, so);
+  }
+}
+
+// Wave speed of every instance of a batch into its slot (one CTA per
+// instance); also sets the instances' time to 0.
+template <int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_smax_batch(const Step1DArgs a, const BatchArgs bt) {
+  constexpr int S = Phys<FLUX>::S;
+  __shared__ double red[NT / 32];
+  for (long b = blockIdx.x; b < bt.B; b += gridDim.x) {
+    const long off = bt.offs[b], N = bt.offs[b + 1] - off;
+    double smax = 0.0;
+    bool bad = false;
+    for (long i = threadIdx.x; i < N; i += NT) {
+      double u[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if constexpr (F32) {
+          const float *p = static_cast<const float *>(a.u_in);
+          u[c] = (double)p[c * bt.M + off + i] + (double)p[(S + c) * bt.M + off + i];
+        } else {
+          u[c] = static_cast<const double *>(a.u_in)[c * bt.M + off + i];
+        }
+      }
+      bool ok;
+      smax = fmax(smax, Phys<FLUX>::speed(u, a.adv, a.gamma, ok));
+      bad |= !ok;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+    const double v = block_max(smax, red);
+    if (threadIdx.x == 0) {
+      atomic_max_pos(&bt.smax[a.slot * bt.B + b], v);
+      bt.t[a.slot * bt.B + b] = 0.0;
+    }
+    __syncthreads();
   }
 }
 
@@ -751,7 +870,63 @@ int launch_smax(int flux, const Step1DArgs &a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+template <int FLUX, bool F32>
+int launch_batch_f(int P, const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  switch (P) {
+#define ACAT_BATCH_CASE(PP)                                                                      \
+  case PP:                                                                                       \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch1d<PP, FLUX, F32>, NT, 0);        \
+    k_batch1d<PP, FLUX, F32><<<(unsigned)(sms * (occ > 0 ? occ : 1)), NT, 0, st>>>(a, bt);      \
+    break;
+    ACAT_BATCH_CASE(1)
+    ACAT_BATCH_CASE(2)
+    ACAT_BATCH_CASE(3)
+    ACAT_BATCH_CASE(4)
+#undef ACAT_BATCH_CASE
+  default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+template <bool F32>
+int launch_batch(int P, int flux, const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st) {
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: return launch_batch_f<ACAT_FLUX_LINEAR, F32>(P, a, bt, st);
+  case ACAT_FLUX_BURGERS: return launch_batch_f<ACAT_FLUX_BURGERS, F32>(P, a, bt, st);
+  case ACAT_FLUX_EULER1D: return launch_batch_f<ACAT_FLUX_EULER1D, F32>(P, a, bt, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <bool F32>
+int launch_smax_batch(int flux, const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st) {
+  const unsigned grid = (unsigned)(bt.B < 4096 ? bt.B : 4096);
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: k_smax_batch<ACAT_FLUX_LINEAR, F32><<<grid, NT, 0, st>>>(a, bt); break;
+  case ACAT_FLUX_BURGERS: k_smax_batch<ACAT_FLUX_BURGERS, F32><<<grid, NT, 0, st>>>(a, bt); break;
+  case ACAT_FLUX_EULER1D: k_smax_batch<ACAT_FLUX_EULER1D, F32><<<grid, NT, 0, st>>>(a, bt); break;
+  default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
 }  // namespace
+
+int acat_launch_batch1d(int P, int flux, int prec, const Step1DArgs &a, const BatchArgs &bt,
+                        void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return prec == ACAT_PREC_F32 ? launch_batch<true>(P, flux, a, bt, st)
+                               : launch_batch<false>(P, flux, a, bt, st);
+}
+
+int acat_launch_smax_batch(int flux, int prec, const Step1DArgs &a, const BatchArgs &bt, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return prec == ACAT_PREC_F32 ? launch_smax_batch<true>(flux, a, bt, st)
+                               : launch_smax_batch<false>(flux, a, bt, st);
+}
 
 int acat_cells_per_cta_1d(int P, int /*prec*/) {
   switch (P) {

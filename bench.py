@@ -47,6 +47,9 @@ def parse():
                     help="ACAT steps per benchmark step (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", default="main",
+                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "batch_f32"],
+                    help="profiling runs: one short measurement of a single workload")
     return ap.parse_args()
 
 
@@ -271,6 +274,45 @@ def measure_2d(torch, acat, W, flops, n, prec, steps, K, flush, peak):
             "flcat2_directions": round(flc / (2 * n * (n + 1)), 4)}
 
 
+def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
+    """4096 independent 1D Euler instances, N uniform in [256, 16384], P = 3,
+    one persistent launch per step."""
+    import numpy as np
+    sizes, states = W.euler1d_batched(n_inst=4096, seed=SEED)
+    kw = W.euler1d_riemann_entropy(nx=256, seed=0, P=3, cfl=CFL).problem_kwargs()
+    u = np.ascontiguousarray(np.concatenate(states, axis=1))
+    ctx = acat.Context(**kw, precision=prec, sizes=sizes)
+    u0 = torch.from_numpy(acat.to_pair(u) if prec == acat.PREC_F32 else u).cuda()
+    v = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    v.copy_(u0)
+    ctx.acat_run(v, 6)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v.copy_(u0)
+        e0.record(stream)
+        ctx.acat_run(v, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    assert ctx.acat_status() == 0
+    M = int(sizes.sum())
+    orders = torch.zeros(M + len(sizes), dtype=torch.int8, device="cuda")
+    tmp = torch.empty_like(v)
+    ctx.acat_step(v, tmp, -1.0, None, None, orders)
+    torch.cuda.synchronize()
+    h = torch.bincount(orders.to(torch.int64), minlength=5).cpu().tolist()
+    fl = flops.step_flops_1d({k: h[k] for k in range(1, 5)}, 3, W.EULER1D, M)
+    t = sum(ms) / K
+    ctx.close()
+    return {"value": M * steps / (t * 1e-3), "unit": UNIT, "ms_per_run": t, "steps": steps,
+            "instances": len(sizes), "cells": M, "roofline_frac": fl / (t / steps * 1e-3) / peak,
+            "order_mix": {str(k): round(h[k] / (M + len(sizes)), 4) for k in range(1, 5)}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -365,6 +407,14 @@ def run_ours(args):
         v32["speedup_vs_f64_per_cell_update"] = v32["value"] / v64["value"]
         variants["2d_euler_P2_4096_f32"] = v32
         variants["2d_euler_P2_1024_f64"] = v64
+        # batched: 4096 ragged instances (P = 3), 1000 steps in FP32, and 10 steps of
+        # the plain FP64 step for the ratio
+        b32 = measure_batch(torch, acat, W, flops, acat.PREC_F32, 1000, 1, flush, peak32)
+        b64 = measure_batch(torch, acat, W, flops, acat.PREC_F64, 10, 1, flush, peak64)
+        b32["roofline_peak"], b64["roofline_peak"] = "fp32", "fp64"
+        b32["speedup_vs_f64_per_cell_update"] = b32["value"] / b64["value"]
+        variants["batched_euler_P3_4096inst_f32"] = b32
+        variants["batched_euler_P3_4096inst_f64"] = b64
 
     if rank != 0:
         return 0
@@ -399,10 +449,36 @@ def run_ours(args):
     return 0
 
 
+def run_single(args):
+    """One short measurement of one workload (for profiler captures)."""
+    import torch
+
+    from paper_2007_01416_gb300 import acat, flops
+    from paper_2007_01416_gb300 import build as B
+    from paper_2007_01416_gb300 import workloads as W
+    B.build()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    n = args.acat_steps
+    if args.workload == "f32_1d":
+        m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F32, n, 1, 1, flush, False, 0)
+        out = {"ms": m["ms"]}
+    elif args.workload in ("2d_f32", "2d_f64"):
+        f32 = args.workload == "2d_f32"
+        out = measure_2d(torch, acat, W, flops, 4096 if f32 else 1024,
+                         acat.PREC_F32 if f32 else acat.PREC_F64, n, 1, flush, 1.0)
+    else:
+        out = measure_batch(torch, acat, W, flops, acat.PREC_F32, n, 1, flush, 1.0)
+    print(json.dumps({"workload": args.workload, **{k: v for k, v in out.items()
+                                                     if isinstance(v, (int, float, list))}}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "main":
+        return run_single(args)
     return run_ours(args)
 
 

@@ -41,6 +41,8 @@ struct Step1DArgs {
   double t_end;               // > 0: clip t at t_end
   double gamma, adv, eps, thr;
   double fact_tau[ACAT_MAXP + 1];
+  float epsf, rf;             // float eps and thr / (1 - thr) of the filtered decision
+  float factf[ACAT_MAXP + 1];
   unsigned long long *smax;   // 3 slots: max wave speed as ordered double bits
   double *tslot;              // 3 slots: simulated time (nullable)
   int8_t *orders;             // N+1 order codes (nullable)
@@ -84,6 +86,8 @@ struct Step2DArgs {
   double dt_fixed, t_end;
   double gamma, adv[2], eps, thr;
   double fact_tau[ACAT_MAXP + 1];
+  float epsf, rf;
+  float factf[ACAT_MAXP + 1];
   unsigned long long *smax;   // 3 slots x 2 directions: [slot][dir]
   double *tslot;              // 3 slots (nullable)
   int8_t *ord_x;              // NY x (NX+1) (nullable)

@@ -97,7 +97,12 @@ Step1DArgs base_args(acat_ctx *c) {
   a.adv = p.adv[0];
   a.eps = p.eps;
   a.thr = 1.0 - p.psi_tol;
-  for (int q = 0; q <= ACAT_MAXP; q++) a.fact_tau[q] = c->fact_tau[q];
+  for (int q = 0; q <= ACAT_MAXP; q++) {
+    a.fact_tau[q] = c->fact_tau[q];
+    a.factf[q] = (float)c->fact_tau[q];
+  }
+  a.epsf = (float)p.eps;
+  a.rf = (float)(a.thr / (1.0 - a.thr));
   a.smax = c->d_smax;
   a.status = c->d_status;
   return a;
@@ -121,7 +126,12 @@ Step2DArgs base_args2(acat_ctx *c) {
   a.adv[1] = p.adv[1];
   a.eps = p.eps;
   a.thr = 1.0 - p.psi_tol;
-  for (int q = 0; q <= ACAT_MAXP; q++) a.fact_tau[q] = c->fact_tau[q];
+  for (int q = 0; q <= ACAT_MAXP; q++) {
+    a.fact_tau[q] = c->fact_tau[q];
+    a.factf[q] = (float)c->fact_tau[q];
+  }
+  a.epsf = (float)p.eps;
+  a.rf = (float)(a.thr / (1.0 - a.thr));
   a.smax = c->d_smax;
   a.status = c->d_status;
   return a;

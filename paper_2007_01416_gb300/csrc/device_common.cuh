@@ -63,24 +63,36 @@ __device__ __forceinline__ long bc_index(long g, long N, int bc) {
 // Indicators and limiter: explicit round-to-nearest FP64 operations, no FMA
 // contraction, in the order of Eqs. 3.6-3.12.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double psi_p_comp(const double *q, int st, int p, double eps, double fact) {
+// q(j) returns the FP64 value of cell i + j.
+template <class Get>
+__device__ __forceinline__ double psi_p_comp_g(Get q, int p, double eps, double fact) {
   double IL = 0.0, IR = 0.0;
   for (int j = -p + 1; j <= -1; j++) {
-    const double d = __dsub_rn(q[(1 + j) * st], q[j * st]);
+    const double d = __dsub_rn(q(1 + j), q(j));
     IL = __dadd_rn(IL, __dmul_rn(d, d));
   }
   IL = __dadd_rn(IL, eps);
   for (int j = 1; j <= p - 1; j++) {
-    const double d = __dsub_rn(q[(1 + j) * st], q[j * st]);
+    const double d = __dsub_rn(q(1 + j), q(j));
     IR = __dadd_rn(IR, __dmul_rn(d, d));
   }
   IR = __dadd_rn(IR, eps);
   const double I = __ddiv_rn(__dmul_rn(IL, IR), __dadd_rn(IL, IR));
   double S = 0.0;
-  for (int j = -p + 1; j <= p; j++) S = __dadd_rn(S, __dmul_rn(c_tab.gd[p][j + p - 1], q[j * st]));
+  for (int j = -p + 1; j <= p; j++) S = __dadd_rn(S, __dmul_rn(c_tab.gd[p][j + p - 1], q(j)));
   const double D = __dmul_rn(fact, S);
   const double tau = __dmul_rn(D, D);
   return __ddiv_rn(I, __dadd_rn(I, tau));
+}
+
+__device__ __forceinline__ double psi_p_comp(const double *q, int st, int p, double eps, double fact) {
+  return psi_p_comp_g([=](int j) { return q[j * st]; }, p, eps, fact);
+}
+
+// The same on a compensated float state: the exact value hi + lo.
+__device__ __forceinline__ double psi_p_comp_pair(const float *hi, const float *lo, int st, int p,
+                                                  double eps, double fact) {
+  return psi_p_comp_g([=](int j) { return (double)hi[j * st] + (double)lo[j * st]; }, p, eps, fact);
 }
 
 __device__ __forceinline__ double lim_ratio(double upw, double loc) {
@@ -154,12 +166,13 @@ struct FiltConst {
   float eps, r;
   float fact[ACAT_MAXP + 1];
 };
-__device__ __forceinline__ FiltConst filt_const(double eps, double thr, const double *fact) {
+// From the float constants computed once on the host (no FP64 work per thread).
+__device__ __forceinline__ FiltConst filt_const(float eps, float r, const float *fact) {
   FiltConst f;
-  f.eps = (float)eps;
-  f.r = (float)(thr / (1.0 - thr));
+  f.eps = eps;
+  f.r = r;
 #pragma unroll
-  for (int q = 0; q <= ACAT_MAXP; q++) f.fact[q] = (float)fact[q];
+  for (int q = 0; q <= ACAT_MAXP; q++) f.fact[q] = fact[q];
   return f;
 }
 
@@ -183,12 +196,11 @@ __device__ __forceinline__ bool admit64(const double *q, int st, bool first, con
   return first ? (v >= thr) : !(v < thr);
 }
 
-// The same for a compensated float state hi + lo (q64 holds hi + lo in FP64
-// for the literal fallback).
+// The same for a compensated float state hi + lo (the literal fallback reads
+// the exact value hi + lo).
 template <int p>
-__device__ __forceinline__ bool admit32(const float *hi, const float *lo, const double *q64, int st,
-                                        bool first, const FiltConst &F, double eps, double thr,
-                                        double fact) {
+__device__ __forceinline__ bool admit32(const float *hi, const float *lo, int st, bool first,
+                                        const FiltConst &F, double eps, double thr, double fact) {
   float d[2 * p - 1], e[2 * p - 1];
 #pragma unroll
   for (int k = 0; k < 2 * p - 1; k++) {
@@ -199,7 +211,7 @@ __device__ __forceinline__ bool admit32(const float *hi, const float *lo, const 
   }
   const int dec = psi_filter<p>(d, e, F.eps, F.r, F.fact[p]);
   if (dec >= 0) return dec == 1;
-  const double v = psi_p_comp(q64, st, p, eps, fact);
+  const double v = psi_p_comp_pair(hi, lo, st, p, eps, fact);
   return first ? (v >= thr) : !(v < thr);
 }
 
@@ -212,13 +224,12 @@ __device__ __forceinline__ bool admit64_p(int p, const double *q, int st, bool f
   default: return admit64<4>(q, st, first, F, eps, thr, fact);
   }
 }
-__device__ __forceinline__ bool admit32_p(int p, const float *hi, const float *lo, const double *q64,
-                                          int st, bool first, const FiltConst &F, double eps,
-                                          double thr, double fact) {
+__device__ __forceinline__ bool admit32_p(int p, const float *hi, const float *lo, int st, bool first,
+                                          const FiltConst &F, double eps, double thr, double fact) {
   switch (p) {
-  case 2: return admit32<2>(hi, lo, q64, st, first, F, eps, thr, fact);
-  case 3: return admit32<3>(hi, lo, q64, st, first, F, eps, thr, fact);
-  default: return admit32<4>(hi, lo, q64, st, first, F, eps, thr, fact);
+  case 2: return admit32<2>(hi, lo, st, first, F, eps, thr, fact);
+  case 3: return admit32<3>(hi, lo, st, first, F, eps, thr, fact);
+  default: return admit32<4>(hi, lo, st, first, F, eps, thr, fact);
   }
 }
 
@@ -227,11 +238,10 @@ __device__ __forceinline__ bool admit32_p(int p, const float *hi, const float *l
 // 0: linear transport with speed `adv`, kind 1: Burgers) use the Roe-speed
 // side unless limiter_form is 1; systems use min(psi(r+), psi(r-)) per
 // component and the minimum over components.
-template <int S>
-__device__ __forceinline__ double psi1_line(const double *q, int cs, int st, int kind,
-                                            int limiter_form, double adv) {
+template <int S, class Get>
+__device__ __forceinline__ double psi1_g(Get q, int kind, int limiter_form, double adv) {
   if (S == 1 && limiter_form == 0) {
-    const double um = q[-st], u0 = q[0], u1 = q[st], u2 = q[2 * st];
+    const double um = q(0, -1), u0 = q(0, 0), u1 = q(0, 1), u2 = q(0, 2);
     double a;
     if (u0 != u1) {
       double f0, f1;
@@ -252,14 +262,28 @@ __device__ __forceinline__ double psi1_line(const double *q, int cs, int st, int
   double best = 2.0;
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const double *p = q + c * cs;
-    const double loc = __dsub_rn(p[st], p[0]);
-    const double pm = superbee(lim_ratio(__dsub_rn(p[0], p[-st]), loc));
-    const double pp = superbee(lim_ratio(__dsub_rn(p[2 * st], p[st]), loc));
+    const double v0 = q(c, 0), v1 = q(c, 1);
+    const double loc = __dsub_rn(v1, v0);
+    const double pm = superbee(lim_ratio(__dsub_rn(v0, q(c, -1)), loc));
+    const double pp = superbee(lim_ratio(__dsub_rn(q(c, 2), v1), loc));
     const double v = pp < pm ? pp : pm;
     if (v < best) best = v;
   }
   return best;
+}
+
+template <int S>
+__device__ __forceinline__ double psi1_line(const double *q, int cs, int st, int kind,
+                                            int limiter_form, double adv) {
+  return psi1_g<S>([=](int c, int k) { return q[c * cs + k * st]; }, kind, limiter_form, adv);
+}
+
+template <int S>
+__device__ __forceinline__ double psi1_pair(const float *hi, const float *lo, int cs, int st, int kind,
+                                            int limiter_form, double adv) {
+  return psi1_g<S>(
+      [=](int c, int k) { return (double)hi[c * cs + k * st] + (double)lo[c * cs + k * st]; }, kind,
+      limiter_form, adv);
 }
 
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {

@@ -107,7 +107,12 @@ extern "C" int acat_run_noalloc(const acat_params *p, void *u_dev, int nsteps, d
   a.adv = p->adv[0];
   a.eps = p->eps;
   a.thr = 1.0 - p->psi_tol;
-  for (int q = 0; q <= ACAT_MAXP; q++) a.fact_tau[q] = p->tau_factorial ? T.fact[q] : 1.0;
+  for (int q = 0; q <= ACAT_MAXP; q++) {
+    a.fact_tau[q] = p->tau_factorial ? T.fact[q] : 1.0;
+    a.factf[q] = (float)a.fact_tau[q];
+  }
+  a.epsf = (float)p->eps;
+  a.rf = (float)(a.thr / (1.0 - a.thr));
   a.smax = smax;
   a.tslot = tslot;
   a.status = status;

@@ -235,6 +235,7 @@ struct DPhys<ACAT_FLUX_LINEAR> {
     df[0] = b.a * d[0];
   }
   __device__ static __forceinline__ float speed(const float *, float a, float) { return fabsf(a); }
+  __device__ static __forceinline__ bool physical(const float *u, float) { return isfinite(u[0]); }
 };
 
 template <>
@@ -249,6 +250,7 @@ struct DPhys<ACAT_FLUX_BURGERS> {
     df[0] = d[0] * fmaf(0.5f, d[0], b.u);
   }
   __device__ static __forceinline__ float speed(const float *u, float, float) { return fabsf(u[0]); }
+  __device__ static __forceinline__ bool physical(const float *u, float) { return isfinite(u[0]); }
 };
 
 template <>
@@ -285,6 +287,10 @@ struct DPhys<ACAT_FLUX_EULER1D> {
     const float v = u[1] / u[0];
     const float p = (gamma - 1.0f) * (u[2] - 0.5f * u[1] * v);
     return fabsf(v) + sqrtf(fmaxf(gamma * p / u[0], 0.0f));
+  }
+  __device__ static __forceinline__ bool physical(const float *u, float gamma) {
+    const float p = (gamma - 1.0f) * (u[2] - 0.5f * u[1] * (u[1] / u[0]));
+    return u[0] > 0.0f && p > 0.0f && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
   }
 };
 
@@ -370,9 +376,9 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
 //   CAT2:    F1 - f(u_i) = (T0 + T1 + D1) / 4
 //   Rusanov: Flo - f(u_i) = D1 / 2 - alpha (u_{i+1} - u_i) / 2
 template <int FLUX>
-__device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, const double *q64,
-                                             int cs, float lam, float adv, float gamma, double advd,
-                                             double gammad, int limiter_form, float *G) {
+__device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, int cs, float lam,
+                                             float adv, float gamma, double advd, int limiter_form,
+                                             float *G) {
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
   const float gm1 = gamma - 1.0f;
@@ -394,8 +400,8 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, c
   DP::dflux(b0, d1, T1);
   const float s0 = DP::speed(u0, adv, gamma), s1 = DP::speed(u1, adv, gamma);
   const float alpha = s1 > s0 ? s1 : s0;
-  const float w = (float)psi1<FLUX>(q64, cs, limiter_form, advd);
-  (void)gammad;
+  const float w = (float)psi1_pair<S>(hi, lo, cs, 1, FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form,
+                                      advd);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const float G1 = 0.25f * (T0[c] + T1[c] + D1[c]);
@@ -466,7 +472,7 @@ __device__ __forceinline__ int select_order(const double *t0, const float *h0, c
       const int p = 2 + q / S, c = q - (q / S) * S;
       bool ok;
       if constexpr (F32)
-        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
+        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
       else
         ok = admit64_p(p, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
       if (!ok) rej |= 1u << (p - 2);
@@ -488,7 +494,6 @@ struct Smem64 {
 };
 template <int P, int S>
 struct Smem32 {
-  double tile[S][Tiling<P>::TW];  // hi + lo, exact
   float thi[S][Tiling<P>::TW], tlo[S][Tiling<P>::TW];
   float Gs[Tiling<P>::NI][S];
   double red[NT / 32];
@@ -514,7 +519,7 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 template <int P, int FLUX>
 __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLUX>::S> &sm,
                                          const double *__restrict__ uin, double *__restrict__ uout,
-                                         long off, long M, long N, long i0, double dt, double dx,
+                                         long off, long M, long N, long i0, double lam,
                                          int8_t *orders, unsigned long long *smax_out) {
   using TL = Tiling<P>;
   constexpr int S = Phys<FLUX>::S;
@@ -523,7 +528,6 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
     sm.tile[c][k] = uin[c * M + off + bc_index(i0 - TL::GH + k, N, a.bc)];
   }
   __syncthreads();
-  const double lam = dt / dx;
   const double gm1 = a.gamma - 1.0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -534,7 +538,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
   const bool active = valid && m <= N;
   const int ic = il - 1 + TL::GH;       // tile index of cell m-1
 
-  const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int ps = select_order<P, S, false>(&sm.tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l,
                                            grp, active, valid, FC, a.eps, a.thr, a.fact_tau);
 
@@ -585,7 +589,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
 template <int P, int FLUX>
 __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FLUX>::S> &sm,
                                          const float *__restrict__ uin, float *__restrict__ uout,
-                                         long off, long M, long N, long i0, double dt, double dx,
+                                         long off, long M, long N, long i0, double lamd,
                                          int8_t *orders, unsigned long long *smax_out) {
   using TL = Tiling<P>;
   using DP = DPhys<FLUX>;
@@ -593,13 +597,11 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
     const int c = q / TL::TW, k = q - c * TL::TW;
     const long g = off + bc_index(i0 - TL::GH + k, N, a.bc);
-    const float h = uin[c * M + g], w = uin[(S + c) * M + g];
-    sm.thi[c][k] = h;
-    sm.tlo[c][k] = w;
-    sm.tile[c][k] = (double)h + (double)w;
+    sm.thi[c][k] = uin[c * M + g];
+    sm.tlo[c][k] = uin[(S + c) * M + g];
   }
   __syncthreads();
-  const float lam = (float)(dt / dx), adv = (float)a.adv, gam = (float)a.gamma;
+  const float lam = (float)lamd, adv = (float)a.adv, gam = (float)a.gamma;
   const float gm1 = (float)(a.gamma - 1.0);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -610,10 +612,10 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   const bool active = valid && m <= N;
   const int ic = il - 1 + TL::GH;
 
-  const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int icv = valid ? ic : 0;
-  const int ps = select_order<P, S, true>(&sm.tile[0][icv], &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW,
-                                          l, grp, active, valid, FC, a.eps, a.thr, a.fact_tau);
+  const int ps = select_order<P, S, true>(nullptr, &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW, l, grp,
+                                          active, valid, FC, a.eps, a.thr, a.fact_tau);
 
   float G[S];
   const int base = grp * TL::L;
@@ -626,8 +628,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     } else if (ps == 2) {
       if constexpr (P >= 2) if (l < 4) cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
     } else if (l == 0) {
-      flcat2_delta<FLUX>(h0, l0, &sm.tile[0][ic], TL::TW, lam, adv, gam, a.adv, a.gamma,
-                         a.limiter_form, G);
+      flcat2_delta<FLUX>(h0, l0, TL::TW, lam, adv, gam, a.adv, a.limiter_form, G);
     }
     if (l == 0) {
 #pragma unroll
@@ -650,7 +651,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
       dl[c] = (sm.thi[c][k - 1] - sm.thi[c][k]) + (sm.tlo[c][k - 1] - sm.tlo[c][k]);
     }
     DP::dflux(DP::base(ui, adv, gm1), dl, B);  // f(u_{i-1}) - f(u_i)
-    double un[S];
+    float un[S], lo_[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const float d = __fmul_rn(lam, __fadd_rn(B[c], __fsub_rn(sm.Gs[t][c], sm.Gs[t + 1][c])));
@@ -665,12 +666,21 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
       const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
       uout[c * M + off + i] = hn;
       uout[(S + c) * M + off + i] = ln;
-      un[c] = (double)hn + (double)ln;
+      un[c] = hn;
+      lo_[c] = ln;
     }
-    bool ok;
-    const double sp = Phys<FLUX>::speed(un, a.adv, a.gamma, ok);
-    bad |= !ok;
-    smax = fmax(smax, sp);
+    // wave speed in float (the FP32 path's dt is exact to float rounding);
+    // a state that looks non-physical in float is re-checked in FP64
+    const float sf = DP::speed(un, adv, gam);
+    if (!DP::physical(un, gam)) {
+      double ud[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) ud[c] = (double)un[c] + (double)lo_[c];
+      bool ok;
+      Phys<FLUX>::speed(ud, a.adv, a.gamma, ok);
+      bad |= !ok;
+    }
+    smax = fmax(smax, (double)sf);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
   const double v = block_max(smax, sm.red);
@@ -681,22 +691,22 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
   __shared__ Smem64<P, Phys<FLUX>::S> sm;
-  __shared__ double s_dt;
-  if (threadIdx.x == 0) s_dt = step_dt(a);
+  __shared__ double s_lam;
+  if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
   __syncthreads();
   tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out), 0,
-                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_dt, a.dx, a.orders,
+                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_lam, a.orders,
                     &a.smax[(a.slot + 1) % 3]);
 }
 
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
   __shared__ Smem32<P, DPhys<FLUX>::S> sm;
-  __shared__ double s_dt;
-  if (threadIdx.x == 0) s_dt = step_dt(a);
+  __shared__ double s_lam;
+  if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
   __syncthreads();
   tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0,
-                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_dt, a.dx, a.orders,
+                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_lam, a.orders,
                     &a.smax[(a.slot + 1) % 3]);
 }
 
@@ -736,22 +746,24 @@ template <int P, int FLUX, bool F32>
 __global__ void __launch_bounds__(NT) k_batch1d(const Step1DArgs a, const BatchArgs bt) {
   using SM = typename std::conditional<F32, Smem32<P, Phys<FLUX>::S>, Smem64<P, Phys<FLUX>::S>>::type;
   __shared__ SM sm;
-  __shared__ double s_dt;
+  __shared__ double s_lam;
   for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
     const int b = bt.tiles[w].b;
     const long i0 = (long)bt.tiles[w].tile * Tiling<P>::T;
     const long off = bt.offs[b], N = bt.offs[b + 1] - off;
-    const double dx = bt.xlen / (double)N;
-    if (threadIdx.x == 0) s_dt = batch_dt(a, bt, b, i0 == 0, dx);
+    if (threadIdx.x == 0) {
+      const double dx = bt.xlen / (double)N;
+      s_lam = batch_dt(a, bt, b, i0 == 0, dx) / dx;
+    }
     __syncthreads();
     int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
     unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
     if constexpr (F32)
       tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), off,
-                        bt.M, N, i0, s_dt, dx, ord, so);
+                        bt.M, N, i0, s_lam, ord, so);
     else
       tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
-                        off, bt.M, N, i0, s_dt, dx, ord, so);
+                        off, bt.M, N, i0, s_lam, ord, so);
   }
 }
 

@@ -62,6 +62,7 @@ struct Phys2<ACAT_FLUX_LINEAR> {
   __device__ static __forceinline__ float fspeed(const float *, float ax, float ay, float, int dir) {
     return dir == 0 ? fabsf(ax) : fabsf(ay);
   }
+  __device__ static __forceinline__ bool fphysical(const float *u, float) { return isfinite(u[0]); }
 };
 
 template <>
@@ -135,6 +136,12 @@ struct Phys2<ACAT_FLUX_EULER2D> {
     const float v = u[1] / u[0], w = u[2] / u[0];
     const float p = (gamma - 1.0f) * (u[3] - 0.5f * (u[1] * v + u[2] * w));
     return fabsf(dir == 0 ? v : w) + sqrtf(fmaxf(gamma * p / u[0], 0.0f));
+  }
+  __device__ static __forceinline__ bool fphysical(const float *u, float gamma) {
+    const float ri = 1.0f / u[0];
+    const float p = (gamma - 1.0f) * (u[3] - 0.5f * (u[1] * u[1] + u[2] * u[2]) * ri);
+    return u[0] > 0.0f && p > 0.0f && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) &&
+           isfinite(u[3]);
   }
 };
 
@@ -394,8 +401,8 @@ __device__ __forceinline__ void flcat2_2d_f64(const double *q, int cs, int rs, b
 
 // FP32 FL-CAT2 in 2D, delta form about the anchor state a (one lane).
 template <int FLUX>
-__device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, const double *q64,
-                                              int cs, int rs, bool wantF, bool wantG, float lx,
+__device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, int cs, int rs,
+                                              bool wantF, bool wantG, float lx,
                                               float ly, float ax, float ay, float gamma, double axd,
                                               double ayd, int limiter_form, float *GF, float *GG) {
   using PH = Phys2<FLUX>;
@@ -430,7 +437,7 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
     PH::dflux2(B, x1, ef, eg);  // f(u10 + U10) - f(u_a)
     const float s0 = PH::fspeed(ua, ax, ay, gamma, 0), s1 = PH::fspeed(u10, ax, ay, gamma, 0);
     const float alpha = s1 > s0 ? s1 : s0;
-    const float w = (float)psi1_line<S>(q64, cs, 1, kind, limiter_form, axd);
+    const float w = (float)psi1_pair<S>(hi, lo, cs, 1, kind, limiter_form, axd);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       // F1 - f(a) = Df10/2 + (e00 + (ef - Df10))/4 ; Flo - f(a) = Df10/2 - alpha d10/2
@@ -446,7 +453,7 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
     PH::dflux2(B, x1, ef, eg);  // g(u01 + U01) - g(u_a)
     const float s0 = PH::fspeed(ua, ax, ay, gamma, 1), s1 = PH::fspeed(u01, ax, ay, gamma, 1);
     const float alpha = s1 > s0 ? s1 : s0;
-    const float w = (float)psi1_line<S>(q64, cs, rs, kind, limiter_form, ayd);
+    const float w = (float)psi1_pair<S>(hi, lo, cs, rs, kind, limiter_form, ayd);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const float G1 = 0.5f * Dg01[c] + 0.25f * (e00g[c] + eg[c] - Dg01[c]);
@@ -499,7 +506,7 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   using R = typename std::conditional<F32, float, double>::type;
-  __shared__ double tile[S][TW2][TW2];
+  __shared__ double tile[F32 ? 1 : S][F32 ? 1 : TW2][F32 ? 1 : TW2];
   __shared__ float thi[F32 ? S : 1][F32 ? TW2 : 1][F32 ? TW2 : 1];
   __shared__ float tlo[F32 ? S : 1][F32 ? TW2 : 1][F32 ? TW2 : 1];
   __shared__ R Fx[TXY][TXY + 1][S];
@@ -509,7 +516,12 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
   const long NXl = a.NX, NYl = a.NY;
   const long x0 = (long)blockIdx.x * TXY, y0 = (long)blockIdx.y * TXY;
 
-  if (threadIdx.x == 0) s_dt = step_dt2(a);
+  __shared__ double s_lx, s_ly;
+  if (threadIdx.x == 0) {
+    s_dt = step_dt2(a);
+    s_lx = s_dt / a.dx;
+    s_ly = s_dt / a.dy;
+  }
   constexpr int CELLS = TW2 * TW2;
   for (int q = threadIdx.x; q < S * CELLS; q += NT) {
     const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW2, xx = rem - yy * TW2;
@@ -517,23 +529,20 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     const long gi = ((long)c * NYl + gy) * NXl + gx;
     if constexpr (F32) {
       const float *u = static_cast<const float *>(a.u_in);
-      const float h = u[gi], w = u[(long)S * NYl * NXl + gi];
-      thi[c][yy][xx] = h;
-      tlo[c][yy][xx] = w;
-      tile[c][yy][xx] = (double)h + (double)w;
+      thi[c][yy][xx] = u[gi];
+      tlo[c][yy][xx] = u[(long)S * NYl * NXl + gi];
     } else {
       tile[c][yy][xx] = static_cast<const double *>(a.u_in)[gi];
     }
   }
   __syncthreads();
-  const double dt = s_dt;
-  const double lxd = dt / a.dx, lyd = dt / a.dy;
+  const double lxd = s_lx, lyd = s_ly;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane >> 4, l = lane & 15, base = grp * 16;
   const unsigned gmask = 0xffffu << base;
   constexpr int CS = TW2 * TW2, RS = TW2;
   constexpr int NPAIR = 2 * (P - 1) * S;
-  const FiltConst FC = filt_const(a.eps, a.thr, a.fact_tau);
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
 
   for (int round = 0; round < NA * NA / 16; round++) {
     const int an = round * 16 + warp * 2 + grp;
@@ -543,18 +552,19 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     const bool needF = inside && ay >= 0;
     const bool needG = inside && ax >= 0;
     const int tx = ax + GH2, ty = ay + GH2;
-    const double *q64 = &tile[0][ty][tx];
+    const double *q64 = F32 ? nullptr : &tile[0][F32 ? 0 : ty][F32 ? 0 : tx];
     // --- dimension-by-dimension order selection -------------------------------
     unsigned rej = 0;
     if (P >= 2) {
       for (int qq = l; qq < NPAIR; qq += 16) {
-        const int dir = qq / ((P - 1) * S), rem = qq - dir * ((P - 1) * S);
+        constexpr int PS = (P > 1 ? P - 1 : 1) * S;
+        const int dir = qq / PS, rem = qq - dir * PS;
         const int p = 2 + rem / S, c = rem - (rem / S) * S;
         if (dir == 0 ? !needF : !needG) continue;
         bool ok;
         if constexpr (F32)
-          ok = admit32_p(p, &thi[c][ty][tx], &tlo[c][ty][tx], q64 + c * CS, dir == 0 ? 1 : RS, c == 0,
-                         FC, a.eps, a.thr, a.fact_tau[p]);
+          ok = admit32_p(p, &thi[c][ty][tx], &tlo[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps,
+                         a.thr, a.fact_tau[p]);
         else
           ok = admit64_p(p, q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau[p]);
         if (!ok) rej |= 1u << (dir * (P - 1) + (p - 2));
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     if (l == 0 && (flF || flG)) {
       R F1[S], G1[S];
       if constexpr (F32) {
-        flcat2_2d_f32<FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], q64, CS, RS, flF, flG, (float)lxd,
+        flcat2_2d_f32<FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, flF, flG, (float)lxd,
                             (float)lyd, (float)a.adv[0], (float)a.adv[1], (float)a.gamma, a.adv[0],
                             a.adv[1], a.limiter_form, F1, G1);
       } else {
@@ -622,7 +632,7 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     const int tx = cx + GH2, ty = cy + GH2;
     double un[S];
     if constexpr (F32) {
-      float uc[S], dlx[S], dly[S], Bx[S], By[S], junk[S];
+      float uc[S], dlx[S], dly[S], Bx[S], By[S], junk[S], hf[S], lf[S];
 #pragma unroll
       for (int c = 0; c < S; c++) {
         uc[c] = thi[c][ty][tx];
@@ -650,8 +660,24 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
         const long gi = ((long)c * NYl + gy) * NXl + gx;
         uo[gi] = hn;
         uo[(long)S * NYl * NXl + gi] = ln;
-        un[c] = (double)hn + (double)ln;
+        hf[c] = hn;
+        lf[c] = ln;
       }
+      // wave speeds in float; a state that looks non-physical is re-checked in FP64
+      const float g = (float)a.gamma;
+      const float sxf = PH::fspeed(hf, (float)a.adv[0], (float)a.adv[1], g, 0);
+      const float syf = PH::fspeed(hf, (float)a.adv[0], (float)a.adv[1], g, 1);
+      if (!PH::fphysical(hf, g)) {
+#pragma unroll
+        for (int c = 0; c < S; c++) un[c] = (double)hf[c] + (double)lf[c];
+        double sx, sy;
+        bool ok;
+        PH::speed2(un, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
+        bad |= !ok;
+      }
+      mx = fmax(mx, (double)sxf);
+      my = fmax(my, (double)syf);
+      continue;
     } else {
       double *uo = static_cast<double *>(a.u_out);
 #pragma unroll

@@ -152,6 +152,21 @@ int acat_run(acat_ctx *ctx, void *u_dev, int nsteps, double t_end, void *stream,
 int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int nsteps, double t_end,
                   void *stream, double *t_host);
 
+/* Adjoint (transposed Jacobian) of one 1D FP64 step:
+ *   ubar_n = (d u^{n+1} / d u^n)^T ubar_np1,
+ * with u^{n+1} = step(u^n) taken with the time step dt (treated as a
+ * constant: the dt the forward step used) and every discrete choice frozen as
+ * the forward step takes it at u_n: the selected orders (Eqs. 3.2-3.3) and,
+ * for FL-CAT2 interfaces (Eq. 3.4), the superbee piece, the upwind side or the
+ * (component, side) of the limiter minimum, and the Rusanov maximum. All else
+ * -- the CAT2p recursion of Sec. 2.2, the limiter value inside its piece, the
+ * Rusanov speed -- is differentiated. u_n, ubar_np1, ubar_n: device FP64
+ * states [s][nx]; ubar_n must not alias ubar_np1. Uses a context-owned
+ * scratch array ((nx+1) x max(2P,4) x s doubles, allocated on first use).
+ * Errors: INVALID_ARG, UNSUPPORTED (2D, batched or FP32 contexts), NOMEM, CUDA. */
+int acat_adjoint_step(acat_ctx *ctx, const void *u_n_dev, double dt, const void *ubar_np1_dev,
+                      void *ubar_n_dev, void *stream);
+
 /* Largest state, in bytes, that acat_run_noalloc accepts: 8 MiB, i.e.
  * 349525 cells of 1D Euler or 1048576 cells of a scalar law in FP64. */
 #define ACAT_NOALLOC_MAX_STATE (8u << 20)

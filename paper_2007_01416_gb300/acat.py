@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
         L.acat_strerror.restype = ctypes.c_char_p
         L.acat_launch_count.argtypes = [vp]
         L.acat_launch_count.restype = ctypes.c_int64
+        L.acat_adjoint_step.argtypes = [vp, vp, d, vp, vp, vp]
         L.acat_measure_fma_peak.argtypes = [i, vp]
         L.acat_measure_fma_peak.restype = ctypes.c_double
         _lib = L
@@ -188,6 +189,10 @@ class Context:
                                    float(t_end), _stream(stream), t),
                "acat_run_host")
         return list(t) if self.n_inst else t[0]
+
+    def acat_adjoint_step(self, u_n, dt: float, ubar_np1, ubar_n, stream=None):
+        _check(lib().acat_adjoint_step(self._h, _ptr(u_n), float(dt), _ptr(ubar_np1), _ptr(ubar_n),
+                                       _stream(stream)), "acat_adjoint_step")
 
     def acat_status(self) -> int:
         f = ctypes.c_uint(0)

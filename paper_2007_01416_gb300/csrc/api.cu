@@ -38,6 +38,7 @@ struct acat_ctx {
   long long ntiles = 0;
   unsigned long long *d_smaxb = nullptr;  // 3 x B
   double *d_tb = nullptr;                 // 3 x B
+  double *d_contrib = nullptr;            // adjoint: per-interface node cotangents
 };
 
 namespace {
@@ -382,6 +383,7 @@ int acat_destroy(acat_ctx *c) {
   cudaFree(c->d_tiles);
   cudaFree(c->d_smaxb);
   cudaFree(c->d_tb);
+  cudaFree(c->d_contrib);
   delete c;
   return ACAT_OK;
 }
@@ -533,6 +535,25 @@ int acat_run_host(acat_ctx *c, const void *u_host_in, void *u_host_out, int nste
   if (t_host && cudaMemcpyAsync(t_host, d_tfin, nt * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return ACAT_ERR_CUDA;
   return cuda_err(cudaStreamSynchronize(st));
+}
+
+int acat_adjoint_step(acat_ctx *c, const void *u_n, double dt, const void *ubar_np1, void *ubar_n,
+                      void *stream) {
+  if (!c || !u_n || !ubar_np1 || !ubar_n || ubar_np1 == ubar_n) return ACAT_ERR_INVALID_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return ACAT_ERR_INVALID_ARG;
+  if (c->dim != 1 || c->batched || c->p.precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;
+  if (!c->d_contrib) {
+    const size_t n = (size_t)(c->p.nx + 1) * (size_t)acat_adjoint_slots(c->p.P) * (size_t)c->s;
+    cudaError_t e = cudaMalloc(&c->d_contrib, n * sizeof(double));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+  }
+  Step1DArgs a = base_args(c);
+  a.u_in = u_n;
+  a.dt_fixed = dt;
+  int e = acat_launch_adjoint1d(c->p.P, c->p.flux, a, static_cast<const double *>(ubar_np1), c->d_contrib,
+                                static_cast<double *>(ubar_n), stream);
+  c->launches += 2;
+  return e ? ACAT_ERR_CUDA : ACAT_OK;
 }
 
 int acat_status(acat_ctx *c, unsigned *flags) {

@@ -34,66 +34,9 @@
 // (Knuth's TwoSum, then Dekker's Fast2Sum).
 #include <type_traits>
 
-#include "device_common.cuh"
+#include "phys1d.cuh"
 
 namespace {
-
-// ---------------------------------------------------------------------------
-// Physics
-// ---------------------------------------------------------------------------
-template <int FLUX>
-struct Phys;
-
-template <>
-struct Phys<ACAT_FLUX_LINEAR> {
-  static constexpr int S = 1;
-  template <typename R>
-  __device__ static __forceinline__ void flux(const R *u, R *f, R a, R /*gm1*/) { f[0] = a * u[0]; }
-  __device__ static __forceinline__ double speed(const double *u, double a, double, bool &ok) {
-    ok = isfinite(u[0]);
-    return fabs(a);
-  }
-};
-
-template <>
-struct Phys<ACAT_FLUX_BURGERS> {
-  static constexpr int S = 1;
-  template <typename R>
-  __device__ static __forceinline__ void flux(const R *u, R *f, R, R) { f[0] = R(0.5) * u[0] * u[0]; }
-  __device__ static __forceinline__ double speed(const double *u, double, double, bool &ok) {
-    ok = isfinite(u[0]);
-    return fabs(u[0]);
-  }
-};
-
-template <>
-struct Phys<ACAT_FLUX_EULER1D> {
-  static constexpr int S = 3;
-  template <typename R>
-  __device__ static __forceinline__ void flux(const R *u, R *f, R, R gm1) {
-    const R ri = recip(u[0]);
-    const R v = u[1] * ri;
-    const R p = gm1 * (u[2] - R(0.5) * u[1] * v);
-    f[0] = u[1];
-    f[1] = u[1] * v + p;
-    f[2] = v * (u[2] + p);
-  }
-  // |v| + c with c = sqrt(gamma p / rho), every operation rounded as written
-  // (no contraction), so that the CFL dt is reproducible bit for bit
-  __device__ static __forceinline__ double speed(const double *u, double, double gamma, bool &ok) {
-    const double v = __ddiv_rn(u[1], u[0]);
-    const double ke = __dmul_rn(__dmul_rn(__dmul_rn(0.5, u[0]), v), v);
-    const double p = __dmul_rn(__dsub_rn(gamma, 1.0), __dsub_rn(u[2], ke));
-    ok = (u[0] > 0.0) && (p > 0.0) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
-    return __dadd_rn(fabs(v), __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), u[0])));
-  }
-};
-
-// psi^1 of a 1D interface (cells consecutive in the tile).
-template <int FLUX>
-__device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form, double adv) {
-  return psi1_line<Phys<FLUX>::S>(q, cs, 1, FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, adv);
-}
 
 // ---------------------------------------------------------------------------
 // CAT2p flux of one interface by a group of 2p lanes (lane l <-> node
@@ -439,50 +382,6 @@ __device__ double step_dt(const Step1DArgs &a) {
     a.smax[(a.slot + 2) % 3] = 0ull;
   }
   return dt;
-}
-
-template <int P>
-struct Tiling {
-  static constexpr int L = 2 * P;             // lanes per interface
-  static constexpr int GPW = 32 / L;          // interface groups per warp
-  static constexpr int NI = (NT / 32) * GPW;  // interfaces per CTA
-  static constexpr int T = NI - 1;            // cells per CTA
-  static constexpr int GH = P > 2 ? P : 2;    // ghost cells each side
-  static constexpr int TW = T + 2 * GH;       // staged cells
-};
-
-// Order selection of the interface of lane group `grp`: the (p, component)
-// pairs p = 2..P are spread over the group's lanes, each lane evaluating
-// psi^p of one component; a group OR-reduction of the rejected orders gives
-// p_s = max A (1 when A is empty). A component's psi is admissible when
-// psi >= thr; as in a literal minimum over components taken from the first
-// component, a NaN in the first component rejects p and a NaN elsewhere is
-// ignored. Must be called by all 32 lanes.
-template <int P, int S, bool F32>
-__device__ __forceinline__ int select_order(const double *t0, const float *h0, const float *l0, int cs,
-                                            int l, int grp, bool active, bool valid,
-                                            const FiltConst &FC, double eps, double thr,
-                                            const double *fact) {
-  using TL = Tiling<P>;
-  if (P < 2) return 1;
-  constexpr int NPAIR = (P - 1) * S;
-  unsigned rej = 0;
-  if (active) {
-    for (int q = l; q < NPAIR; q += TL::L) {
-      const int p = 2 + q / S, c = q - (q / S) * S;
-      bool ok;
-      if constexpr (F32)
-        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
-      else
-        ok = admit64_p(p, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
-      if (!ok) rej |= 1u << (p - 2);
-    }
-  }
-  constexpr unsigned spare = (TL::GPW * TL::L >= 32) ? 0u : (0xffffffffu << (TL::GPW * TL::L));
-  const unsigned gmask = valid ? (((1u << TL::L) - 1u) << (grp * TL::L)) : spare;
-  rej = __reduce_or_sync(gmask, rej);
-  const unsigned accept = ~rej & ((1u << (P - 1)) - 1u);
-  return accept ? (32 - __clz(accept)) + 1 : 1;
 }
 
 // Shared-memory workspace of one 1D tile.
@@ -971,5 +870,6 @@ int acat_upload_tables_current_device() {
   acat_build_tables(&T);
   int e = acat_upload_tables_1d(&T);
   if (e == 0) e = acat_upload_tables_2d(&T);
+  if (e == 0) e = acat_upload_tables_adj(&T);
   return e;
 }

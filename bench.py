@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "batch_f32"],
+                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "batch_f32", "adjoint"],
                     help="profiling runs: one short measurement of a single workload")
     return ap.parse_args()
 
@@ -313,6 +313,71 @@ def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
             "order_mix": {str(k): round(h[k] / (M + len(sizes)), 4) for k in range(1, 5)}}
 
 
+def measure_adjoint(torch, acat, W, K, flush, steps=2000):
+    """Gradient of the L2 misfit L = dx/2 sum |u^n - u_target|^2 for the 1D
+    Euler acoustic pulse (P = 2, N = 8192, periodic, 2000 steps, target from a
+    second seed): the recorded forward run plus the reverse run (recompute per
+    sqrt(n) segment + adjoint steps), against the plain FP64 forward run."""
+    from paper_2007_01416_gb300 import adjoint as A
+    c = W.acoustic_pulse(nx=8192, seed=SEED, P=2, steps=steps)
+    tc = W.acoustic_pulse(nx=8192, seed=SEED + 1, P=2, steps=steps)
+    n, nx = c.steps, c.nx
+    dx = (c.x1 - c.x0) / nx
+    ctx = acat.Context(**c.problem_kwargs())
+    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    target = torch.from_numpy(tc.u0.copy()).cuda()
+    ctx.acat_run(target, n)
+    every = A.default_every(n)
+    ckpt = torch.empty((-(-n // every),) + tuple(u0.shape), dtype=torch.float64, device="cuda")
+    dts = torch.empty(n, dtype=torch.float64, device="cuda")
+    uN, g, u = torch.empty_like(u0), torch.empty_like(u0), torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    u.copy_(u0)
+    ctx.acat_run(u, 96)
+    m = min(n, 64)
+    ctx.acat_run_record(u0, uN, m, every, ckpt, dts)
+    ctx.acat_adjoint_run(ckpt, dts, m, every, uN, g)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    tf, tr, ta = [], [], []
+    for _ in range(K):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        flush.zero_()
+        u.copy_(u0)
+        e[0].record(stream)
+        ctx.acat_run(u, n)
+        e[1].record(stream)
+        flush.zero_()
+        e[2].record(stream)
+        ctx.acat_run_record(u0, uN, n, every, ckpt, dts)
+        g.copy_(uN).sub_(target).mul_(dx)  # dL/du^n
+        ctx.acat_adjoint_run(ckpt, dts, n, every, g, g)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        tf.append(e[0].elapsed_time(e[1]))
+        tr.append(e[2].elapsed_time(e[3]))
+    assert ctx.acat_status() == 0
+    # the reverse run alone
+    for _ in range(K):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        g.copy_(uN).sub_(target).mul_(dx)
+        e0.record(stream)
+        ctx.acat_adjoint_run(ckpt, dts, n, every, g, g)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ta.append(e0.elapsed_time(e1))
+    launches = ctx.launch_count() - l0
+    ctx.close()
+    t_f, t_g, t_a = min(tf), min(tr), min(ta)
+    recompute = (n - len(ckpt)) * t_f / n
+    return {"value": nx * n / (t_g * 1e-3), "unit": "gradient cell-updates/s", "steps": n, "nx": nx,
+            "checkpoint_every": every, "ms_forward_plain": t_f, "ms_gradient": t_g, "ms_reverse_run": t_a,
+            "gradient_vs_forward_time": t_g / t_f,
+            "adjoint_step_vs_forward_step_est": (t_a - recompute) / t_f,
+            "launches": launches}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -415,6 +480,8 @@ def run_ours(args):
         b32["speedup_vs_f64_per_cell_update"] = b32["value"] / b64["value"]
         variants["batched_euler_P3_4096inst_f32"] = b32
         variants["batched_euler_P3_4096inst_f64"] = b64
+        # gradient through 2000 steps (hand-written adjoint, sqrt(n) checkpoints)
+        variants["adjoint_euler_P2_8192_f64"] = measure_adjoint(torch, acat, W, 2, flush)
 
     if rank != 0:
         return 0
@@ -466,6 +533,8 @@ def run_single(args):
         f32 = args.workload == "2d_f32"
         out = measure_2d(torch, acat, W, flops, 4096 if f32 else 1024,
                          acat.PREC_F32 if f32 else acat.PREC_F64, n, 1, flush, 1.0)
+    elif args.workload == "adjoint":
+        out = measure_adjoint(torch, acat, W, 1, flush, steps=n)
     else:
         out = measure_batch(torch, acat, W, flops, acat.PREC_F32, n, 1, flush, 1.0)
     print(json.dumps({"workload": args.workload, **{k: v for k, v in out.items()

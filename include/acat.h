@@ -167,6 +167,30 @@ int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int ns
 int acat_adjoint_step(acat_ctx *ctx, const void *u_n_dev, double dt, const void *ubar_np1_dev,
                       void *ubar_n_dev, void *stream);
 
+/* Forward run that records what the reverse run needs (1D FP64 contexts).
+ * Takes nsteps CFL steps (as acat_run, without t_end) from u0_dev, which is
+ * not modified, and writes u^nsteps to u_out_dev.
+ *   every >= 1: checkpoint interval; the state before step n, for every n
+ *     with n % every == 0, goes to ckpt_dev + (n / every) * state_bytes, so
+ *     ckpt_dev holds ceil(nsteps / every) states (caller-owned).
+ *   dts_dev: nsteps doubles (caller-owned), receives the dt of each step.
+ * u0_dev, u_out_dev and ckpt_dev must not overlap. Device memory beyond the
+ * context's is not allocated. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int acat_run_record(acat_ctx *ctx, const void *u0_dev, void *u_out_dev, int nsteps, int every,
+                    void *ckpt_dev, double *dts_dev, void *stream);
+
+/* Reverse run over a recorded forward run: ubar_0 = J_1^T ... J_nsteps^T
+ * ubar_n, where J_k is the Jacobian of step k at the recorded dt with the
+ * discrete choices frozen as in acat_adjoint_step. The states of each
+ * checkpoint segment are recomputed from its checkpoint with the recorded dt
+ * (bit-identical to the forward run) into a context-owned buffer of every-1
+ * states, allocated on first use and grown on demand; then the adjoint steps
+ * run in reverse. ckpt_dev, dts_dev, nsteps, every: as given to
+ * acat_run_record. ubar_n_dev, ubar_0_dev: device FP64 states [s][nx]; they
+ * may be the same buffer. Errors: INVALID_ARG, UNSUPPORTED, NOMEM, CUDA. */
+int acat_adjoint_run(acat_ctx *ctx, const void *ckpt_dev, const double *dts_dev, int nsteps, int every,
+                     const void *ubar_n_dev, void *ubar_0_dev, void *stream);
+
 /* Largest state, in bytes, that acat_run_noalloc accepts: 8 MiB, i.e.
  * 349525 cells of 1D Euler or 1048576 cells of a scalar law in FP64. */
 #define ACAT_NOALLOC_MAX_STATE (8u << 20)

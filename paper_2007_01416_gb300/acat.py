@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         L.acat_launch_count.argtypes = [vp]
         L.acat_launch_count.restype = ctypes.c_int64
         L.acat_adjoint_step.argtypes = [vp, vp, d, vp, vp, vp]
+        L.acat_run_record.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
+        L.acat_adjoint_run.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
         L.acat_measure_fma_peak.argtypes = [i, vp]
         L.acat_measure_fma_peak.restype = ctypes.c_double
         _lib = L
@@ -193,6 +195,14 @@ class Context:
     def acat_adjoint_step(self, u_n, dt: float, ubar_np1, ubar_n, stream=None):
         _check(lib().acat_adjoint_step(self._h, _ptr(u_n), float(dt), _ptr(ubar_np1), _ptr(ubar_n),
                                        _stream(stream)), "acat_adjoint_step")
+
+    def acat_run_record(self, u0, u_out, nsteps: int, every: int, ckpt, dts, stream=None):
+        _check(lib().acat_run_record(self._h, _ptr(u0), _ptr(u_out), int(nsteps), int(every), _ptr(ckpt),
+                                     _ptr(dts), _stream(stream)), "acat_run_record")
+
+    def acat_adjoint_run(self, ckpt, dts, nsteps: int, every: int, ubar_n, ubar_0, stream=None):
+        _check(lib().acat_adjoint_run(self._h, _ptr(ckpt), _ptr(dts), int(nsteps), int(every), _ptr(ubar_n),
+                                      _ptr(ubar_0), _stream(stream)), "acat_adjoint_run")
 
     def acat_status(self) -> int:
         f = ctypes.c_uint(0)

@@ -1,13 +1,13 @@
 """Gradients through n ACAT steps with respect to the initial state.
 
-ACATRun is a torch.autograd.Function over the C ABI: the forward pass runs
-the steps on the device (acat_step, CFL dt computed on the device and
-recorded), keeping the state every `every` steps (default round(sqrt(n)));
-the backward pass walks the segments from the last, recomputes each
-segment's states from its checkpoint with the recorded dt (bit-identical to
-the forward), and applies the hand-written adjoint step (acat_adjoint_step)
-in reverse. The discrete choices of every step and its dt are those of the
-forward pass. Only argument marshalling happens here.
+ACATRun is a torch.autograd.Function over the C ABI. The forward pass is
+acat_run_record: n CFL steps on the device, the dt of each step recorded on
+the device, the state kept every `every` steps (default round(sqrt(n))). The
+backward pass is acat_adjoint_run: segment by segment from the last, the
+states are recomputed from the checkpoint with the recorded dt (bit-identical
+to the forward) and the hand-written adjoint step is applied in reverse. The
+discrete choices of every step and its dt are those of the forward pass.
+Only argument marshalling happens here; no step returns to the host.
 """
 from __future__ import annotations
 
@@ -15,44 +15,35 @@ import math
 
 import torch
 
-from . import acat
+
+def default_every(nsteps: int) -> int:
+    return max(1, int(round(math.sqrt(max(nsteps, 1)))))
 
 
 class ACATRun(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u0, actx, nsteps: int, every: int = 0):
-        every = every or max(1, int(round(math.sqrt(max(nsteps, 1)))))
+        every = every or default_every(nsteps)
+        u0 = u0.detach().contiguous()
+        nck = max(1, -(-nsteps // every))
+        ckpt = torch.empty((nck,) + tuple(u0.shape), dtype=u0.dtype, device=u0.device)
         dts = torch.empty(max(nsteps, 1), dtype=torch.float64, device=u0.device)
-        ckpts = []
-        u = u0.detach().contiguous().clone()
-        nxt = torch.empty_like(u)
-        for n in range(nsteps):
-            if n % every == 0:
-                ckpts.append(u.clone())
-            actx.acat_step(u, nxt, -1.0, None, dts[n:n + 1], None)
-            u, nxt = nxt, u
-        ctx.save_for_backward(dts, *ckpts)
+        out = torch.empty_like(u0)
+        if nsteps == 0:
+            out.copy_(u0)
+        else:
+            actx.acat_run_record(u0, out, nsteps, every, ckpt, dts)
+        ctx.save_for_backward(ckpt, dts)
         ctx.actx, ctx.nsteps, ctx.every = actx, nsteps, every
-        return u.clone()
+        return out
 
     @staticmethod
     def backward(ctx, gN):
-        dts, *ckpts = ctx.saved_tensors
-        actx, nsteps, every = ctx.actx, ctx.nsteps, ctx.every
-        ub = gN.detach().contiguous().clone()
-        ub2 = torch.empty_like(ub)
-        dt = dts.cpu().tolist()
-        for seg in reversed(range(len(ckpts))):
-            start, end = seg * every, min(nsteps, (seg + 1) * every)
-            states = [ckpts[seg]]
-            for n in range(start, end - 1):
-                nxt = torch.empty_like(ub)
-                actx.acat_step(states[-1], nxt, dt[n])
-                states.append(nxt)
-            for n in reversed(range(start, end)):
-                actx.acat_adjoint_step(states[n - start], dt[n], ub, ub2)
-                ub, ub2 = ub2, ub
-        return ub, None, None, None
+        ckpt, dts = ctx.saved_tensors
+        g = gN.detach().contiguous().clone()
+        if ctx.nsteps > 0:
+            ctx.actx.acat_adjoint_run(ckpt, dts, ctx.nsteps, ctx.every, g, g)
+        return g, None, None, None
 
 
 def run(u0: torch.Tensor, actx, nsteps: int, every: int = 0) -> torch.Tensor:

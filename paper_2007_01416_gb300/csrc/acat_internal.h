@@ -38,6 +38,7 @@ struct Step1DArgs {
   int slot;                   // step index mod 3 (dt-reduction slots)
   double dx, cfl;
   double dt_fixed;            // > 0: imposed dt
+  const double *dt_in;        // device: imposed dt (nullable; takes precedence)
   double t_end;               // > 0: clip t at t_end
   double gamma, adv, eps, thr;
   double fact_tau[ACAT_MAXP + 1];
@@ -101,7 +102,7 @@ int acat_launch_smax2d(int flux, int prec, const Step2DArgs &a, void *stream);
 int acat_upload_tables_1d(const AcatTables *T);
 int acat_upload_tables_adj(const AcatTables *T);
 int acat_adjoint_slots(int P);
-// Adjoint of one 1D FP64 step (a.u_in = u^n, a.dt_fixed = dt): ubar0 from ubar1.
+// Adjoint of one 1D FP64 step (a.u_in = u^n, dt from a.dt_in or a.dt_fixed): ubar0 from ubar1.
 int acat_launch_adjoint1d(int P, int flux, const Step1DArgs &a, const double *ubar1, double *contrib,
                           double *ubar0, void *stream);
 int acat_upload_tables_2d(const AcatTables *T);

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(NT) k_adj1d(const Step1DArgs a, const double *
     tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
   }
   __syncthreads();
-  const double lam = a.dt_fixed / a.dx;
+  const double lam = (a.dt_in ? *a.dt_in : a.dt_fixed) / a.dx;
   const double gm1 = a.gamma - 1.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / TL::L, l = lane - grp * TL::L;

@@ -3,6 +3,7 @@
 // the time loop with the dt reduction kept on the device), status words.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -39,6 +40,9 @@ struct acat_ctx {
   unsigned long long *d_smaxb = nullptr;  // 3 x B
   double *d_tb = nullptr;                 // 3 x B
   double *d_contrib = nullptr;            // adjoint: per-interface node cotangents
+  void *d_seg = nullptr;                  // adjoint run: recomputed states of a segment
+  size_t seg_bytes = 0;
+  void *d_bar = nullptr;                  // adjoint run: second cotangent buffer
 };
 
 namespace {
@@ -384,6 +388,8 @@ int acat_destroy(acat_ctx *c) {
   cudaFree(c->d_smaxb);
   cudaFree(c->d_tb);
   cudaFree(c->d_contrib);
+  cudaFree(c->d_seg);
+  cudaFree(c->d_bar);
   delete c;
   return ACAT_OK;
 }
@@ -537,23 +543,133 @@ int acat_run_host(acat_ctx *c, const void *u_host_in, void *u_host_out, int nste
   return cuda_err(cudaStreamSynchronize(st));
 }
 
+namespace {
+
+int ensure_contrib(acat_ctx *c) {
+  if (c->d_contrib) return ACAT_OK;
+  const size_t n = (size_t)(c->p.nx + 1) * (size_t)acat_adjoint_slots(c->p.P) * (size_t)c->s;
+  cudaError_t e = cudaMalloc(&c->d_contrib, n * sizeof(double));
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+  return ACAT_OK;
+}
+
+int adjoint_launch(acat_ctx *c, const void *u_n, double dt, const double *dt_dev, const void *ubar1,
+                   void *ubar0, cudaStream_t st) {
+  Step1DArgs a = base_args(c);
+  a.u_in = u_n;
+  a.dt_fixed = dt;
+  a.dt_in = dt_dev;
+  int e = acat_launch_adjoint1d(c->p.P, c->p.flux, a, static_cast<const double *>(ubar1), c->d_contrib,
+                                static_cast<double *>(ubar0), st);
+  c->launches += 2;
+  return e ? ACAT_ERR_CUDA : ACAT_OK;
+}
+
+bool adjoint_ctx(const acat_ctx *c) {
+  return c->dim == 1 && !c->batched && c->p.precision == ACAT_PREC_F64;
+}
+
+}  // namespace
+
 int acat_adjoint_step(acat_ctx *c, const void *u_n, double dt, const void *ubar_np1, void *ubar_n,
                       void *stream) {
   if (!c || !u_n || !ubar_np1 || !ubar_n || ubar_np1 == ubar_n) return ACAT_ERR_INVALID_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return ACAT_ERR_INVALID_ARG;
-  if (c->dim != 1 || c->batched || c->p.precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;
-  if (!c->d_contrib) {
-    const size_t n = (size_t)(c->p.nx + 1) * (size_t)acat_adjoint_slots(c->p.P) * (size_t)c->s;
-    cudaError_t e = cudaMalloc(&c->d_contrib, n * sizeof(double));
+  if (!adjoint_ctx(c)) return ACAT_ERR_UNSUPPORTED;
+  int rc = ensure_contrib(c);
+  if (rc) return rc;
+  return adjoint_launch(c, u_n, dt, nullptr, ubar_np1, ubar_n, static_cast<cudaStream_t>(stream));
+}
+
+int acat_run_record(acat_ctx *c, const void *u0, void *u_out, int nsteps, int every, void *ckpt,
+                    double *dts, void *stream) {
+  if (!c || !u0 || !u_out || u0 == u_out || nsteps < 0 || every < 1) return ACAT_ERR_INVALID_ARG;
+  if (nsteps > 0 && (!ckpt || !dts)) return ACAT_ERR_INVALID_ARG;
+  if (!adjoint_ctx(c)) return ACAT_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sb = (size_t)acat_state_bytes(c);
+  if (cudaMemsetAsync(c->d_smax, 0, 6 * sizeof(unsigned long long), st) != cudaSuccess) return ACAT_ERR_CUDA;
+  Step1DArgs a = base_args(c);
+  a.tslot = c->d_t;
+  a.u_in = u0;
+  a.slot = 0;
+  if (acat_launch_smax1d(c->p.flux, c->p.precision, a, st)) return ACAT_ERR_CUDA;
+  c->launches++;
+  const void *cur = u0;
+  for (long n = 0; n < nsteps; n++) {
+    if (n % every == 0 &&
+        cudaMemcpyAsync(static_cast<char *>(ckpt) + (size_t)(n / every) * sb, cur, sb, cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess)
+      return ACAT_ERR_CUDA;
+    void *nxt = (cur == u_out) ? c->d_work : u_out;
+    a.u_in = cur;
+    a.u_out = nxt;
+    a.slot = (int)(n % 3);
+    a.dt_out = dts + n;
+    int rc = launch_step(c, a, st);
+    if (rc) return rc;
+    cur = nxt;
+  }
+  if (cur != u_out && cudaMemcpyAsync(u_out, cur, sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  return ACAT_OK;
+}
+
+int acat_adjoint_run(acat_ctx *c, const void *ckpt, const double *dts, int nsteps, int every, const void *ubar_n,
+                     void *ubar_0, void *stream) {
+  if (!c || !ubar_n || !ubar_0 || nsteps < 0 || every < 1) return ACAT_ERR_INVALID_ARG;
+  if (nsteps > 0 && (!ckpt || !dts)) return ACAT_ERR_INVALID_ARG;
+  if (!adjoint_ctx(c)) return ACAT_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sb = (size_t)acat_state_bytes(c);
+  int rc = ensure_contrib(c);
+  if (rc) return rc;
+  const size_t need = (size_t)(every - 1) * sb;
+  if (need > c->seg_bytes) {
+    if (c->d_seg && cudaStreamSynchronize(st) != cudaSuccess) return ACAT_ERR_CUDA;
+    cudaFree(c->d_seg);
+    c->d_seg = nullptr;
+    c->seg_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->d_seg, need);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+    c->seg_bytes = need;
+  }
+  if (!c->d_bar) {
+    cudaError_t e = cudaMalloc(&c->d_bar, sb);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
   }
+  if (ubar_n != ubar_0 && cudaMemcpyAsync(ubar_0, ubar_n, sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  // the cotangent lives in ubar_0 between steps, d_bar takes the odd copies
+  void *cur = ubar_0;
   Step1DArgs a = base_args(c);
-  a.u_in = u_n;
-  a.dt_fixed = dt;
-  int e = acat_launch_adjoint1d(c->p.P, c->p.flux, a, static_cast<const double *>(ubar_np1), c->d_contrib,
-                                static_cast<double *>(ubar_n), stream);
-  c->launches += 2;
-  return e ? ACAT_ERR_CUDA : ACAT_OK;
+  const int nseg = (nsteps + every - 1) / every;
+  for (int seg = nseg - 1; seg >= 0; seg--) {
+    const long start = (long)seg * every;
+    const long end = std::min((long)nsteps, start + every);
+    const char *base = static_cast<const char *>(ckpt) + (size_t)seg * sb;
+    auto state = [&](long n) -> const void * {
+      return n == start ? static_cast<const void *>(base)
+                        : static_cast<const void *>(static_cast<char *>(c->d_seg) + (size_t)(n - start - 1) * sb);
+    };
+    for (long n = start; n < end - 1; n++) {
+      a.u_in = state(n);
+      a.u_out = const_cast<void *>(state(n + 1));
+      a.slot = 0;
+      a.dt_in = dts + n;
+      rc = launch_step(c, a, st);
+      if (rc) return rc;
+    }
+    for (long n = end - 1; n >= start; n--) {
+      void *nxt = (cur == ubar_0) ? c->d_bar : ubar_0;
+      rc = adjoint_launch(c, state(n), -1.0, dts + n, cur, nxt, st);
+      if (rc) return rc;
+      cur = nxt;
+    }
+  }
+  if (cur != ubar_0 && cudaMemcpyAsync(ubar_0, cur, sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return ACAT_ERR_CUDA;
+  return ACAT_OK;
 }
 
 int acat_status(acat_ctx *c, unsigned *flags) {

@@ -357,7 +357,9 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
 // the simulated time and recycles the slot two steps ahead (block 0).
 __device__ double step_dt(const Step1DArgs &a) {
   double dt;
-  if (a.dt_fixed > 0.0) {
+  if (a.dt_in) {
+    dt = *a.dt_in;
+  } else if (a.dt_fixed > 0.0) {
     dt = a.dt_fixed;
   } else {
     const double smax = __longlong_as_double((long long)a.smax[a.slot]);

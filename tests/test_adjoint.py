@@ -239,3 +239,39 @@ def test_gradient_acoustic_pulse_finite_differences(env):
             ad = float((g * d).sum().item())
             worst = max(worst, abs(fd - ad) / max(abs(ad), 1e-12))
         assert worst < 1e-5, worst
+
+
+def test_record_and_reverse_run_checkpoint_intervals(env):
+    """The recorded forward equals acat_run, its checkpoints are the states
+    it passed, and the reverse run gives the same cotangent for every
+    checkpoint interval (the recompute is bit-identical to the forward)."""
+    torch, O, acat, adjoint = env
+    c = _state("riemann", 256, 3, 1, seed=4)
+    n = 23
+    with acat.Context(**c.problem_kwargs()) as ctx:
+        u0 = torch.from_numpy(c.u0.copy()).cuda()
+        ref = u0.clone()
+        ctx.acat_run(ref, n)
+        wN = torch.from_numpy(np.random.default_rng(5).normal(size=c.u0.shape)).cuda()
+        outs = []
+        for every in (1, 4, 7, 23, 40):
+            nck = -(-n // every)
+            ckpt = torch.empty((nck,) + tuple(u0.shape), dtype=torch.float64, device="cuda")
+            dts = torch.empty(n, dtype=torch.float64, device="cuda")
+            uN = torch.empty_like(u0)
+            ctx.acat_run_record(u0, uN, n, every, ckpt, dts)
+            assert torch.equal(uN, ref)
+            assert torch.equal(ckpt[0], u0)
+            if nck > 1:
+                v = u0.clone()
+                ctx.acat_run(v, every)
+                assert torch.equal(ckpt[1], v)
+            g = torch.empty_like(u0)
+            ctx.acat_adjoint_run(ckpt, dts, n, every, wN, g)
+            g2 = wN.clone()
+            ctx.acat_adjoint_run(ckpt, dts, n, every, g2, g2)  # in place
+            assert torch.equal(g, g2)
+            outs.append(g.cpu().numpy())
+        assert ctx.acat_status() == 0
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])

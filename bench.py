@@ -108,6 +108,36 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The maximum of x over the ranks of the default process group (the
+    slowest replica's time); x itself on a single process."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, cells_per_run: int, runs: int, max_ms: float) -> float:
+    """Whole-job throughput: every replica processes cells_per_run cell
+    updates per run, the job takes the slowest replica's time."""
+    return world * cells_per_run * runs / (max_ms * 1e-3)
+
+
+def barrier_sync(world: int, cuda: bool = True):
+    """Synchronise the device, then all ranks (both sides of a timed region)."""
+    import torch
+    if cuda:
+        torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if cuda:
+        torch.cuda.synchronize()
+
+
 def cpu_baseline(budget_s: float = 12.0, max_steps: int = 200) -> dict:
     """The CPU oracle as it stands, on a bounded sample of the workload:
     consecutive oracle steps from the seeded initial state."""
@@ -192,7 +222,8 @@ def order_hist(ctx, torch, u0, steps, nx, probes=5):
     return hists
 
 
-def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_clocks, dev_index):
+def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_clocks, dev_index,
+            world=1):
     c = W.euler1d_riemann_entropy(nx=nx, seed=SEED, P=P, steps=acat_steps, cfl=CFL)
     ctx = acat.Context(**c.problem_kwargs(), precision=prec)
     host = acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()
@@ -214,12 +245,13 @@ def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_c
     l0 = ctx.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
+    barrier_sync(world)
     for k in range(K):
         flush.zero_()  # evict L2 between timed runs (outside the timed events)
         ev[k][0].record(stream)
         one()
         ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    barrier_sync(world)
     launches = ctx.launch_count() - l0
     clk = clocks.stop() if clocks else None
     assert ctx.acat_status() == 0, "device status flags set"
@@ -397,19 +429,11 @@ def run_ours(args):
     peak64 = max(acat.acat_measure_fma_peak(0) for _ in range(3))
     peak32 = max(acat.acat_measure_fma_peak(1) for _ in range(3))
 
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F64, args.acat_steps, args.steps,
-                args.warmup, flush, rank == 0, dev_index)
-    tot_ms = sum(m["ms"])
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        dist.barrier()
+                args.warmup, flush, rank == 0, dev_index, world)
+    tot_ms = max_over_ranks(sum(m["ms"]), world)
     cells_steps = NX * args.acat_steps
-    value = world * cells_steps * args.steps / (tot_ms * 1e-3)
+    value = job_value(world, cells_steps, args.steps, tot_ms)
     ms_per_step = tot_ms / args.steps
     kernel_ms = ms_per_step / args.acat_steps  # one step kernel per ACAT step
     achieved = m["flops_per_step"] / (kernel_ms * 1e-3)
@@ -429,7 +453,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     sb = ctx.state_bytes()
-    e2e_val = cells_steps / (min(e2e_ms) * 1e-3)
+    e2e_best = max_over_ranks(min(e2e_ms), world)
+    e2e_val = job_value(world, cells_steps, 1, e2e_best)
 
     variants = {}
     if not args.no_variants and rank == 0:
@@ -502,7 +527,7 @@ def run_ours(args):
                      "flops_per_launch": m["flops_per_step"], "kernel_ms": kernel_ms,
                      "order_mix": m["order_mix"]},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb,
-                "ms_per_step": min(e2e_ms)},
+                "ms_per_step": e2e_best},
         "gpu_launches": m["launches"],
         "clocks": m["clocks"],
         "fma_peaks_tflops": {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12},

@@ -6,11 +6,14 @@
 // [i0 - GH, i0 + T + GH) are staged once in shared memory with the boundary
 // condition applied while loading. Each interface is worked by a group of 2P
 // lanes of one warp, one lane per stencil node j = -p+1..p:
-//   - lanes 0..P-2 of the group evaluate the indicators psi^{l+2}
-//     (Eqs. 3.8-3.12, minimum over components, Sec. 3.4) with explicitly
-//     rounded FP64 operations in the order of their definition, so that the
-//     order decision is bit-identical to a literal FP64 evaluation of the same
-//     state; a warp ballot then gives p_s = max A (Eqs. 3.2-3.3);
+//   - the (p, component) pairs of the indicators psi^p (Eqs. 3.8-3.12, the
+//     minimum over components of Sec. 3.4) are spread over the group's lanes.
+//     Each pair is decided by a float test with a certified error margin
+//     (psi_filter); only when the margin cannot settle it is psi^p evaluated
+//     literally with explicitly rounded FP64 operations in the order of its
+//     definition. Either way the decision is the one a literal FP64
+//     evaluation of the same state takes. An OR-reduction over the group
+//     gives p_s = max A (Eqs. 3.2-3.3);
 //   - for p_s >= 2 every lane runs the local Taylor recursion of Sec. 2.2 for
 //     its node in registers, in the dt-scaled form
 //         U^(k-1)_j = -lambda sum_r gamma^{1,j}_r F^(k-2)_r     (shuffles)
@@ -24,9 +27,11 @@
 // epilogue reduces the wave speed of the new state for the next step's CFL
 // dt into a triple-buffered slot (atomic max on ordered double bits).
 //
-// FP32 variant: the state is a compensated float pair (hi, lo). The
-// indicators, the limiter and the wave speed see the exact value hi + lo in
-// FP64. The recursion runs in float in a delta formulation (see cat_delta):
+// FP32 variant: the state is a compensated float pair (hi, lo). The order
+// decisions are those of FP64 on the exact value hi + lo (the filtered test
+// falls back to FP64 on hi + lo), and so is the limiter psi^1 of FL-CAT2
+// interfaces; the wave speed for the next step's dt is reduced in float. The
+// recursion runs in float in a delta formulation (see cat_delta):
 // every flux is carried as f(u_i) + G, G built from flux increments computed
 // in a cancellation-free form, so float rounding is relative to increments of
 // size O(dx) rather than to |f|. The update adds lambda (f(u_{i-1}) - f(u_i) +

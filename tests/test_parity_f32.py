@@ -1,5 +1,6 @@
-"""FP32 path (ACAT_PREC_F32): float recursion on a compensated (hi, lo) state,
-indicators and wave speed in FP64 on hi + lo.
+"""FP32 path (ACAT_PREC_F32): float recursion on a compensated (hi, lo) state;
+order decisions and limiter as FP64 takes them on hi + lo; the first step's
+dt from an FP64 wave-speed reduction (later steps of a run reduce in float).
 
 Bars (derived in the design doc from the arithmetic): the order codes of one step
 match the FP64 oracle bit for bit from the same state value hi + lo (the

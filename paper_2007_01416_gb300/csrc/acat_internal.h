@@ -49,6 +49,9 @@ struct Step1DArgs {
   int8_t *orders;             // N+1 order codes (nullable)
   double *dt_out;             // dt used (nullable)
   unsigned *status;           // sticky status bits
+  double *flux_buf;           // FP64 single instance: [S][N+1] CTA-edge fluxes, and
+  int *cnt;                   // one hand-off counter per CTA boundary (both nullable: the
+                              // fused 8-warp step kernel runs instead of the small-CTA one)
 };
 
 // Work description of a batch of independent 1D instances (ragged sizes),
@@ -113,4 +116,6 @@ int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream);
 int acat_launch_step1d(int P, int flux, int prec, const Step1DArgs &a, void *stream);
 int acat_upload_tables_current_device();
 int acat_cells_per_cta_1d(int P, int prec);
+// CTAs of the small-CTA FP64 step (boundary counters it needs: that many).
+int acat_fine_ctas_1d(int P, long N);
 double acat_fma_peak_run(int precision, void *stream);

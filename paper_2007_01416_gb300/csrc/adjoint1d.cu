@@ -370,16 +370,16 @@ __device__ void flcat2_adj(const double *q, int cs, double lam, double adv, doub
 // Per-interface cotangents of the stencil nodes: contrib[(m * NS + s) * S + c],
 // node j = s - NS/2 + 1.
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NT) k_adj1d(const Step1DArgs a, const double *__restrict__ ubar1,
-                                              double *__restrict__ contrib) {
-  using TL = Tiling<P>;
+__global__ void __launch_bounds__(NWF * 32) k_adj1d(const Step1DArgs a, const double *__restrict__ ubar1,
+                                                    double *__restrict__ contrib) {
+  using TL = Tiling<P, NWF>;
   constexpr int S = Phys<FLUX>::S;
   constexpr int NS = 2 * P > 4 ? 2 * P : 4;
   __shared__ double tile[S][TL::TW];
   const double *__restrict__ uin = static_cast<const double *>(a.u_in);
   const long N = a.N;
-  const long i0 = (long)blockIdx.x * TL::T;
-  for (int q = threadIdx.x; q < S * TL::TW; q += NT) {
+  const long i0 = (long)blockIdx.x * TL::NI;
+  for (int q = threadIdx.x; q < S * TL::TW; q += NWF * 32) {
     const int c = q / TL::TW, k = q - c * TL::TW;
     tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
   }
@@ -506,8 +506,8 @@ int launch_adj_f(int P, const Step1DArgs &a, const double *ub1, double *contrib,
   switch (P) {
 #define ACAT_ADJ_CASE(PP)                                                                         \
   case PP: {                                                                                      \
-    const unsigned grid = (unsigned)((a.N + Tiling<PP>::T) / Tiling<PP>::T);                      \
-    k_adj1d<PP, FLUX><<<grid, NT, 0, st>>>(a, ub1, contrib);                                      \
+    const unsigned grid = (unsigned)((a.N + Tiling<PP, NWF>::NI) / Tiling<PP, NWF>::NI);          \
+    k_adj1d<PP, FLUX><<<grid, NWF * 32, 0, st>>>(a, ub1, contrib);                                \
     k_adj_gather<PP, S><<<g2, NT, 0, st>>>(a, ub1, contrib, ub0);                                 \
   } break;
     ACAT_ADJ_CASE(1)

@@ -43,6 +43,8 @@ struct acat_ctx {
   void *d_seg = nullptr;                  // adjoint run: recomputed states of a segment
   size_t seg_bytes = 0;
   void *d_bar = nullptr;                  // adjoint run: second cotangent buffer
+  double *d_flux = nullptr;               // 1D FP64: CTA-edge fluxes of the small-CTA step
+  int *d_cnt = nullptr;                   // 1D FP64: its boundary hand-off counters
 };
 
 namespace {
@@ -110,6 +112,8 @@ Step1DArgs base_args(acat_ctx *c) {
   a.rf = (float)(a.thr / (1.0 - a.thr));
   a.smax = c->d_smax;
   a.status = c->d_status;
+  a.flux_buf = c->d_flux;
+  a.cnt = c->d_cnt;
   return a;
 }
 
@@ -299,6 +303,18 @@ int acat_create(const acat_params *p, acat_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_t, 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_work, sb);
+  // 1D FP64: the small-CTA step when the 8-warp fused step would not fit its
+  // CTAs in ~3/4 of one wave at 2 CTAs per SM (it then leaves SMs idle)
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const long fused_ctas = (p->nx + acat_cells_per_cta_1d(p->P, ACAT_PREC_F64) - 1) /
+                          acat_cells_per_cta_1d(p->P, ACAT_PREC_F64);
+  if (e == cudaSuccess && c->dim == 1 && p->precision == ACAT_PREC_F64 && 4 * fused_ctas > 3 * 2 * (long)sms) {
+    const size_t nc = (size_t)acat_fine_ctas_1d(p->P, p->nx);
+    e = cudaMalloc(&c->d_flux, (size_t)c->s * (size_t)(p->nx + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cnt, nc * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, nc * sizeof(int));
+  }
   if (e == cudaSuccess) e = cudaMemset(c->d_smax, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_t, 0, 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
@@ -333,6 +349,10 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
   // replace the single-instance workspace by the batch's
   cudaFree(c->d_work);
   c->d_work = nullptr;
+  cudaFree(c->d_flux);
+  c->d_flux = nullptr;
+  cudaFree(c->d_cnt);
+  c->d_cnt = nullptr;
   c->batched = 1;
   c->B = n_inst;
   c->cells = M;
@@ -390,6 +410,8 @@ int acat_destroy(acat_ctx *c) {
   cudaFree(c->d_contrib);
   cudaFree(c->d_seg);
   cudaFree(c->d_bar);
+  cudaFree(c->d_flux);
+  cudaFree(c->d_cnt);
   delete c;
   return ACAT_OK;
 }

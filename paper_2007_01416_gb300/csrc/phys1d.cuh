@@ -63,15 +63,22 @@ __device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form
   return psi1_line<Phys<FLUX>::S>(q, cs, 1, FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, adv);
 }
 
-template <int P>
+// Interface tiling of a CTA of NW warps: groups of L = 2P lanes, one per
+// interface; a fused step tile updates T = NI - 1 cells, a flux-only tile
+// computes NI interfaces. TW cells are staged (GH ghosts each side).
+template <int P, int NW = NT / 32>
 struct Tiling {
   static constexpr int L = 2 * P;             // lanes per interface
   static constexpr int GPW = 32 / L;          // interface groups per warp
-  static constexpr int NI = (NT / 32) * GPW;  // interfaces per CTA
+  static constexpr int NI = NW * GPW;         // interfaces per CTA
   static constexpr int T = NI - 1;            // cells per CTA
   static constexpr int GH = P > 2 ? P : 2;    // ghost cells each side
   static constexpr int TW = T + 2 * GH;       // staged cells
 };
+
+// Warps per CTA of the flux-only and adjoint kernels: small CTAs spread a
+// step's interfaces evenly over the SMs (no CTA-sized tail).
+constexpr int NWF = 2;
 
 // Order selection of the interface of lane group `grp`: the (p, component)
 // pairs p = 2..P are spread over the group's lanes, each lane evaluating

@@ -119,32 +119,44 @@ __device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R 
 }
 
 // FL-CAT2 flux (Eq. 3.4), FP64: the CAT2 flux (p = 1 recursion, Eqs.
-// 2.16-2.17) blended with Rusanov by the limiter psi^1. Single lane.
-template <int FLUX>
-__device__ __forceinline__ void flcat2_flux(const double *q, int cs, double lam, double adv,
-                                            double gamma, int limiter_form, double *F) {
+// 2.16-2.17) blended with Rusanov by the limiter psi^1. Worked by the L lanes
+// of the interface group (all of them call it): lanes of even and odd rank
+// evaluate the two nodes' fluxes and wave speeds, exchanged by shuffles, and
+// the limiter's ratios are spread over the group. Every lane returns F.
+template <int FLUX, int L>
+__device__ __forceinline__ void flcat2_flux(const double *q, int cs, int l, unsigned gmask, double lam,
+                                            double adv, double gamma, int limiter_form, double *F) {
   constexpr int S = Phys<FLUX>::S;
   const double gm1 = gamma - 1.0;
-  double u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
+  const int me = l & 1;  // node i + me
+  double u[S], f[S], a[S], t[S], u0[S], u1[S], f0[S], f1[S], t0[S], t1[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) u[c] = q[c * cs + me];
+  Phys<FLUX>::flux(u, f, adv, gm1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
+    const double o = __shfl_xor_sync(gmask, f[c], 1);
+    f0[c] = me ? o : f[c];
+    f1[c] = me ? f[c] : o;
     u0[c] = q[c * cs];
     u1[c] = q[c * cs + 1];
+    const double U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
+    a[c] = u[c] + U;
   }
-  Phys<FLUX>::flux(u0, f0, adv, gm1);
-  Phys<FLUX>::flux(u1, f1, adv, gm1);
+  Phys<FLUX>::flux(a, t, adv, gm1);
+  bool ok;
+  const double s = Phys<FLUX>::speed(u, adv, gamma, ok);
+  const double so = __shfl_xor_sync(gmask, s, 1);
+  const double s0 = me ? so : s, s1 = me ? s : so;
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const double U = -lam * (f1[c] - f0[c]);  // gamma^{1,j}_1 = (-1, 1), both nodes
-    a0[c] = u0[c] + U;
-    a1[c] = u1[c] + U;
+    const double o = __shfl_xor_sync(gmask, t[c], 1);
+    t0[c] = me ? o : t[c];
+    t1[c] = me ? t[c] : o;
   }
-  Phys<FLUX>::flux(a0, t0, adv, gm1);
-  Phys<FLUX>::flux(a1, t1, adv, gm1);
-  bool ok;
-  const double s0 = Phys<FLUX>::speed(u0, adv, gamma, ok), s1 = Phys<FLUX>::speed(u1, adv, gamma, ok);
   const double alpha = s1 > s0 ? s1 : s0;
-  const double w = psi1<FLUX>(q, cs, limiter_form, adv);
+  const double w = psi1_group<S, L>([=](int c, int k) { return q[c * cs + k]; },
+                                    FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, adv, l, gmask);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const double F1 = 0.5 * (f0[c] + f1[c]) + 0.25 * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
@@ -319,14 +331,16 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
   }
 }
 
-// FL-CAT2 increment G (F* = f(u_i) + G), single lane. With D1 = f(u_{i+1}) -
+// FL-CAT2 increment G (F* = f(u_i) + G), worked by the L lanes of the
+// interface group (all of them call it; the limiter's ratios are spread over
+// the lanes, every lane returns G). With D1 = f(u_{i+1}) -
 // f(u_i), U = -lambda D1, T0 = df(u_i; U), T1 = df(u_i; u_{i+1} - u_i + U):
 //   CAT2:    F1 - f(u_i) = (T0 + T1 + D1) / 4
 //   Rusanov: Flo - f(u_i) = D1 / 2 - alpha (u_{i+1} - u_i) / 2
-template <int FLUX>
-__device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, int cs, float lam,
-                                             float adv, float gamma, double advd, int limiter_form,
-                                             float *G) {
+template <int FLUX, int L>
+__device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, int cs, int l, unsigned gmask,
+                                             float lam, float adv, float gamma, double advd,
+                                             int limiter_form, float *G) {
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
   const float gm1 = gamma - 1.0f;
@@ -348,8 +362,9 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
   DP::dflux(b0, d1, T1);
   const float s0 = DP::speed(u0, adv, gamma), s1 = DP::speed(u1, adv, gamma);
   const float alpha = s1 > s0 ? s1 : s0;
-  const float w = (float)psi1_pair<S>(hi, lo, cs, 1, FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form,
-                                      advd);
+  const float w = (float)psi1_group<S, L>(
+      [=](int c, int k) { return (double)hi[c * cs + k] + (double)lo[c * cs + k]; },
+      FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, advd, l, gmask);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const float G1 = 0.25f * (T0[c] + T1[c] + D1[c]);
@@ -358,10 +373,19 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
   }
 }
 
-// dt of this step from the reduced wave speed (1D CFL rule); also advances
-// the simulated time and recycles the slot two steps ahead (block 0).
-__device__ double step_dt(const Step1DArgs &a) {
+// Resident CTAs per SM the step kernels are compiled for (register cap
+// 65536 / (256 x value)): enough warps to hide the recursion's latency
+// without spilling.
+template <int P, bool F32>
+struct MinCtas {
+  static constexpr int value = F32 ? 4 : 2;
+};
+
+// dt of this step from the reduced wave speed (1D CFL rule), clipped at
+// t_end; no side effects. *t receives the time at the start of the step.
+__device__ double step_dt_value(const Step1DArgs &a, double *t, bool *bad) {
   double dt;
+  *bad = false;
   if (a.dt_in) {
     dt = *a.dt_in;
   } else if (a.dt_fixed > 0.0) {
@@ -369,21 +393,31 @@ __device__ double step_dt(const Step1DArgs &a) {
   } else {
     const double smax = __longlong_as_double((long long)a.smax[a.slot]);
     if (!(smax > 0.0) || !isfinite(smax)) {
-      if (blockIdx.x == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_BAD_DT);
+      *bad = true;
       dt = 0.0;
     } else {
       dt = a.cfl * a.dx / smax;
     }
   }
-  double t = 0.0;
+  *t = 0.0;
   if (a.tslot) {
-    t = a.tslot[a.slot];
+    *t = a.tslot[a.slot];
     if (a.t_end > 0.0) {
-      if (t >= a.t_end) dt = 0.0;
-      else if (dt > a.t_end - t) dt = a.t_end - t;
+      if (*t >= a.t_end) dt = 0.0;
+      else if (dt > a.t_end - *t) dt = a.t_end - *t;
     }
   }
+  return dt;
+}
+
+// step_dt_value, and block 0 advances the simulated time, records dt,
+// flags a bad wave speed and recycles the slot two steps ahead.
+__device__ double step_dt(const Step1DArgs &a) {
+  double t;
+  bool bad;
+  const double dt = step_dt_value(a, &t, &bad);
   if (blockIdx.x == 0) {
+    if (bad) atomicOr(a.status, (unsigned)ACAT_STATUS_BAD_DT);
     if (a.tslot) a.tslot[(a.slot + 1) % 3] = t + dt;
     if (a.dt_out) *a.dt_out = dt;
     a.smax[(a.slot + 2) % 3] = 0ull;
@@ -458,8 +492,9 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
       if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else if (ps == 2) {
       if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
-    } else if (l == 0) {
-      flcat2_flux<FLUX>(q0, TL::TW, lam, a.adv, a.gamma, a.limiter_form, F);
+    } else {
+      flcat2_flux<FLUX, TL::L>(q0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, a.adv, a.gamma,
+                               a.limiter_form, F);
     }
     if (l == 0) {
 #pragma unroll
@@ -533,8 +568,9 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
       if constexpr (P >= 3) if (l < 6) cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
     } else if (ps == 2) {
       if constexpr (P >= 2) if (l < 4) cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-    } else if (l == 0) {
-      flcat2_delta<FLUX>(h0, l0, TL::TW, lam, adv, gam, a.adv, a.limiter_form, G);
+    } else {
+      flcat2_delta<FLUX, TL::L>(h0, l0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, adv, gam, a.adv,
+                                a.limiter_form, G);
     }
     if (l == 0) {
 #pragma unroll
@@ -595,7 +631,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
 }
 
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
+__global__ void __launch_bounds__(NT, MinCtas<P, false>::value) k_step1d_f64(const Step1DArgs a) {
   __shared__ Smem64<P, Phys<FLUX>::S> sm;
   __shared__ double s_lam;
   if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
@@ -606,7 +642,7 @@ __global__ void __launch_bounds__(NT) k_step1d_f64(const Step1DArgs a) {
 }
 
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
+__global__ void __launch_bounds__(NT, MinCtas<P, true>::value) k_step1d_f32(const Step1DArgs a) {
   __shared__ Smem32<P, DPhys<FLUX>::S> sm;
   __shared__ double s_lam;
   if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
@@ -614,6 +650,146 @@ __global__ void __launch_bounds__(NT) k_step1d_f32(const Step1DArgs a) {
   tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0,
                     a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_lam, a.orders,
                     &a.smax[(a.slot + 1) % 3]);
+}
+
+// FP64 step in small CTAs (NWF warps): CTA b computes the NI interfaces
+// [b NI, b NI + NI) and updates the cells between them; the cell between
+// two CTAs is updated by whichever of the two finishes second. Each CTA
+// publishes its edge fluxes, fences, and counts itself in at the boundary
+// counters of its left and right neighbours (atomicAdd; no CTA ever waits):
+// the one that reads 1 owns the boundary cell, reads the other edge flux from
+// L2 and resets the counter for the next step. Small CTAs spread a step's
+// interfaces evenly over the SMs, and no interface is computed twice.
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1DArgs a) {
+  using TL = Tiling<P, NWF>;
+  constexpr int S = Phys<FLUX>::S;
+  constexpr int NTF = NWF * 32;
+  __shared__ double tile[S][TL::TW];
+  __shared__ double Fs[TL::NI][S];
+  __shared__ double red[NWF];
+  __shared__ double s_lam;
+  __shared__ int s_own[2];
+  const long N = a.N, i0 = (long)blockIdx.x * TL::NI;
+  const double *__restrict__ uin = static_cast<const double *>(a.u_in);
+  double *__restrict__ uout = static_cast<double *>(a.u_out);
+  if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
+  for (int q = threadIdx.x; q < S * TL::TW; q += NTF) {
+    const int c = q / TL::TW, k = q - c * TL::TW;
+    tile[c][k] = uin[c * N + bc_index(i0 - TL::GH + k, N, a.bc)];
+  }
+  __syncthreads();
+  const double lam = s_lam, gm1 = a.gamma - 1.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / TL::L, l = lane - grp * TL::L;
+  const bool valid = grp < TL::GPW;
+  const int il = warp * TL::GPW + grp;
+  const long m = i0 + il;
+  const bool active = valid && m <= N;
+  const int ic = il - 1 + TL::GH;
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  const int ps = select_order<P, S, false>(&tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l, grp,
+                                           active, valid, FC, a.eps, a.thr, a.fact_tau);
+  if (active) {
+    double F[S];
+    const int base = grp * TL::L;
+    const double *q0 = &tile[0][ic];
+    if (ps == 4) {
+      if constexpr (P >= 4) cat_flux<4, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+    } else if (ps == 3) {
+      if constexpr (P >= 3) if (l < 6) cat_flux<3, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+    } else if (ps == 2) {
+      if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
+    } else {
+      flcat2_flux<FLUX, TL::L>(q0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, a.adv, a.gamma,
+                               a.limiter_form, F);
+    }
+    if (l == 0) {
+#pragma unroll
+      for (int c = 0; c < S; c++) Fs[il][c] = F[c];
+      if (a.orders) a.orders[m] = (int8_t)ps;
+    }
+  }
+  __syncthreads();
+  const long nI = (N + 1 - i0) < TL::NI ? (N + 1 - i0) : TL::NI;  // interfaces of this CTA
+  const bool has_left = blockIdx.x > 0, has_right = i0 + TL::NI <= N;
+  if (threadIdx.x == 0) {
+    // publish the edge fluxes, then count in at both boundaries
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      if (has_left) a.flux_buf[c * (N + 1) + i0] = Fs[0][c];
+      if (has_right) a.flux_buf[c * (N + 1) + i0 + TL::NI - 1] = Fs[TL::NI - 1][c];
+    }
+    __threadfence();
+    int own0 = 0, own1 = 0;
+    if (has_left && atomicAdd(&a.cnt[blockIdx.x - 1], 1) == 1) {
+      own0 = 1;
+      a.cnt[blockIdx.x - 1] = 0;
+    }
+    if (has_right && atomicAdd(&a.cnt[blockIdx.x], 1) == 1) {
+      own1 = 1;
+      a.cnt[blockIdx.x] = 0;
+    }
+    s_own[0] = own0;
+    s_own[1] = own1;
+  }
+  __syncthreads();
+  double smax = 0.0;
+  bool bad = false;
+  // cells t = 0 .. nI - 2 lie between two interfaces of this CTA; task nI - 1
+  // is the left boundary cell i0 - 1, task nI the right one i0 + NI - 1
+  for (int t = threadIdx.x; t <= nI; t += NTF) {
+    long i;
+    int k;
+    double Fl[S], Fr[S];
+    if (t < nI - 1) {
+      i = i0 + t;
+      k = t + TL::GH;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Fl[c] = Fs[t][c];
+        Fr[c] = Fs[t + 1][c];
+      }
+    } else if (t == nI - 1) {
+      if (!s_own[0]) continue;
+      i = i0 - 1;
+      k = TL::GH - 1;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Fl[c] = __ldcg(&a.flux_buf[c * (N + 1) + i0 - 1]);
+        Fr[c] = Fs[0][c];
+      }
+    } else {
+      if (!s_own[1]) continue;
+      i = i0 + TL::NI - 1;
+      k = TL::NI - 1 + TL::GH;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Fl[c] = Fs[TL::NI - 1][c];
+        Fr[c] = __ldcg(&a.flux_buf[c * (N + 1) + i0 + TL::NI]);
+      }
+    }
+    double un[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      un[c] = tile[c][k] + lam * (Fl[c] - Fr[c]);
+      uout[c * N + i] = un[c];
+    }
+    bool ok;
+    smax = fmax(smax, Phys<FLUX>::speed(un, a.adv, a.gamma, ok));
+    bad |= !ok;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0) red[warp] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = red[0];
+#pragma unroll
+    for (int w = 1; w < NWF; w++) v = fmax(v, red[w]);
+    atomic_max_pos(&a.smax[(a.slot + 1) % 3], v);
+  }
 }
 
 // dt of instance b of a batch (1D CFL rule on the instance's own wave speed
@@ -649,7 +825,7 @@ __device__ double batch_dt(const Step1DArgs &a, const BatchArgs &bt, int b, bool
 // Persistent batched step: the CTAs stride over the (instance, first cell)
 // work list; every instance is advanced with its own dt.
 template <int P, int FLUX, bool F32>
-__global__ void __launch_bounds__(NT) k_batch1d(const Step1DArgs a, const BatchArgs bt) {
+__global__ void __launch_bounds__(NT, MinCtas<P, F32>::value) k_batch1d(const Step1DArgs a, const BatchArgs bt) {
   using SM = typename std::conditional<F32, Smem32<P, Phys<FLUX>::S>, Smem64<P, Phys<FLUX>::S>>::type;
   __shared__ SM sm;
   __shared__ double s_lam;
@@ -748,6 +924,13 @@ __global__ void __launch_bounds__(NT) k_smax1d(const Step1DArgs a) {
 template <int P, int FLUX, bool F32>
 int launch_p(const Step1DArgs &a, cudaStream_t st) {
   using TL = Tiling<P>;
+  if constexpr (!F32) {
+    if (a.flux_buf && a.cnt) {  // small-CTA step with boundary hand-off
+      const unsigned g = (unsigned)acat_fine_ctas_1d(P, a.N);
+      k_step1d_fine<P, FLUX><<<g, NWF * 32, 0, st>>>(a);
+      return (int)cudaGetLastError();
+    }
+  }
   const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
   if constexpr (F32) k_step1d_f32<P, FLUX><<<grid, NT, 0, st>>>(a);
   else k_step1d_f64<P, FLUX><<<grid, NT, 0, st>>>(a);
@@ -854,6 +1037,18 @@ int acat_cells_per_cta_1d(int P, int /*prec*/) {
   case 4: return Tiling<4>::T;
   }
   return 0;
+}
+
+int acat_fine_ctas_1d(int P, long N) {
+  int ni = 0;
+  switch (P) {
+  case 1: ni = Tiling<1, NWF>::NI; break;
+  case 2: ni = Tiling<2, NWF>::NI; break;
+  case 3: ni = Tiling<3, NWF>::NI; break;
+  case 4: ni = Tiling<4, NWF>::NI; break;
+  default: return -1;
+  }
+  return (int)((N + 1 + ni - 1) / ni);
 }
 
 int acat_launch_step1d(int P, int flux, int prec, const Step1DArgs &a, void *stream) {

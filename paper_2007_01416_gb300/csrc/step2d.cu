@@ -103,7 +103,7 @@ struct Phys2<ACAT_FLUX_EULER2D> {
     b.rho = u[0];
     b.mx = u[1];
     b.my = u[2];
-    const float ri = __frcp_rn(u[0]);
+    const float ri = recip(u[0]);
     b.v = u[1] * ri;
     b.w = u[2] * ri;
     const float p = gm1 * (u[3] - 0.5f * fmaf(u[1], b.v, u[2] * b.w));
@@ -116,7 +116,7 @@ struct Phys2<ACAT_FLUX_EULER2D> {
   //   d(mx v) = mx dv + bx (v + dv), d(my w) = my dw + by (w + dw),
   //   d(mx w) = mx dw + bx (w + dw), dp = (gamma - 1)(c - (d(mx v) + d(my w))/2)
   __device__ static __forceinline__ void dflux2(const Base &B, const float *d, float *df, float *dg) {
-    const float ri = __frcp_rn(B.rho + d[0]);
+    const float ri = recip(B.rho + d[0]);
     const float dv = fmaf(-B.v, d[0], d[1]) * ri, dw = fmaf(-B.w, d[0], d[2]) * ri;
     const float vn = B.v + dv, wn = B.w + dw;
     const float dmv = fmaf(B.mx, dv, d[1] * vn), dmw = fmaf(B.my, dw, d[2] * wn);

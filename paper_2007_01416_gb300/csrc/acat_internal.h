@@ -44,6 +44,7 @@ struct Step1DArgs {
   double fact_tau[ACAT_MAXP + 1];
   float epsf, rf;             // float eps and thr / (1 - thr) of the filtered decision
   float factf[ACAT_MAXP + 1];
+  float advf, gammaf, gm1f;   // adv, gamma, gamma - 1 rounded to float (FP32 path)
   unsigned long long *smax;   // 3 slots: max wave speed as ordered double bits
   double *tslot;              // 3 slots: simulated time (nullable)
   int8_t *orders;             // N+1 order codes (nullable)
@@ -92,6 +93,7 @@ struct Step2DArgs {
   double fact_tau[ACAT_MAXP + 1];
   float epsf, rf;
   float factf[ACAT_MAXP + 1];
+  float advf[2], gammaf, gm1f;  // adv, gamma, gamma - 1 rounded to float (FP32 path)
   unsigned long long *smax;   // 3 slots x 2 directions: [slot][dir]
   double *tslot;              // 3 slots (nullable)
   int8_t *ord_x;              // NY x (NX+1) (nullable)

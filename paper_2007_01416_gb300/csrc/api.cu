@@ -110,6 +110,9 @@ Step1DArgs base_args(acat_ctx *c) {
   }
   a.epsf = (float)p.eps;
   a.rf = (float)(a.thr / (1.0 - a.thr));
+  a.advf = (float)p.adv[0];
+  a.gammaf = (float)p.gamma;
+  a.gm1f = (float)(p.gamma - 1.0);
   a.smax = c->d_smax;
   a.status = c->d_status;
   a.flux_buf = c->d_flux;
@@ -141,6 +144,10 @@ Step2DArgs base_args2(acat_ctx *c) {
   }
   a.epsf = (float)p.eps;
   a.rf = (float)(a.thr / (1.0 - a.thr));
+  a.advf[0] = (float)p.adv[0];
+  a.advf[1] = (float)p.adv[1];
+  a.gammaf = (float)p.gamma;
+  a.gm1f = (float)(p.gamma - 1.0);
   a.smax = c->d_smax;
   a.status = c->d_status;
   return a;

@@ -317,6 +317,96 @@ __device__ __forceinline__ double psi1_group(Get q, int kind, int limiter_form, 
   return m;
 }
 
+// ---------------------------------------------------------------------------
+// psi^1 of systems on a compensated float state, in float-float arithmetic
+// (an unevaluated sum hi + lo of two floats: Knuth's TwoSum and Dekker's
+// Fast2Sum renormalisation, division by one correction of the quotient). The
+// jumps of hi + lo are formed to about 2^-44 relative, the ratio r is rounded
+// to float once, so psi^1 = superbee(r) carries only the rounding of a float
+// result (the FP32 path rounds the limiter to float in any case).
+// ---------------------------------------------------------------------------
+struct FF {
+  float h, l;
+};
+
+// (h1 + l1) - (h0 + l0)
+__device__ __forceinline__ FF ff_jump(float h0, float l0, float h1, float l1) {
+  const float s = __fsub_rn(h1, h0);
+  const float bb = __fsub_rn(s, h1);
+  const float e = __fadd_rn(__fsub_rn(h1, __fsub_rn(s, bb)), __fsub_rn(-h0, bb));
+  const float t = __fadd_rn(e, __fsub_rn(l1, l0));
+  const float hi = __fadd_rn(s, t);
+  return FF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+// the limiter ratio u / d rounded to float, with the conventions of lim_ratio
+// for d == 0
+__device__ __forceinline__ float ff_ratio(FF u, FF d) {
+  if (d.h == 0.0f) {
+    if (u.h == 0.0f) return 1.0f;
+    return u.h > 0.0f ? __int_as_float(0x7f800000) : __int_as_float((int)0xff800000u);
+  }
+  const float q = __fdiv_rn(u.h, d.h);
+  const float r = fmaf(-q, d.h, u.h);             // u.h - q d.h, exact
+  const float rem = fmaf(-q, d.l, __fadd_rn(r, u.l));
+  return __fadd_rn(q, __fdiv_rn(rem, d.h));
+}
+
+__device__ __forceinline__ float superbee_f(float r) {
+  const float r2 = 2.0f * r;
+  const float a = r2 < 1.0f ? r2 : 1.0f;
+  const float b = r < 2.0f ? r : 2.0f;
+  const float m = a > b ? a : b;
+  return m > 0.0f ? m : 0.0f;
+}
+
+// psi^1 of a system interface on the compensated state (min form, Eq. 3.7),
+// the (component, side) ratios spread over the L lanes of the group (gmask;
+// all lanes call it); every lane returns it.
+template <int S, int L>
+__device__ __forceinline__ float psi1_group_ff(const float *hi, const float *lo, int cs, int st, int l,
+                                               unsigned gmask) {
+  float best = 2.0f;
+  for (int k = l; k < 2 * S; k += L) {
+    const int c = k >> 1;
+    const float *h = hi + c * cs, *w = lo + c * cs;
+    const FF loc = ff_jump(h[0], w[0], h[st], w[st]);
+    const FF upw = (k & 1) ? ff_jump(h[st], w[st], h[2 * st], w[2 * st]) : ff_jump(h[-st], w[-st], h[0], w[0]);
+    const float v = superbee_f(ff_ratio(upw, loc));
+    if (v < best) best = v;
+  }
+  const int base = __ffs(gmask) - 1;
+  float m = best;
+#pragma unroll
+  for (int r = 0; r < (L < 2 * S ? L : 2 * S); r++) {
+    const float w = __shfl_sync(gmask, best, base + r);
+    if (w < m) m = w;
+  }
+  return m;
+}
+
+// psi^1 along a line of the compensated state by one lane, float-float
+// ratios: systems (and the min form) take the minimum over (component, side);
+// linear transport with the Roe-speed form takes the upwind side of the
+// constant speed adv (r- for adv > 0, else r+).
+template <int S>
+__device__ __forceinline__ float psi1_line_ff(const float *hi, const float *lo, int cs, int st, bool roe_linear,
+                                              float adv) {
+  float best = 2.0f;
+#pragma unroll
+  for (int k = 0; k < 2 * S; k++) {
+    const int c = k >> 1;
+    if (roe_linear && ((k & 1) == (adv > 0.0f ? 1 : 0))) continue;
+    const float *h = hi + c * cs, *w = lo + c * cs;
+    const FF loc = ff_jump(h[0], w[0], h[st], w[st]);
+    const FF upw = (k & 1) ? ff_jump(h[st], w[st], h[2 * st], w[2 * st]) : ff_jump(h[-st], w[-st], h[0], w[0]);
+    const float v = superbee_f(ff_ratio(upw, loc));
+    if (roe_linear) return v;
+    if (v < best) best = v;
+  }
+  return best;
+}
+
 template <int S>
 __device__ __forceinline__ double psi1_pair(const float *hi, const float *lo, int cs, int st, int kind,
                                             int limiter_form, double adv) {

@@ -113,6 +113,9 @@ extern "C" int acat_run_noalloc(const acat_params *p, void *u_dev, int nsteps, d
   }
   a.epsf = (float)p->eps;
   a.rf = (float)(a.thr / (1.0 - a.thr));
+  a.advf = (float)p->adv[0];
+  a.gammaf = (float)p->gamma;
+  a.gm1f = (float)(p->gamma - 1.0);
   a.smax = smax;
   a.tslot = tslot;
   a.status = status;

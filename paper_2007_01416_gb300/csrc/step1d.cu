@@ -362,9 +362,13 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
   DP::dflux(b0, d1, T1);
   const float s0 = DP::speed(u0, adv, gamma), s1 = DP::speed(u1, adv, gamma);
   const float alpha = s1 > s0 ? s1 : s0;
-  const float w = (float)psi1_group<S, L>(
-      [=](int c, int k) { return (double)hi[c * cs + k] + (double)lo[c * cs + k]; },
-      FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, advd, l, gmask);
+  // scalar laws with the Roe-speed side: the side decision in FP64 on hi + lo;
+  // systems (and the min form): float-float ratios
+  const float w =
+      (S == 1 && limiter_form == 0)
+          ? (float)psi1_g<S>([=](int c, int k) { return (double)hi[c * cs + k] + (double)lo[c * cs + k]; },
+                             FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, advd)
+          : psi1_group_ff<S, L>(hi, lo, cs, 1, l, gmask);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const float G1 = 0.25f * (T0[c] + T1[c] + D1[c]);
@@ -436,8 +440,21 @@ template <int P, int S>
 struct Smem32 {
   float thi[S][Tiling<P>::TW], tlo[S][Tiling<P>::TW];
   float Gs[Tiling<P>::NI][S];
-  double red[NT / 32];
+  float redf[NT / 32];
 };
+
+// Block-wide maximum of a non-negative float `v` (thread 0 returns it).
+__device__ __forceinline__ float block_max_f(float v, float *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NT / 32; w++) v = fmaxf(v, red[w]);
+  }
+  return v;
+}
 
 // Block-wide maximum of `v` (thread 0 returns it).
 __device__ __forceinline__ double block_max(double v, double *red) {
@@ -530,7 +547,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
 template <int P, int FLUX>
 __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FLUX>::S> &sm,
                                          const float *__restrict__ uin, float *__restrict__ uout,
-                                         long off, long M, long N, long i0, double lamd,
+                                         long off, long M, long N, long i0, float lam,
                                          int8_t *orders, unsigned long long *smax_out) {
   using TL = Tiling<P>;
   using DP = DPhys<FLUX>;
@@ -542,8 +559,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     sm.tlo[c][k] = uin[(S + c) * M + g];
   }
   __syncthreads();
-  const float lam = (float)lamd, adv = (float)a.adv, gam = (float)a.gamma;
-  const float gm1 = (float)(a.gamma - 1.0);
+  const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / TL::L, l = lane - grp * TL::L;
@@ -580,7 +596,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   }
   __syncthreads();
 
-  double smax = 0.0;
+  float smax = 0.0f;
   bool bad = false;
   for (int t = threadIdx.x; t < TL::T; t += NT) {
     const long i = i0 + t;
@@ -622,11 +638,11 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
       Phys<FLUX>::speed(ud, a.adv, a.gamma, ok);
       bad |= !ok;
     }
-    smax = fmax(smax, (double)sf);
+    smax = fmaxf(smax, sf);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
-  const double v = block_max(smax, sm.red);
-  if (threadIdx.x == 0) atomic_max_pos(smax_out, v);
+  const float v = block_max_f(smax, sm.redf);
+  if (threadIdx.x == 0) atomic_max_pos(smax_out, (double)v);
   __syncthreads();
 }
 
@@ -644,8 +660,8 @@ __global__ void __launch_bounds__(NT, MinCtas<P, false>::value) k_step1d_f64(con
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NT, MinCtas<P, true>::value) k_step1d_f32(const Step1DArgs a) {
   __shared__ Smem32<P, DPhys<FLUX>::S> sm;
-  __shared__ double s_lam;
-  if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
+  __shared__ float s_lam;
+  if (threadIdx.x == 0) s_lam = (float)(step_dt(a) / a.dx);
   __syncthreads();
   tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0,
                     a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_lam, a.orders,
@@ -829,6 +845,7 @@ __global__ void __launch_bounds__(NT, MinCtas<P, F32>::value) k_batch1d(const St
   using SM = typename std::conditional<F32, Smem32<P, Phys<FLUX>::S>, Smem64<P, Phys<FLUX>::S>>::type;
   __shared__ SM sm;
   __shared__ double s_lam;
+  __shared__ float s_lamf;
   for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
     const int b = bt.tiles[w].b;
     const long i0 = (long)bt.tiles[w].tile * Tiling<P>::T;
@@ -836,13 +853,14 @@ __global__ void __launch_bounds__(NT, MinCtas<P, F32>::value) k_batch1d(const St
     if (threadIdx.x == 0) {
       const double dx = bt.xlen / (double)N;
       s_lam = batch_dt(a, bt, b, i0 == 0, dx) / dx;
+      s_lamf = (float)s_lam;
     }
     __syncthreads();
     int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
     unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
     if constexpr (F32)
       tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), off,
-                        bt.M, N, i0, s_lam, ord, so);
+                        bt.M, N, i0, s_lamf, ord, so);
     else
       tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
                         off, bt.M, N, i0, s_lam, ord, so);

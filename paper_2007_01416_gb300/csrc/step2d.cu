@@ -403,11 +403,11 @@ __device__ __forceinline__ void flcat2_2d_f64(const double *q, int cs, int rs, b
 template <int FLUX>
 __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, int cs, int rs,
                                               bool wantF, bool wantG, float lx,
-                                              float ly, float ax, float ay, float gamma, double axd,
-                                              double ayd, int limiter_form, float *GF, float *GG) {
+                                              float ly, float ax, float ay, float gamma, float gm1,
+                                              int limiter_form, float *GF, float *GG) {
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
-  const float gm1 = gamma - 1.0f;
+  const bool roe_linear = FLUX == ACAT_FLUX_LINEAR && limiter_form == 0;
   float ua[S], d10[S], d01[S], d11[S], u10[S], u01[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
@@ -429,7 +429,6 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
   for (int c = 0; c < S; c++) U00[c] = -lx * Df10[c] - ly * Dg01[c];
   float e00f[S], e00g[S];
   PH::dflux2(B, U00, e00f, e00g);
-  const int kind = 0;
   if (wantF) {
     float x1[S], ef[S], eg[S];
 #pragma unroll
@@ -437,7 +436,7 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
     PH::dflux2(B, x1, ef, eg);  // f(u10 + U10) - f(u_a)
     const float s0 = PH::fspeed(ua, ax, ay, gamma, 0), s1 = PH::fspeed(u10, ax, ay, gamma, 0);
     const float alpha = s1 > s0 ? s1 : s0;
-    const float w = (float)psi1_pair<S>(hi, lo, cs, 1, kind, limiter_form, axd);
+    const float w = psi1_line_ff<S>(hi, lo, cs, 1, roe_linear, ax);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       // F1 - f(a) = Df10/2 + (e00 + (ef - Df10))/4 ; Flo - f(a) = Df10/2 - alpha d10/2
@@ -453,7 +452,7 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
     PH::dflux2(B, x1, ef, eg);  // g(u01 + U01) - g(u_a)
     const float s0 = PH::fspeed(ua, ax, ay, gamma, 1), s1 = PH::fspeed(u01, ax, ay, gamma, 1);
     const float alpha = s1 > s0 ? s1 : s0;
-    const float w = (float)psi1_pair<S>(hi, lo, cs, rs, kind, limiter_form, ayd);
+    const float w = psi1_line_ff<S>(hi, lo, cs, rs, roe_linear, ay);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const float G1 = 0.5f * Dg01[c] + 0.25f * (e00g[c] + eg[c] - Dg01[c]);
@@ -502,7 +501,7 @@ __device__ double step_dt2(const Step2DArgs &a) {
 __device__ __forceinline__ long bc2(long g, long n, int bc) { return bc_index(g, n, bc); }
 
 template <int P, int FLUX, bool F32>
-__global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
+__global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 1)) k_step2d(const Step2DArgs a) {
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   using R = typename std::conditional<F32, float, double>::type;
@@ -517,10 +516,13 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
   const long x0 = (long)blockIdx.x * TXY, y0 = (long)blockIdx.y * TXY;
 
   __shared__ double s_lx, s_ly;
+  __shared__ float s_lxf, s_lyf;
   if (threadIdx.x == 0) {
     s_dt = step_dt2(a);
     s_lx = s_dt / a.dx;
     s_ly = s_dt / a.dy;
+    s_lxf = (float)s_lx;
+    s_lyf = (float)s_ly;
   }
   constexpr int CELLS = TW2 * TW2;
   for (int q = threadIdx.x; q < S * CELLS; q += NT) {
@@ -583,8 +585,8 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     if (P >= 2 && (blkF || blkG)) {
       if constexpr (P >= 2) {
         if constexpr (F32) {
-          cat2d_f32<2, FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, l, base, (float)lxd,
-                             (float)lyd, (float)a.adv[0], (float)a.adv[1], (float)(a.gamma - 1.0), F, G);
+          cat2d_f32<2, FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, l, base, s_lxf, s_lyf, a.advf[0],
+                             a.advf[1], a.gm1f, F, G);
         } else {
           cat2d_f64<2, FLUX>(q64, CS, RS, l, base, lxd, lyd, a.adv[0], a.adv[1], a.gamma - 1.0, F, G);
         }
@@ -594,9 +596,8 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     if (l == 0 && (flF || flG)) {
       R F1[S], G1[S];
       if constexpr (F32) {
-        flcat2_2d_f32<FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, flF, flG, (float)lxd,
-                            (float)lyd, (float)a.adv[0], (float)a.adv[1], (float)a.gamma, a.adv[0],
-                            a.adv[1], a.limiter_form, F1, G1);
+        flcat2_2d_f32<FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, flF, flG, s_lxf, s_lyf, a.advf[0],
+                            a.advf[1], a.gammaf, a.gm1f, a.limiter_form, F1, G1);
       } else {
         flcat2_2d_f64<FLUX>(q64, CS, RS, flF, flG, lxd, lyd, a.adv[0], a.adv[1], a.gamma,
                             a.limiter_form, F1, G1);
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
   __syncthreads();
 
   // --- update and wave-speed epilogue ------------------------------------------
-  double mx = 0.0, my = 0.0;
+  R mx = 0, my = 0;
   bool bad = false;
   for (int t = threadIdx.x; t < TXY * TXY; t += NT) {
     const int cy = t / TXY, cx = t - cy * TXY;
@@ -639,12 +640,11 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
         dlx[c] = (thi[c][ty][tx - 1] - thi[c][ty][tx]) + (tlo[c][ty][tx - 1] - tlo[c][ty][tx]);
         dly[c] = (thi[c][ty - 1][tx] - thi[c][ty][tx]) + (tlo[c][ty - 1][tx] - tlo[c][ty][tx]);
       }
-      const typename PH::Base B =
-          PH::base(uc, (float)a.adv[0], (float)a.adv[1], (float)(a.gamma - 1.0));
+      const typename PH::Base B = PH::base(uc, a.advf[0], a.advf[1], a.gm1f);
       PH::dflux2(B, dlx, Bx, junk);  // f(u_{x-1,y}) - f(u)
       PH::dflux2(B, dly, junk, By);  // g(u_{x,y-1}) - g(u)
       float *uo = static_cast<float *>(a.u_out);
-      const float lx = (float)lxd, ly = (float)lyd;
+      const float lx = s_lxf, ly = s_lyf;
 #pragma unroll
       for (int c = 0; c < S; c++) {
         const float dx_ = __fmul_rn(lx, __fadd_rn(Bx[c], __fsub_rn(Fx[cy][cx][c], Fx[cy][cx + 1][c])));
@@ -664,9 +664,9 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
         lf[c] = ln;
       }
       // wave speeds in float; a state that looks non-physical is re-checked in FP64
-      const float g = (float)a.gamma;
-      const float sxf = PH::fspeed(hf, (float)a.adv[0], (float)a.adv[1], g, 0);
-      const float syf = PH::fspeed(hf, (float)a.adv[0], (float)a.adv[1], g, 1);
+      const float g = a.gammaf;
+      const float sxf = PH::fspeed(hf, a.advf[0], a.advf[1], g, 0);
+      const float syf = PH::fspeed(hf, a.advf[0], a.advf[1], g, 1);
       if (!PH::fphysical(hf, g)) {
 #pragma unroll
         for (int c = 0; c < S; c++) un[c] = (double)hf[c] + (double)lf[c];
@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
         PH::speed2(un, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
         bad |= !ok;
       }
-      mx = fmax(mx, (double)sxf);
-      my = fmax(my, (double)syf);
+      mx = fmaxf(mx, sxf);
+      my = fmaxf(my, syf);
       continue;
     } else {
       double *uo = static_cast<double *>(a.u_out);
@@ -691,18 +691,21 @@ __global__ void __launch_bounds__(NT) k_step2d(const Step2DArgs a) {
     bool ok;
     PH::speed2(un, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
     bad |= !ok;
-    mx = fmax(mx, sx);
-    my = fmax(my, sy);
+    if constexpr (!F32) {
+      mx = fmax(mx, sx);
+      my = fmax(my, sy);
+    }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+    const R ox = __shfl_xor_sync(0xffffffffu, mx, o), oy = __shfl_xor_sync(0xffffffffu, my, o);
+    mx = ox > mx ? ox : mx;
+    my = oy > my ? oy : my;
   }
   if (lane == 0) {
-    s_red[0][warp] = mx;
-    s_red[1][warp] = my;
+    s_red[0][warp] = (double)mx;
+    s_red[1][warp] = (double)my;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -152,7 +152,7 @@ int acat_run(acat_ctx *ctx, void *u_dev, int nsteps, double t_end, void *stream,
 int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int nsteps, double t_end,
                   void *stream, double *t_host);
 
-/* Adjoint (transposed Jacobian) of one 1D FP64 step:
+/* Adjoint (transposed Jacobian) of one 1D step:
  *   ubar_n = (d u^{n+1} / d u^n)^T ubar_np1,
  * with u^{n+1} = step(u^n) taken with the time step dt (treated as a
  * constant: the dt the forward step used) and every discrete choice frozen as
@@ -160,14 +160,17 @@ int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int ns
  * for FL-CAT2 interfaces (Eq. 3.4), the superbee piece, the upwind side or the
  * (component, side) of the limiter minimum, and the Rusanov maximum. All else
  * -- the CAT2p recursion of Sec. 2.2, the limiter value inside its piece, the
- * Rusanov speed -- is differentiated. u_n, ubar_np1, ubar_n: device FP64
- * states [s][nx]; ubar_n must not alias ubar_np1. Uses a context-owned
- * scratch array ((nx+1) x max(2P,4) x s doubles, allocated on first use).
- * Errors: INVALID_ARG, UNSUPPORTED (2D, batched or FP32 contexts), NOMEM, CUDA. */
+ * Rusanov speed -- is differentiated. u_n, ubar_np1, ubar_n: device states
+ * in the context's layout: FP64 [s][nx]; FP32 compensated pairs
+ * [hi(s x nx); lo(s x nx)], the cotangents as compensated values too (the
+ * FP32 reverse sweep runs in float, FL-CAT2 interfaces in FP64 on hi + lo).
+ * ubar_n must not alias ubar_np1. Uses a context-owned scratch array
+ * ((nx+1) x max(2P,4) x s doubles, allocated on first use).
+ * Errors: INVALID_ARG, UNSUPPORTED (2D or batched contexts), NOMEM, CUDA. */
 int acat_adjoint_step(acat_ctx *ctx, const void *u_n_dev, double dt, const void *ubar_np1_dev,
                       void *ubar_n_dev, void *stream);
 
-/* Forward run that records what the reverse run needs (1D FP64 contexts).
+/* Forward run that records what the reverse run needs (1D contexts).
  * Takes nsteps CFL steps (as acat_run, without t_end) from u0_dev, which is
  * not modified, and writes u^nsteps to u_out_dev.
  *   every >= 1: checkpoint interval; the state before step n, for every n
@@ -186,8 +189,9 @@ int acat_run_record(acat_ctx *ctx, const void *u0_dev, void *u_out_dev, int nste
  * (bit-identical to the forward run) into a context-owned buffer of every-1
  * states, allocated on first use and grown on demand; then the adjoint steps
  * run in reverse. ckpt_dev, dts_dev, nsteps, every: as given to
- * acat_run_record. ubar_n_dev, ubar_0_dev: device FP64 states [s][nx]; they
- * may be the same buffer. Errors: INVALID_ARG, UNSUPPORTED, NOMEM, CUDA. */
+ * acat_run_record. ubar_n_dev, ubar_0_dev: device cotangents in the state
+ * layout of the context (as acat_adjoint_step); they may be the same buffer.
+ * Errors: INVALID_ARG, UNSUPPORTED, NOMEM, CUDA. */
 int acat_adjoint_run(acat_ctx *ctx, const void *ckpt_dev, const double *dts_dev, int nsteps, int every,
                      const void *ubar_n_dev, void *ubar_0_dev, void *stream);
 

@@ -8,6 +8,11 @@ states are recomputed from the checkpoint with the recorded dt (bit-identical
 to the forward) and the hand-written adjoint step is applied in reverse. The
 discrete choices of every step and its dt are those of the forward pass.
 Only argument marshalling happens here; no step returns to the host.
+
+FP32 contexts take and return compensated pair states [2][s][nx] (hi, lo).
+Their state value is hi + lo, so the cotangent of the value is read from the
+hi half of the incoming gradient, and the gradient returned for u0 carries
+the cotangent of the value in both halves.
 """
 from __future__ import annotations
 
@@ -40,14 +45,22 @@ class ACATRun(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gN):
         ckpt, dts = ctx.saved_tensors
-        g = gN.detach().contiguous().clone()
+        f32 = gN.dtype == torch.float32
+        if f32:
+            g = torch.zeros_like(gN)
+            g[0] = gN[0]  # compensated cotangent (value, 0)
+        else:
+            g = gN.detach().contiguous().clone()
         if ctx.nsteps > 0:
             ctx.actx.acat_adjoint_run(ckpt, dts, ctx.nsteps, ctx.every, g, g)
+        if f32:
+            v = g[0] + g[1]
+            g = torch.stack([v, v])
         return g, None, None, None
 
 
 def run(u0: torch.Tensor, actx, nsteps: int, every: int = 0) -> torch.Tensor:
-    """u^n as a differentiable function of u0 (1D FP64 context)."""
+    """u^n as a differentiable function of u0 (1D context, FP64 or FP32)."""
     return ACATRun.apply(u0, actx, nsteps, every)
 
 

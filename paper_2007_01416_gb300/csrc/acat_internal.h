@@ -107,9 +107,10 @@ int acat_launch_smax2d(int flux, int prec, const Step2DArgs &a, void *stream);
 int acat_upload_tables_1d(const AcatTables *T);
 int acat_upload_tables_adj(const AcatTables *T);
 int acat_adjoint_slots(int P);
-// Adjoint of one 1D FP64 step (a.u_in = u^n, dt from a.dt_in or a.dt_fixed): ubar0 from ubar1.
-int acat_launch_adjoint1d(int P, int flux, const Step1DArgs &a, const double *ubar1, double *contrib,
-                          double *ubar0, void *stream);
+// Adjoint of one 1D step (a.u_in = u^n, dt from a.dt_in or a.dt_fixed): ubar0 from ubar1.
+// FP64: double states and cotangents, double contrib; FP32: compensated float pairs, float contrib.
+int acat_launch_adjoint1d(int P, int flux, int prec, const Step1DArgs &a, const void *ubar1, void *contrib,
+                          void *ubar0, void *stream);
 int acat_upload_tables_2d(const AcatTables *T);
 
 // Initial wave-speed reduction into smax[slot] (and t = 0 into tslot[slot]).

@@ -1,5 +1,5 @@
 // adjoint1d.cu -- hand-written adjoint (transposed Jacobian) of one 1D ACAT
-// step, FP64.
+// step, FP64 and FP32 (compensated state and cotangent).
 //
 // The step u^{n+1} = u^n + lambda (F_{i-1/2} - F_{i+1/2}) is differentiated
 // with its discrete choices frozen at u^n: the selected order of every
@@ -33,7 +33,8 @@ struct Jac;
 
 template <>
 struct Jac<ACAT_FLUX_LINEAR> {
-  __device__ static void jt(const double *, const double *y, double *out, double a, double) {
+  template <typename R>
+  __device__ static void jt(const R *, const R *y, R *out, R a, R) {
     out[0] += a * y[0];
   }
   __device__ static void grad_speed(const double *, double, double *g) { g[0] = 0.0; }
@@ -41,7 +42,8 @@ struct Jac<ACAT_FLUX_LINEAR> {
 
 template <>
 struct Jac<ACAT_FLUX_BURGERS> {
-  __device__ static void jt(const double *u, const double *y, double *out, double, double) {
+  template <typename R>
+  __device__ static void jt(const R *u, const R *y, R *out, R, R) {
     out[0] += u[0] * y[0];
   }
   __device__ static void grad_speed(const double *u, double, double *g) { g[0] = u[0] < 0.0 ? -1.0 : 1.0; }
@@ -52,14 +54,15 @@ struct Jac<ACAT_FLUX_EULER1D> {
   // f = (m, m v + p, v (E + p)), v = m / rho, p = (gamma - 1)(E - m v / 2):
   // df1 = ((gm1 - 2) v^2 / 2, (2 - gm1) v, gm1),
   // df2 = (v (gm1 v^2 / 2 - H), H - gm1 v^2, gamma v), H = (E + p) / rho.
-  __device__ static void jt(const double *u, const double *y, double *out, double, double gm1) {
-    const double ri = 1.0 / u[0];
-    const double v = u[1] * ri;
-    const double p = gm1 * (u[2] - 0.5 * u[1] * v);
-    const double H = (u[2] + p) * ri;
-    out[0] += y[1] * (0.5 * (gm1 - 2.0) * v * v) + y[2] * (v * (0.5 * gm1 * v * v - H));
-    out[1] += y[0] + y[1] * ((2.0 - gm1) * v) + y[2] * (H - gm1 * v * v);
-    out[2] += y[1] * gm1 + y[2] * ((1.0 + gm1) * v);
+  template <typename R>
+  __device__ static void jt(const R *u, const R *y, R *out, R, R gm1) {
+    const R ri = R(1) / u[0];
+    const R v = u[1] * ri;
+    const R p = gm1 * (u[2] - R(0.5) * u[1] * v);
+    const R H = (u[2] + p) * ri;
+    out[0] += y[1] * (R(0.5) * (gm1 - R(2)) * v * v) + y[2] * (v * (R(0.5) * gm1 * v * v - H));
+    out[1] += y[0] + y[1] * ((R(2) - gm1) * v) + y[2] * (H - gm1 * v * v);
+    out[2] += y[1] * gm1 + y[2] * ((R(1) + gm1) * v);
   }
   // s = |v| + c, c = sqrt(gamma p / rho)
   __device__ static void grad_speed(const double *u, double gamma, double *g) {
@@ -79,28 +82,27 @@ struct Jac<ACAT_FLUX_EULER1D> {
 // Reverse sweep of the CAT2p flux of one interface (lane l <-> node
 // j = l - p + 1). Fbar: cotangent of the interface flux. ubar: cotangent of
 // this lane's node.
-template <int p, int FLUX>
-__device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int base, double lam,
-                                             double adv, double gm1, const double *Fbar,
-                                             double *ubar) {
-  using TB = Tab<double>;
+template <int p, int FLUX, typename R>
+__device__ __forceinline__ void cat_flux_adj(const R *q, int cs, int l, int base, R lam, R adv, R gm1,
+                                             const R *Fbar, R *ubar) {
+  using TB = Tab<R>;
   constexpr int S = Phys<FLUX>::S;
   constexpr int n = 2 * p;
   const unsigned mask = ((1u << n) - 1u) << base;
   const int j = l - p + 1;
-  double g1r[n], g1c[n];
+  R g1r[n], g1c[n];
 #pragma unroll
   for (int r = 0; r < n; r++) {
     g1r[r] = TB::g1(p, l, r);  // row: d/dx at node j
     g1c[r] = TB::g1(p, r, l);  // column: weight of node j at node r
   }
-  double u[S], f0[S], Uk[n + 1][S];
+  R u[S], f0[S], Uk[n + 1][S];
 #pragma unroll
   for (int c = 0; c < S; c++) u[c] = q[c * cs + j];
   Phys<FLUX>::flux(u, f0, adv, gm1);
   // forward recomputation, keeping U^(k)
   {
-    double arg[n][S], Fprev[S];
+    R arg[n][S], Fprev[S];
 #pragma unroll
     for (int rr = 0; rr < n; rr++)
 #pragma unroll
@@ -109,13 +111,13 @@ __device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int
     for (int c = 0; c < S; c++) Fprev[c] = f0[c];
 #pragma unroll
     for (int k = 2; k <= n; k++) {
-      double U[S], acc[S];
+      R U[S], acc[S];
 #pragma unroll
-      for (int c = 0; c < S; c++) U[c] = 0.0;
+      for (int c = 0; c < S; c++) U[c] = R(0);
 #pragma unroll
       for (int r = 0; r < n; r++)
 #pragma unroll
-        for (int c = 0; c < S; c++) U[c] = fma(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
+        for (int c = 0; c < S; c++) U[c] = fmar(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
 #pragma unroll
       for (int c = 0; c < S; c++) {
         U[c] *= -lam;
@@ -126,12 +128,12 @@ __device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int
 #pragma unroll
         for (int rr = 0; rr < n; rr++) {
           if (rr == p - 1) continue;
-          double fr[S];
+          R fr[S];
 #pragma unroll
-          for (int c = 0; c < S; c++) arg[rr][c] = fma(TB::taylor(p, rr, k - 1), U[c], arg[rr][c]);
+          for (int c = 0; c < S; c++) arg[rr][c] = fmar(TB::taylor(p, rr, k - 1), U[c], arg[rr][c]);
           Phys<FLUX>::flux(arg[rr], fr, adv, gm1);
 #pragma unroll
-          for (int c = 0; c < S; c++) acc[c] = fma(TB::gk(p, k - 1, rr), fr[c], acc[c]);
+          for (int c = 0; c < S; c++) acc[c] = fmar(TB::gk(p, k - 1, rr), fr[c], acc[c]);
         }
 #pragma unroll
         for (int c = 0; c < S; c++) Fprev[c] = acc[c];
@@ -139,20 +141,20 @@ __device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int
     }
   }
   // reverse sweep
-  double Fsb[S], f0b[S], argb[n][S], Ub[S];
+  R Fsb[S], f0b[S], argb[n][S], Ub[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     Fsb[c] = TB::gh(p, l) * Fbar[c];
     f0b[c] = Fsb[c];
-    Ub[c] = 0.0;
+    Ub[c] = R(0);
   }
 #pragma unroll
   for (int rr = 0; rr < n; rr++)
 #pragma unroll
-    for (int c = 0; c < S; c++) argb[rr][c] = 0.0;
+    for (int c = 0; c < S; c++) argb[rr][c] = R(0);
 #pragma unroll
   for (int k = n; k >= 2; k--) {
-    double accb[S];
+    R accb[S];
 #pragma unroll
     for (int c = 0; c < S; c++) accb[c] = TB::invfact(k) * Fsb[c];
     if (k < n) {
@@ -160,14 +162,14 @@ __device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int
 #pragma unroll
       for (int i = 0; i < n; i++)
 #pragma unroll
-        for (int c = 0; c < S; c++) accb[c] = fma(-lam * g1c[i], __shfl_sync(mask, Ub[c], base + i), accb[c]);
+        for (int c = 0; c < S; c++) accb[c] = fmar(-lam * g1c[i], __shfl_sync(mask, Ub[c], base + i), accb[c]);
     }
 #pragma unroll
-    for (int c = 0; c < S; c++) f0b[c] = fma(TB::gk(p, k - 1, p - 1), accb[c], f0b[c]);
+    for (int c = 0; c < S; c++) f0b[c] = fmar(TB::gk(p, k - 1, p - 1), accb[c], f0b[c]);
 #pragma unroll
     for (int rr = 0; rr < n; rr++) {
       if (rr == p - 1) continue;
-      double a[S], y[S];
+      R a[S], y[S];
 #pragma unroll
       for (int c = 0; c < S; c++) {
         a[c] = u[c];
@@ -176,15 +178,15 @@ __device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int
 #pragma unroll
       for (int kk = 2; kk <= k; kk++)
 #pragma unroll
-        for (int c = 0; c < S; c++) a[c] = fma(TB::taylor(p, rr, kk - 1), Uk[kk][c], a[c]);
+        for (int c = 0; c < S; c++) a[c] = fmar(TB::taylor(p, rr, kk - 1), Uk[kk][c], a[c]);
       Jac<FLUX>::jt(a, y, argb[rr], adv, gm1);
     }
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      double s = 0.0;
+      R s = R(0);
 #pragma unroll
       for (int rr = 0; rr < n; rr++)
-        if (rr != p - 1) s = fma(TB::taylor(p, rr, k - 1), argb[rr][c], s);
+        if (rr != p - 1) s = fmar(TB::taylor(p, rr, k - 1), argb[rr][c], s);
       Ub[c] = s;  // Ubar of U^(k)
     }
   }
@@ -192,10 +194,10 @@ __device__ __forceinline__ void cat_flux_adj(const double *q, int cs, int l, int
 #pragma unroll
   for (int i = 0; i < n; i++)
 #pragma unroll
-    for (int c = 0; c < S; c++) f0b[c] = fma(-lam * g1c[i], __shfl_sync(mask, Ub[c], base + i), f0b[c]);
+    for (int c = 0; c < S; c++) f0b[c] = fmar(-lam * g1c[i], __shfl_sync(mask, Ub[c], base + i), f0b[c]);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    double s = 0.0;
+    R s = R(0);
 #pragma unroll
     for (int rr = 0; rr < n; rr++)
       if (rr != p - 1) s += argb[rr][c];
@@ -497,6 +499,184 @@ __global__ void __launch_bounds__(NT) k_adj_gather(const Step1DArgs a, const dou
   }
 }
 
+// FP32 adjoint step on the compensated state [hi(S x N); lo(S x N)] with a
+// compensated cotangent of the same layout. The order decisions are the FP32
+// forward's (taken on hi + lo); Fbar_m = lambda (ubar_m - ubar_{m-1}) is
+// formed from the cotangent pairs in float-float; the CAT2p reverse sweep runs
+// in float on hi (the Jacobians are evaluated, not differenced, so float
+// arguments carry only relative rounding); FL-CAT2 interfaces are
+// differentiated in FP64 on hi + lo. Per-interface node cotangents go to a
+// float scratch array.
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NWF * 32) k_adj1d_f32(const Step1DArgs a, const float *__restrict__ ubar1,
+                                                        float *__restrict__ contrib) {
+  using TL = Tiling<P, NWF>;
+  constexpr int S = Phys<FLUX>::S;
+  constexpr int NS = 2 * P > 4 ? 2 * P : 4;
+  __shared__ float thi[S][TL::TW], tlo[S][TL::TW];
+  const float *__restrict__ uin = static_cast<const float *>(a.u_in);
+  const long N = a.N;
+  const long i0 = (long)blockIdx.x * TL::NI;
+  for (int q = threadIdx.x; q < S * TL::TW; q += NWF * 32) {
+    const int c = q / TL::TW, k = q - c * TL::TW;
+    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
+    thi[c][k] = uin[c * N + g];
+    tlo[c][k] = uin[(S + c) * N + g];
+  }
+  __syncthreads();
+  const double lamd = (a.dt_in ? *a.dt_in : a.dt_fixed) / a.dx;
+  const float lam = (float)lamd;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / TL::L, l = lane - grp * TL::L;
+  const bool valid = grp < TL::GPW;
+  const int il = warp * TL::GPW + grp;
+  const long m = i0 + il;
+  const bool active = valid && m <= N;
+  const int ic = il - 1 + TL::GH;
+  const int icv = valid ? ic : 0;
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  const int ps = select_order<P, S, true>(nullptr, &thi[0][icv], &tlo[0][icv], TL::TW, l, grp, active, valid,
+                                          FC, a.eps, a.thr, a.fact_tau);
+  if (!active) return;
+  // Fbar_m = lambda (ubar_m - ubar_{m-1}), cells outside 0..N-1 contribute nothing
+  float Fb[S];
+  double Fbd[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const float rh = m <= N - 1 ? ubar1[c * N + m] : 0.0f, rl = m <= N - 1 ? ubar1[(S + c) * N + m] : 0.0f;
+    const float lh = m >= 1 ? ubar1[c * N + m - 1] : 0.0f, ll = m >= 1 ? ubar1[(S + c) * N + m - 1] : 0.0f;
+    const FF d = ff_jump(lh, ll, rh, rl);
+    Fbd[c] = lamd * ((double)d.h + (double)d.l);
+    Fb[c] = (float)Fbd[c];
+  }
+  const int base = grp * TL::L;
+  float *out = contrib + m * NS * S;
+  if (ps >= 2) {
+    float ub[S];
+    bool mine = false;
+    int pp = 2;
+    const float *q0 = &thi[0][ic];
+    if (ps == 4) {
+      if constexpr (P >= 4) {
+        cat_flux_adj<4, FLUX, float>(q0, TL::TW, l, base, lam, a.advf, a.gm1f, Fb, ub);
+        mine = true;
+        pp = 4;
+      }
+    } else if (ps == 3) {
+      if constexpr (P >= 3) {
+        if (l < 6) {
+          cat_flux_adj<3, FLUX, float>(q0, TL::TW, l, base, lam, a.advf, a.gm1f, Fb, ub);
+          mine = true;
+        }
+        pp = 3;
+      }
+    } else {
+      if constexpr (P >= 2) {
+        if (l < 4) {
+          cat_flux_adj<2, FLUX, float>(q0, TL::TW, l, base, lam, a.advf, a.gm1f, Fb, ub);
+          mine = true;
+        }
+        pp = 2;
+      }
+    }
+    if (mine) {
+      const int s = (l - pp + 1) + NS / 2 - 1;
+#pragma unroll
+      for (int c = 0; c < S; c++) out[s * S + c] = ub[c];
+    } else if (l < NS) {
+      const int k = l - 2 * pp;
+      const int s = k < NS / 2 - pp ? k : k + 2 * pp;
+      if (s >= 0 && s < NS)
+#pragma unroll
+        for (int c = 0; c < S; c++) out[s * S + c] = 0.0f;
+    }
+  } else if (l == 0) {
+    // cells i-1..i+2 of the interface as FP64 values hi + lo
+    double qd[S][4], ub[4 * S];
+#pragma unroll
+    for (int c = 0; c < S; c++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) qd[c][k] = (double)thi[c][ic - 1 + k] + (double)tlo[c][ic - 1 + k];
+    flcat2_adj<FLUX>(&qd[0][1], 4, lamd, a.adv, a.gamma, a.limiter_form, Fbd, ub);
+    for (int s = 0; s < NS; s++) {
+      const int node = s - NS / 2 + 1;
+#pragma unroll
+      for (int c = 0; c < S; c++)
+        out[s * S + c] = (node >= -1 && node <= 2) ? (float)ub[(node + 1) * S + c] : 0.0f;
+    }
+  }
+}
+
+// Compensated gather: ubar^n = ubar^{n+1} + the float sum of the contributions
+// that map to the cell, added to the pair with TwoSum and renormalised.
+template <int P, int S>
+__global__ void __launch_bounds__(NT) k_adj_gather_f32(const Step1DArgs a, const float *__restrict__ ubar1,
+                                                       const float *__restrict__ contrib,
+                                                       float *__restrict__ ubar0) {
+  constexpr int NS = 2 * P > 4 ? 2 * P : 4;
+  constexpr int GA = P > 2 ? P : 2;
+  const long N = a.N;
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < N; i += (long)gridDim.x * NT) {
+    float acc[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) acc[c] = 0.0f;
+    long gs[2 * GA + 3];
+    int ng = 0;
+    if (a.bc == ACAT_BC_PERIODIC) {
+      for (long g = i - N; g <= i + N; g += N)
+        if (g >= -GA && g <= N - 1 + GA) gs[ng++] = g;
+    } else {
+      gs[ng++] = i;
+      if (i == 0)
+        for (long g = -GA; g < 0; g++) gs[ng++] = g;
+      if (i == N - 1)
+        for (long g = N; g <= N - 1 + GA; g++) gs[ng++] = g;
+    }
+    for (int t = 0; t < ng; t++) {
+      const long g = gs[t];
+      for (int s = 0; s < NS; s++) {
+        const long m = g + 1 - (s - NS / 2 + 1);
+        if (m < 0 || m > N) continue;
+#pragma unroll
+        for (int c = 0; c < S; c++) acc[c] += contrib[(m * NS + s) * S + c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const float h = ubar1[c * N + i], w = ubar1[(S + c) * N + i], d = acc[c];
+      const float s = __fadd_rn(h, d);
+      const float bp = __fsub_rn(s, h);
+      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+      const float w2 = __fadd_rn(w, e);
+      const float hn = __fadd_rn(s, w2);
+      ubar0[c * N + i] = hn;
+      ubar0[(S + c) * N + i] = __fsub_rn(w2, __fsub_rn(hn, s));
+    }
+  }
+}
+
+template <int FLUX>
+int launch_adj_f32(int P, const Step1DArgs &a, const float *ub1, float *contrib, float *ub0, cudaStream_t st) {
+  constexpr int S = Phys<FLUX>::S;
+  const long blocks = (a.N + NT - 1) / NT;
+  const unsigned g2 = (unsigned)(blocks < 4096 ? blocks : 4096);
+  switch (P) {
+#define ACAT_ADJ32_CASE(PP)                                                                       \
+  case PP: {                                                                                      \
+    const unsigned grid = (unsigned)((a.N + Tiling<PP, NWF>::NI) / Tiling<PP, NWF>::NI);          \
+    k_adj1d_f32<PP, FLUX><<<grid, NWF * 32, 0, st>>>(a, ub1, contrib);                            \
+    k_adj_gather_f32<PP, S><<<g2, NT, 0, st>>>(a, ub1, contrib, ub0);                             \
+  } break;
+    ACAT_ADJ32_CASE(1)
+    ACAT_ADJ32_CASE(2)
+    ACAT_ADJ32_CASE(3)
+    ACAT_ADJ32_CASE(4)
+#undef ACAT_ADJ32_CASE
+  default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
 template <int FLUX>
 int launch_adj_f(int P, const Step1DArgs &a, const double *ub1, double *contrib, double *ub0,
                  cudaStream_t st) {
@@ -524,9 +704,21 @@ int launch_adj_f(int P, const Step1DArgs &a, const double *ub1, double *contrib,
 
 int acat_adjoint_slots(int P) { return 2 * P > 4 ? 2 * P : 4; }
 
-int acat_launch_adjoint1d(int P, int flux, const Step1DArgs &a, const double *ubar1, double *contrib,
-                          double *ubar0, void *stream) {
+int acat_launch_adjoint1d(int P, int flux, int prec, const Step1DArgs &a, const void *ubar1_, void *contrib_,
+                          void *ubar0_, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == ACAT_PREC_F32) {
+    const float *ubar1 = static_cast<const float *>(ubar1_);
+    float *contrib = static_cast<float *>(contrib_), *ubar0 = static_cast<float *>(ubar0_);
+    switch (flux) {
+    case ACAT_FLUX_LINEAR: return launch_adj_f32<ACAT_FLUX_LINEAR>(P, a, ubar1, contrib, ubar0, st);
+    case ACAT_FLUX_BURGERS: return launch_adj_f32<ACAT_FLUX_BURGERS>(P, a, ubar1, contrib, ubar0, st);
+    case ACAT_FLUX_EULER1D: return launch_adj_f32<ACAT_FLUX_EULER1D>(P, a, ubar1, contrib, ubar0, st);
+    }
+    return (int)cudaErrorInvalidValue;
+  }
+  const double *ubar1 = static_cast<const double *>(ubar1_);
+  double *contrib = static_cast<double *>(contrib_), *ubar0 = static_cast<double *>(ubar0_);
   switch (flux) {
   case ACAT_FLUX_LINEAR: return launch_adj_f<ACAT_FLUX_LINEAR>(P, a, ubar1, contrib, ubar0, st);
   case ACAT_FLUX_BURGERS: return launch_adj_f<ACAT_FLUX_BURGERS>(P, a, ubar1, contrib, ubar0, st);

@@ -588,15 +588,12 @@ int adjoint_launch(acat_ctx *c, const void *u_n, double dt, const double *dt_dev
   a.u_in = u_n;
   a.dt_fixed = dt;
   a.dt_in = dt_dev;
-  int e = acat_launch_adjoint1d(c->p.P, c->p.flux, a, static_cast<const double *>(ubar1), c->d_contrib,
-                                static_cast<double *>(ubar0), st);
+  int e = acat_launch_adjoint1d(c->p.P, c->p.flux, c->p.precision, a, ubar1, c->d_contrib, ubar0, st);
   c->launches += 2;
   return e ? ACAT_ERR_CUDA : ACAT_OK;
 }
 
-bool adjoint_ctx(const acat_ctx *c) {
-  return c->dim == 1 && !c->batched && c->p.precision == ACAT_PREC_F64;
-}
+bool adjoint_ctx(const acat_ctx *c) { return c->dim == 1 && !c->batched; }
 
 }  // namespace
 

@@ -41,6 +41,10 @@ __device__ __forceinline__ float recip(float x) {
   return y;
 }
 
+// fused multiply-add in the arithmetic type of its arguments
+__device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <typename R>
 struct Tab;
 template <>

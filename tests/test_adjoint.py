@@ -275,3 +275,75 @@ def test_record_and_reverse_run_checkpoint_intervals(env):
         assert ctx.acat_status() == 0
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+# ---------------------------------------------------------------------------
+# FP32 adjoint (compensated state and cotangent)
+# ---------------------------------------------------------------------------
+F32_STEP_TOL = 2e-6
+
+
+@pytest.mark.parametrize("kind,P,N,bc", [("riemann", 2, 64, 1), ("riemann", 3, 96, 1), ("riemann", 4, 128, 0),
+                                         ("pulse", 2, 64, 0), ("burgers", 3, 60, 1)])
+def test_adjoint_step_f32_matches_f64(env, kind, P, N, bc):
+    """The FP32 adjoint step against the FP64 adjoint step at the same state
+    value hi + lo (same order decisions): float rounding of the reverse sweep
+    only. Bound: a node cotangent is a sum of about 30 products of O(1)
+    Jacobian entries and weights with the interface cotangent, each rounded
+    within eps32 = 6e-8 of its size: 30 x 6e-8 < 2e-6 of max|J^T w| (observed
+    2e-7)."""
+    torch, O, acat, adjoint = env
+    c = _state(kind, N, P, bc)
+    kw = c.problem_kwargs()
+    pair = acat.to_pair(c.u0)
+    x = acat.from_pair(pair)
+    pr = O.Problem(**kw)
+    dt = O.dt_cfl(pr, x)
+    w = np.random.default_rng(11).normal(size=c.u0.shape)
+    with acat.Context(**kw) as c64, acat.Context(**kw, precision=acat.PREC_F32) as c32:
+        out64 = torch.empty(c.u0.shape, dtype=torch.float64, device="cuda")
+        c64.acat_adjoint_step(torch.from_numpy(x).cuda(), dt, torch.from_numpy(w).cuda(), out64)
+        wp = torch.from_numpy(acat.to_pair(w)).cuda()
+        out32 = torch.empty_like(wp)
+        c32.acat_adjoint_step(torch.from_numpy(pair).cuda(), dt, wp, out32)
+        torch.cuda.synchronize()
+        ref = out64.cpu().numpy()
+        got = acat.from_pair(out32.cpu().numpy())
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"f32 adjoint {kind} P={P}: rel err {err:.2e}")
+    assert err < F32_STEP_TOL, err
+
+
+def test_adjoint_run_f32_along_its_trajectory(env):
+    """60 steps: the FP32 gradient (recorded FP32 forward, FP32 reverse run)
+    against FP64 adjoint steps applied along the same FP32 trajectory (states
+    hi + lo, recorded dt); per-step float rounding accumulates at most
+    linearly: 60 x 2e-6 (observed 2e-6)."""
+    torch, O, acat, adjoint = env
+    c = _state("riemann", 512, 3, 1, seed=2)
+    kw = c.problem_kwargs()
+    n = 60
+    wN = np.random.default_rng(3).normal(size=c.u0.shape)
+    with acat.Context(**kw, precision=acat.PREC_F32) as c32, acat.Context(**kw) as c64:
+        u0 = torch.from_numpy(acat.to_pair(c.u0)).cuda().requires_grad_(True)
+        uN = adjoint.run(u0, c32, n, every=7)
+        (uN * torch.from_numpy(np.stack([wN, wN])).cuda().float()).sum().backward()
+        g32 = u0.grad[0].double().cpu().numpy()
+        assert np.array_equal(u0.grad[0].cpu().numpy(), u0.grad[1].cpu().numpy())
+        # the FP32 trajectory and its dt: the recorded run with every state kept
+        p0 = torch.from_numpy(acat.to_pair(c.u0)).cuda()
+        ckpt = torch.empty((n,) + tuple(p0.shape), dtype=torch.float32, device="cuda")
+        dtt = torch.empty(n, dtype=torch.float64, device="cuda")
+        c32.acat_run_record(p0, torch.empty_like(p0), n, 1, ckpt, dtt)
+        torch.cuda.synchronize()
+        states = [acat.from_pair(ckpt[k].cpu().numpy()) for k in range(n)]
+        dts = dtt.cpu().tolist()
+        wb = torch.from_numpy(wN.copy()).cuda()
+        out = torch.empty_like(wb)
+        for k in reversed(range(n)):
+            c64.acat_adjoint_step(torch.from_numpy(states[k]).cuda(), dts[k], wb, out)
+            wb, out = out, wb
+        g64 = wb.cpu().numpy()
+    err = np.abs(g32 - g64).max() / np.abs(g64).max()
+    print(f"f32 gradient 60 steps: rel err {err:.2e}")
+    assert err < n * F32_STEP_TOL, err

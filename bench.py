@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "batch_f32", "adjoint"],
+                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "batch_f32", "adjoint", "adjoint_f32"],
                     help="profiling runs: one short measurement of a single workload")
     return ap.parse_args()
 
@@ -356,25 +356,36 @@ def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
             "order_mix": {str(k): round(h[k] / (M + len(sizes)), 4) for k in range(1, 5)}}
 
 
-def measure_adjoint(torch, acat, W, K, flush, steps=2000):
+def measure_adjoint(torch, acat, W, K, flush, steps=2000, prec=0):
     """Gradient of the L2 misfit L = dx/2 sum |u^n - u_target|^2 for the 1D
     Euler acoustic pulse (P = 2, N = 8192, periodic, 2000 steps, target from a
     second seed): the recorded forward run plus the reverse run (recompute per
-    sqrt(n) segment + adjoint steps), against the plain FP64 forward run."""
+    sqrt(n) segment + adjoint steps), against the plain forward run of the
+    same precision (FP32: compensated pair states and cotangents)."""
     from paper_2007_01416_gb300 import adjoint as A
     c = W.acoustic_pulse(nx=8192, seed=SEED, P=2, steps=steps)
     tc = W.acoustic_pulse(nx=8192, seed=SEED + 1, P=2, steps=steps)
     n, nx = c.steps, c.nx
     dx = (c.x1 - c.x0) / nx
-    ctx = acat.Context(**c.problem_kwargs())
-    u0 = torch.from_numpy(c.u0.copy()).cuda()
-    target = torch.from_numpy(tc.u0.copy()).cuda()
+    f32 = prec == acat.PREC_F32
+    conv = acat.to_pair if f32 else (lambda v: v.copy())
+    ctx = acat.Context(**c.problem_kwargs(), precision=prec)
+    u0 = torch.from_numpy(conv(c.u0)).cuda()
+    target = torch.from_numpy(conv(tc.u0)).cuda()
     ctx.acat_run(target, n)
     every = A.default_every(n)
-    ckpt = torch.empty((-(-n // every),) + tuple(u0.shape), dtype=torch.float64, device="cuda")
+    ckpt = torch.empty((-(-n // every),) + tuple(u0.shape), dtype=u0.dtype, device="cuda")
     dts = torch.empty(n, dtype=torch.float64, device="cuda")
     uN, g, u = torch.empty_like(u0), torch.empty_like(u0), torch.empty_like(u0)
     stream = torch.cuda.current_stream()
+
+    def seed(gb):
+        if f32:  # compensated cotangent (value, 0) of the state value hi + lo
+            gb[0] = ((uN[0] - target[0]) + (uN[1] - target[1])) * dx
+            gb[1].zero_()
+        else:
+            gb.copy_(uN).sub_(target).mul_(dx)
+
     u.copy_(u0)
     ctx.acat_run(u, 96)
     m = min(n, 64)
@@ -393,7 +404,7 @@ def measure_adjoint(torch, acat, W, K, flush, steps=2000):
         flush.zero_()
         e[2].record(stream)
         ctx.acat_run_record(u0, uN, n, every, ckpt, dts)
-        g.copy_(uN).sub_(target).mul_(dx)  # dL/du^n
+        seed(g)  # dL/du^n
         ctx.acat_adjoint_run(ckpt, dts, n, every, g, g)
         e[3].record(stream)
         torch.cuda.synchronize()
@@ -404,7 +415,7 @@ def measure_adjoint(torch, acat, W, K, flush, steps=2000):
     for _ in range(K):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
-        g.copy_(uN).sub_(target).mul_(dx)
+        seed(g)
         e0.record(stream)
         ctx.acat_adjoint_run(ckpt, dts, n, every, g, g)
         e1.record(stream)
@@ -419,6 +430,89 @@ def measure_adjoint(torch, acat, W, K, flush, steps=2000):
             "gradient_vs_forward_time": t_g / t_f,
             "adjoint_step_vs_forward_step_est": (t_a - recompute) / t_f,
             "launches": launches}
+
+
+def measure_small(torch, acat, W, K):
+    """The launch-bound configuration: Burgers P = 2, N = 400 cells, periodic,
+    CFL 0.5, 300 steps (FP64). Reports the time per step when the run is
+    replayed from CUDA graphs and when every step is its own stream launch
+    (acat_step at the run's recorded dt)."""
+    c = W.burgers_sine(nx=400, seed=SEED, P=2, steps=300)
+    n = c.steps
+    ctx = acat.Context(**c.problem_kwargs())
+    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    u, nxt = torch.empty_like(u0), torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    # the run's dt sequence (recorded forward, outside timing)
+    ck = torch.empty((n,) + tuple(u0.shape), dtype=torch.float64, device="cuda")
+    dts = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.acat_run_record(u0, u, n, 1, ck, dts)
+    dt_host = dts.cpu().tolist()
+    u.copy_(u0)
+    ctx.acat_run(u, n)
+    torch.cuda.synchronize()
+    tg, ts = [], []
+    for _ in range(K):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        e0.record(stream)
+        ctx.acat_run(u, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tg.append(e0.elapsed_time(e1))
+        a, b = u0.clone(), nxt
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(n):
+            ctx.acat_step(a, b, dt_host[k])
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.close()
+    g, st = min(tg), min(ts)
+    return {"value": c.nx * n / (g * 1e-3), "unit": UNIT, "steps": n, "nx": c.nx,
+            "us_per_step_graph": 1e3 * g / n, "us_per_step_stream_launches": 1e3 * st / n,
+            "graph_saving_us_per_step": 1e3 * (st - g) / n}
+
+
+def measure_linear(torch, acat, W, flops, prec, P, nx, steps, K, flush, peak):
+    """Linear transport u_t + u_x = 0 (periodic, CFL 0.5) from the seeded
+    sine data of the Burgers configuration: the recursion's FMA and shuffle
+    core without divisions."""
+    import numpy as np
+    c = W.burgers_sine(nx=nx, seed=SEED, P=P, steps=steps)
+    kw = dict(c.problem_kwargs(), flux=W.LINEAR, adv=(1.0, 0.0))
+    ctx = acat.Context(**kw, precision=prec)
+    host = acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()
+    u0 = torch.from_numpy(host).cuda()
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    u.copy_(u0)
+    ctx.acat_run(u, 96)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        e0.record(stream)
+        ctx.acat_run(u, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    orders = torch.zeros(nx + 1, dtype=torch.int8, device="cuda")
+    tmp = torch.empty_like(u)
+    ctx.acat_step(u, tmp, -1.0, None, None, orders)
+    torch.cuda.synchronize()
+    h = np.bincount(orders.cpu().numpy().astype(np.int64), minlength=5)
+    fl = flops.step_flops_1d({k: int(h[k]) for k in range(1, 5)}, P, W.LINEAR, nx)
+    t = min(ms)
+    ctx.close()
+    return {"value": nx * steps / (t * 1e-3), "unit": UNIT, "steps": steps, "nx": nx, "P": P,
+            "roofline_frac": fl / (t / steps * 1e-3) / peak,
+            "order_mix": {str(k): round(int(h[k]) / (nx + 1), 4) for k in range(1, 5)}}
 
 
 def run_ours(args):
@@ -517,7 +611,18 @@ def run_ours(args):
         variants["batched_euler_P3_4096inst_f32"] = b32
         variants["batched_euler_P3_4096inst_f64"] = b64
         # gradient through 2000 steps (hand-written adjoint, sqrt(n) checkpoints)
-        variants["adjoint_euler_P2_8192_f64"] = measure_adjoint(torch, acat, W, 2, flush)
+        # the launch-bound Burgers configuration and linear transport (no divisions)
+        variants["burgers_P2_400_f64"] = measure_small(torch, acat, W, 3)
+        lin64 = measure_linear(torch, acat, W, flops, acat.PREC_F64, 4, NX, 1000, 2, flush, peak64)
+        lin32 = measure_linear(torch, acat, W, flops, acat.PREC_F32, 4, NX, 1000, 2, flush, peak32)
+        lin64["roofline_peak"], lin32["roofline_peak"] = "fp64", "fp32"
+        variants["linear_P4_16384_f64"] = lin64
+        variants["linear_P4_16384_f32"] = lin32
+        a64 = measure_adjoint(torch, acat, W, 2, flush)
+        a32 = measure_adjoint(torch, acat, W, 2, flush, prec=acat.PREC_F32)
+        a32["gradient_speedup_vs_f64"] = a64["ms_gradient"] / a32["ms_gradient"]
+        variants["adjoint_euler_P2_8192_f64"] = a64
+        variants["adjoint_euler_P2_8192_f32"] = a32
 
     if rank != 0:
         return 0
@@ -568,8 +673,9 @@ def run_single(args):
         f32 = args.workload == "2d_f32"
         out = measure_2d(torch, acat, W, flops, 4096 if f32 else 1024,
                          acat.PREC_F32 if f32 else acat.PREC_F64, n, 1, flush, 1.0)
-    elif args.workload == "adjoint":
-        out = measure_adjoint(torch, acat, W, 1, flush, steps=n)
+    elif args.workload in ("adjoint", "adjoint_f32"):
+        out = measure_adjoint(torch, acat, W, 1, flush, steps=n,
+                              prec=acat.PREC_F32 if args.workload == "adjoint_f32" else acat.PREC_F64)
     else:
         out = measure_batch(torch, acat, W, flops, acat.PREC_F32, n, 1, flush, 1.0)
     print(json.dumps({"workload": args.workload, **{k: v for k, v in out.items()

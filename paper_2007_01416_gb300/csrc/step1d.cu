@@ -544,10 +544,16 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
 }
 
 // One FP32 tile on the compensated state [hi(s x M); lo(s x M)].
+// Two CTA barriers per tile: after staging (which also publishes *lam_sm,
+// written by the caller before the call) and between the flux and update
+// phases. There is none at the end: a caller that loops over tiles
+// alternates between two workspaces (and two lam slots), so the next tile's
+// staging cannot overwrite what a slower warp still reads. The wave speed
+// maximum goes out per warp (atomic max of the warps that updated cells).
 template <int P, int FLUX>
 __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FLUX>::S> &sm,
                                          const float *__restrict__ uin, float *__restrict__ uout,
-                                         long off, long M, long N, long i0, float lam,
+                                         long off, long M, long N, long i0, const float *lam_sm,
                                          int8_t *orders, unsigned long long *smax_out) {
   using TL = Tiling<P>;
   using DP = DPhys<FLUX>;
@@ -559,6 +565,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     sm.tlo[c][k] = uin[(S + c) * M + g];
   }
   __syncthreads();
+  const float lam = *lam_sm;
   const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -641,9 +648,9 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     smax = fmaxf(smax, sf);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
-  const float v = block_max_f(smax, sm.redf);
-  if (threadIdx.x == 0) atomic_max_pos(smax_out, (double)v);
-  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0 && warp * 32 < TL::T) atomic_max_pos(smax_out, (double)smax);
 }
 
 template <int P, int FLUX>
@@ -662,9 +669,8 @@ __global__ void __launch_bounds__(NT, MinCtas<P, true>::value) k_step1d_f32(cons
   __shared__ Smem32<P, DPhys<FLUX>::S> sm;
   __shared__ float s_lam;
   if (threadIdx.x == 0) s_lam = (float)(step_dt(a) / a.dx);
-  __syncthreads();
   tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0,
-                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_lam, a.orders,
+                    a.N, a.N, (long)blockIdx.x * Tiling<P>::T, &s_lam, a.orders,
                     &a.smax[(a.slot + 1) % 3]);
 }
 
@@ -843,27 +849,32 @@ __device__ double batch_dt(const Step1DArgs &a, const BatchArgs &bt, int b, bool
 template <int P, int FLUX, bool F32>
 __global__ void __launch_bounds__(NT, MinCtas<P, F32>::value) k_batch1d(const Step1DArgs a, const BatchArgs bt) {
   using SM = typename std::conditional<F32, Smem32<P, Phys<FLUX>::S>, Smem64<P, Phys<FLUX>::S>>::type;
-  __shared__ SM sm;
+  // FP32: two workspaces used alternately (tile_f32 ends without a barrier)
+  __shared__ SM sm[F32 ? 2 : 1];
   __shared__ double s_lam;
-  __shared__ float s_lamf;
+  __shared__ float s_lamf[2];
+  int par = 0;
   for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
     const int b = bt.tiles[w].b;
     const long i0 = (long)bt.tiles[w].tile * Tiling<P>::T;
     const long off = bt.offs[b], N = bt.offs[b + 1] - off;
     if (threadIdx.x == 0) {
       const double dx = bt.xlen / (double)N;
-      s_lam = batch_dt(a, bt, b, i0 == 0, dx) / dx;
-      s_lamf = (float)s_lam;
+      const double l = batch_dt(a, bt, b, i0 == 0, dx) / dx;
+      if constexpr (F32) s_lamf[par] = (float)l;
+      else s_lam = l;
     }
-    __syncthreads();
     int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
     unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
-    if constexpr (F32)
-      tile_f32<P, FLUX>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), off,
-                        bt.M, N, i0, s_lamf, ord, so);
-    else
-      tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
+    if constexpr (F32) {
+      tile_f32<P, FLUX>(a, sm[par], static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), off,
+                        bt.M, N, i0, &s_lamf[par], ord, so);
+      par ^= 1;
+    } else {
+      __syncthreads();
+      tile_f64<P, FLUX>(a, sm[0], static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
                         off, bt.M, N, i0, s_lam, ord, so);
+    }
   }
 }
 

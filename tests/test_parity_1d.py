@@ -49,6 +49,8 @@ CASES = [
     ("linear", 4, 257, 0), ("linear", 2, 130, 1),
     ("euler", 4, 16384, 1), ("euler", 3, 1001, 1), ("euler", 2, 777, 0), ("euler", 1, 64, 1),
     ("euler", 4, 16, 0), ("euler", 2, 8, 1),
+    # sizes large enough for the small-CTA step with the boundary hand-off
+    ("euler", 3, 12001, 0), ("burgers", 4, 15001, 1), ("linear", 2, 30001, 0), ("euler", 1, 40001, 1),
 ]
 
 
@@ -127,9 +129,10 @@ def test_free_run_burgers_config(env):
     assert abs(math.fsum(ug[0]) - math.fsum(c.u0[0])) < 1e-11 * 400 * b
 
 
-def test_run_equals_repeated_steps(env):
+@pytest.mark.parametrize("nx", [3000, 20001])  # 8-warp fused step, small-CTA step
+def test_run_equals_repeated_steps(env, nx):
     torch, O, acat = env
-    c = W.euler1d_riemann_entropy(nx=3000, seed=5, P=4, steps=101)
+    c = W.euler1d_riemann_entropy(nx=nx, seed=5, P=4, steps=101)
     kw = c.problem_kwargs()
     with acat.Context(**kw) as ctx:
         u = torch.from_numpy(c.u0.copy()).cuda()
@@ -143,9 +146,10 @@ def test_run_equals_repeated_steps(env):
         assert torch.equal(u, v)
 
 
-def test_t_end_clipping(env):
+@pytest.mark.parametrize("nx", [1024, 30001])
+def test_t_end_clipping(env, nx):
     torch, O, acat = env
-    c = W.euler1d_riemann_entropy(nx=1024, seed=6, P=2)
+    c = W.euler1d_riemann_entropy(nx=nx, seed=6, P=2)
     kw = c.problem_kwargs()
     with acat.Context(**kw) as ctx:
         u = torch.from_numpy(c.u0.copy()).cuda()

@@ -47,6 +47,7 @@ class _Params(ctypes.Structure):
     _fields_ = [
         ("flux", ctypes.c_int), ("P", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("bc", ctypes.c_int), ("tau_factorial", ctypes.c_int), ("limiter_form", ctypes.c_int),
+        ("psi2_mod", ctypes.c_int), ("lo_flux", ctypes.c_int),
         ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2), ("cfl", ctypes.c_double),
         ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
         ("y1", ctypes.c_double), ("psi_tol", ctypes.c_double), ("eps", ctypes.c_double),
@@ -72,6 +73,8 @@ class Problem:
     eps: float = 1e-12
     tau_factorial: int = 1
     limiter_form: int = 0
+    psi2_mod: int = 0   # 1: modified indicator psi~^2 (Sec. 3.2)
+    lo_flux: int = 0    # F^lo: 0 Rusanov, 1 global Lax-Friedrichs, 2 HLL
     extra: dict = field(default_factory=dict)
 
     @property
@@ -90,6 +93,7 @@ class Problem:
         p = _Params()
         p.flux, p.P, p.nx, p.ny, p.bc = self.flux, self.P, self.nx, self.ny, self.bc
         p.tau_factorial, p.limiter_form = self.tau_factorial, self.limiter_form
+        p.psi2_mod, p.lo_flux = self.psi2_mod, self.lo_flux
         p.gamma = self.gamma
         p.adv[0], p.adv[1] = self.adv
         p.cfl, p.x0, p.x1, p.y0, p.y1 = self.cfl, self.x0, self.x1, self.y0, self.y1

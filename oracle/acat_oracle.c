@@ -150,6 +150,29 @@ static double or_psi_p(const or_params *P, const or_tables *T, int p, const doub
   return Ip / (Ip + tau);
 }
 
+/* Modified indicator psi~^2 of one component (Sec. 3.2, the variant for
+ * critical points at the midpoints x_{i-1/2}, x_{i+3/2}): the two splits of
+ * the three differences of S_2 into lateral weights that keep the central
+ * difference,
+ *   I^1_L = d_{-1}^2 + eps,          I^1_R = d_0^2 + d_1^2 + eps,
+ *   I^2_L = d_{-1}^2 + d_0^2 + eps,  I^2_R = d_1^2 + eps,
+ * with d_j = f_{i+1+j} - f_{i+j}; I^j = I^j_L I^j_R / (I^j_L + I^j_R); and
+ * psi~^2 = max(I^1 / (I^1 + tau_2), I^2 / (I^2 + tau_2)), tau_2 as in
+ * Eq. 3.12. The maximum is taken as (a > b ? a : b). */
+static double or_psi2_mod(const or_params *P, const or_tables *T, const double *q, int ic) {
+  const double dm = q[ic] - q[ic - 1], d0 = q[ic + 1] - q[ic], dp = q[ic + 2] - q[ic + 1];
+  const double I1L = dm * dm + P->eps, I1R = (d0 * d0 + dp * dp) + P->eps;
+  const double I2L = (dm * dm + d0 * d0) + P->eps, I2R = dp * dp + P->eps;
+  const double I1 = I1L * I1R / (I1L + I1R), I2 = I2L * I2R / (I2L + I2R);
+  double S = 0.0;
+  for (int j = -1; j <= 2; j++) S = S + T->gd[2][j + 1] * q[ic + j];
+  const double fact = P->tau_factorial ? 6.0 : 1.0; /* (2p-1)! at p = 2 */
+  const double D = fact * S;
+  const double tau = D * D;
+  const double a = I1 / (I1 + tau), b = I2 / (I2 + tau);
+  return a > b ? a : b;
+}
+
 /* Admissible set and selected order (Eqs. 3.2-3.3; systems: minimum over the
  * components, Sec. 3.4). Returns p_s = max A, or 1 when A is empty. */
 static int or_select(const or_params *P, const or_tables *T, const double *line, int LW,
@@ -161,7 +184,8 @@ static int or_select(const or_params *P, const or_tables *T, const double *line,
   for (int p = 2; p <= P->P; p++) {
     double m = 0.0;
     for (int c = 0; c < s; c++) {
-      const double v = or_psi_p(P, T, p, line + c * LW, ic);
+      const double v = (p == 2 && P->psi2_mod) ? or_psi2_mod(P, T, line + c * LW, ic)
+                                               : or_psi_p(P, T, p, line + c * LW, ic);
       if (c == 0 || v < m) m = v;
     }
     if (psi) psi[p] = m;

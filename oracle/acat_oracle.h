@@ -36,6 +36,11 @@ typedef struct {
   int tau_factorial; /* 1: tau_p = ((2p-1)! Delta)^2 as printed in Eq. 3.12     */
   int limiter_form;  /* 0: Roe-speed side (Eq. 3.6) for scalar laws, min form
                         (Eq. 3.7) for systems; 1: min form everywhere          */
+  int psi2_mod;      /* 1: the modified indicator psi~^2 of Sec. 3.2 (maximum of
+                        the two lateral-weight splits that include the central
+                        difference) in place of psi^2                          */
+  int lo_flux;       /* robust first-order flux F^lo of Eq. 3.4: 0 Rusanov
+                        (local LF), 1 global LF (alpha = dx / dt), 2 HLL        */
   double gamma;      /* ratio of specific heats (Euler)                         */
   double adv[2];     /* linear advection speeds a, b                            */
   double cfl;

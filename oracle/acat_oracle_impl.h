@@ -307,15 +307,73 @@ static R FN(psi1)(const or_params *P, const R *line, int LW, int ic, int dir) {
   return best;
 }
 
-/* Robust first-order flux F^lo: Rusanov (local Lax-Friedrichs), the reading
- * taken for the unspecified "robust first order numerical flux" of Eq. 3.4. */
-static void FN(rusanov)(const or_params *P, const R *ul, const R *ur, int dir, R *F) {
+/* Smallest and largest eigenvalue of the flux Jacobian in direction dir:
+ * a (transport), u (Burgers), v_n -/+ c (Euler). */
+static void FN(eig_bounds)(const or_params *P, const R *u, int dir, R *lmin, R *lmax) {
+  switch (P->flux) {
+  case OR_LINEAR: *lmin = *lmax = P->adv[dir]; return;
+  case OR_BURGERS: *lmin = *lmax = u[0]; return;
+  case OR_EULER1D: {
+    R rho = u[0], m = u[1], E = u[2];
+    R v = m / rho;
+    R p = (P->gamma - 1.0) * (E - 0.5 * rho * v * v);
+    R c = SQRT_R(P->gamma * p / rho);
+    *lmin = v - c;
+    *lmax = v + c;
+    return;
+  }
+  default: {
+    R rho = u[0], mx = u[1], my = u[2], E = u[3];
+    R v = mx / rho, w = my / rho;
+    R p = (P->gamma - 1.0) * (E - 0.5 * rho * (v * v + w * w));
+    R vn = dir == 0 ? v : w;
+    R c = SQRT_R(P->gamma * p / rho);
+    *lmin = vn - c;
+    *lmax = vn + c;
+    return;
+  }
+  }
+}
+
+/* Robust first-order flux F^lo of Eq. 3.4 (left unspecified there), between
+ * the states ul, ur in direction dir; h = dx or dy. lo_flux selects
+ *   0: Rusanov (local Lax-Friedrichs), 1/2 (f_l + f_r) - 1/2 alpha (u_r - u_l),
+ *      alpha the larger spectral radius of the two states (the default reading);
+ *   1: global Lax-Friedrichs, the same with alpha = h / dt;
+ *   2: HLL with the wave-speed bounds s_l = min of the two states' smallest
+ *      eigenvalues, s_r = max of their largest:
+ *      f_l if s_l >= 0, f_r if s_r <= 0, otherwise
+ *      (s_r f_l - s_l f_r + s_l s_r (u_r - u_l)) / (s_r - s_l).
+ * The LF and HLL schemes are the first-order comparisons of Sec. 5. */
+static void FN(flux_lo)(const or_params *P, const R *ul, const R *ur, int dir, double dt, double h,
+                        R *F) {
   const int s = or_nvars(P);
   R fl[OR_MAXS], fq[OR_MAXS];
   FN(flux_dir)(P, ul, fl, dir);
   FN(flux_dir)(P, ur, fq, dir);
-  R al = FN(speed)(P, ul, dir), ar = FN(speed)(P, ur, dir);
-  R alpha = RE(ar) > RE(al) ? ar : al;
+  if (P->lo_flux == 2) {
+    R al, bl, ar, br;
+    FN(eig_bounds)(P, ul, dir, &al, &bl);
+    FN(eig_bounds)(P, ur, dir, &ar, &br);
+    R sl = RE(ar) < RE(al) ? ar : al;
+    R sr = RE(br) > RE(bl) ? br : bl;
+    if (RE(sl) >= 0.0) {
+      for (int c = 0; c < s; c++) F[c] = fl[c];
+    } else if (RE(sr) <= 0.0) {
+      for (int c = 0; c < s; c++) F[c] = fq[c];
+    } else {
+      for (int c = 0; c < s; c++)
+        F[c] = (sr * fl[c] - sl * fq[c] + sl * sr * (ur[c] - ul[c])) / (sr - sl);
+    }
+    return;
+  }
+  R alpha;
+  if (P->lo_flux == 1) {
+    alpha = h / dt;
+  } else {
+    R al = FN(speed)(P, ul, dir), ar = FN(speed)(P, ur, dir);
+    alpha = RE(ar) > RE(al) ? ar : al;
+  }
   for (int c = 0; c < s; c++) F[c] = 0.5 * (fl[c] + fq[c]) - 0.5 * alpha * (ur[c] - ul[c]);
 }
 
@@ -344,7 +402,7 @@ static int FN(iface_1d)(const or_params *P, const or_tables *T, const R *line,
     ur[c] = line[c * LW + ic + 1];
   }
   FN(cat_flux_1d)(P, T, 1, us, dt, dx, F1);
-  FN(rusanov)(P, ul, ur, 0, Flo);
+  FN(flux_lo)(P, ul, ur, 0, dt, dx, Flo);
   R w = FN(psi1)(P, line, LW, ic, 0);
   if (psi) psi[1] = RE(w);
   for (int c = 0; c < s; c++) F[c] = w * F1[c] + (1.0 - w) * Flo[c];
@@ -436,7 +494,7 @@ static int FN(iface_2d)(const or_params *P, const or_tables *T, const R *u, long
   FN(cat_flux_2d)(P, T, 1, ub, dt, dx, dy, F, Gf);
   R ul[OR_MAXS], ur[OR_MAXS], lo[OR_MAXS];
   for (int c = 0; c < s; c++) { ul[c] = line[c * LW + ic]; ur[c] = line[c * LW + ic + 1]; }
-  FN(rusanov)(P, ul, ur, dir, lo);
+  FN(flux_lo)(P, ul, ur, dir, dt, dir == 0 ? dx : dy, lo);
   R w = FN(psi1)(P, line, LW, ic, dir);
   for (int c = 0; c < s; c++) out[c] = w * (dir == 0 ? F[c] : Gf[c]) + (1.0 - w) * lo[c];
   return 1;

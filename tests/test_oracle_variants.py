@@ -1,0 +1,171 @@
+"""Pins of the oracle's switchable variants: the modified indicator psi~^2
+(Sec. 3.2) and the robust first-order fluxes F^lo of Eq. 3.4 (Rusanov, global
+Lax-Friedrichs, HLL: the first-order schemes the paper compares with, Sec. 5).
+
+The variants are fixed by independent statements: the critical-point case
+psi~^2 was introduced for (psi^2 rejects, psi~^2 accepts, 1 - psi~^2 = O(dx^2)),
+its behaviour on constant data, jumps and homotheties, and the textbook forms
+of the Lax-Friedrichs, upwind and HLL schemes on data where FL-CAT2 reduces to
+F^lo (psi^1 = 0).
+"""
+import numpy as np
+import pytest
+
+from paper_2007_01416_gb300 import workloads as W
+
+
+def _psi2(oracle, u, m, mod, eps=1e-12, bc=1):
+    """psi^2 (mod 0) or psi~^2 (mod 1) at interface m of the scalar state u."""
+    pr = oracle.Problem(flux=oracle.BURGERS, P=2, nx=u.size, bc=bc, psi2_mod=mod, eps=eps)
+    _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-9, want_psi=True)
+    return psi[m, 1]  # column p - 1 holds psi^p
+
+
+def _critical_state(h, n=16, m=8):
+    """f(x) = (x - x*)^2 + (x - x*)^3 sampled at cell centres, x* at the midpoint
+    between cells m-2 and m-1 (interface m separates cells m-1 and m): a critical
+    point of order 1 at 0.5 (x_{i-1} + x_i) with f''' != 0."""
+    x = (np.arange(n) + 0.5) * h
+    xs = 0.5 * (x[m - 2] + x[m - 1])
+    return (x - xs) ** 2 + (x - xs) ** 3
+
+
+def test_psi2_mod_accepts_the_midpoint_critical_point(oracle):
+    # Sec. 3.2: psi^2 cannot be shown to be 1 - O(dx^2) there (one term in a
+    # lateral weight); psi~^2 is, with k = 1 of its proposition
+    # (eps = 0: the estimates are for the indicator proper; eps = 1e-12 would
+    # dominate the h^6 lateral weight of psi^2 at this dx)
+    h = 1e-3
+    u = _critical_state(h)
+    p2, p2m = _psi2(oracle, u, 8, 0, eps=0.0), _psi2(oracle, u, 8, 1, eps=0.0)
+    assert p2 < 1e-3 and p2m > 0.999, (p2, p2m)
+    # 1 - psi~^2 = O(dx^2)
+    r = (1.0 - _psi2(oracle, _critical_state(2 * h), 8, 1, eps=0.0)) / (1.0 - p2m)
+    assert 3.5 < r < 4.5, r
+
+
+def test_psi2_mod_constant_jump_and_homothety(oracle):
+    u = np.full(12, 0.7)
+    assert _psi2(oracle, u, 6, 1) == 1.0  # tau = 0 exactly
+    # an isolated unit jump inside S_2 of smooth data: rejected for small dx
+    h = 1e-3
+    x = (np.arange(12) + 0.5) * h
+    u = np.sin(x) + (x > x[5] + 0.5 * h)
+    for m in (5, 6, 7):
+        assert _psi2(oracle, u, m, 1) < 1e-4
+    # homothetic invariance (eps = 0): psi~ of alpha f(beta x) equals psi~ of f
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        v = rng.normal(size=12)
+        a = rng.uniform(0.1, 10)
+        assert _psi2(oracle, a * v + 3.0, 6, 1, eps=0.0) == pytest.approx(_psi2(oracle, v, 6, 1, eps=0.0),
+                                                                           rel=1e-12)
+
+
+def _zigzag(n, base, amp):
+    return base + amp * (-1.0) ** np.arange(n)
+
+
+@pytest.mark.parametrize("flux", ["burgers", "linear", "euler"])
+def test_global_lf_is_the_lax_friedrichs_scheme(oracle, flux):
+    """P = 1 on zig-zag data: every limiter ratio is -1, psi^1 = 0, so the
+    step is the first-order scheme with F^lo. With alpha = dx/dt that is
+    u_i + (u_{i-1} + u_{i+1})/2 - u_i - lambda/2 (f_{i+1} - f_{i-1})."""
+    n = 20
+    if flux == "euler":
+        rho = _zigzag(n, 1.0, 0.2)
+        vel = np.full(n, 0.3)
+        p = _zigzag(n, 1.0, -0.1)
+        u = W.prim_to_cons_1d(rho, vel, p)
+        pr = oracle.Problem(flux=oracle.EULER1D, P=1, nx=n, bc=0, lo_flux=1)
+        f = lambda q: np.array([q[1], q[1] ** 2 / q[0] + 0.4 * (q[2] - 0.5 * q[1] ** 2 / q[0]),  # noqa: E731
+                                q[1] / q[0] * (q[2] + 0.4 * (q[2] - 0.5 * q[1] ** 2 / q[0]))])
+    elif flux == "burgers":
+        u = _zigzag(n, 1.0, 0.3)[None, :]
+        pr = oracle.Problem(flux=oracle.BURGERS, P=1, nx=n, bc=0, lo_flux=1)
+        f = lambda q: 0.5 * q * q  # noqa: E731
+    else:
+        u = _zigzag(n, 0.5, 0.25)[None, :]
+        pr = oracle.Problem(flux=oracle.LINEAR, P=1, nx=n, bc=0, lo_flux=1, adv=(0.8, 0.0))
+        f = lambda q: 0.8 * q  # noqa: E731
+    dt = 0.3 * pr.dx
+    un, _, orders = oracle.step_1d(pr, u, dt)
+    assert np.all(orders == 1)
+    lam = dt / pr.dx
+    um, up = np.roll(u, 1, axis=1), np.roll(u, -1, axis=1)
+    ref = 0.5 * (um + up) - 0.5 * lam * (f(up) - f(um))
+    assert np.allclose(un, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_hll_upwind_cases(oracle):
+    """HLL takes f(u_l) when both states' smallest eigenvalues are >= 0: the
+    first-order upwind scheme u_i - lambda (f_i - f_{i-1}); transport with
+    a > 0 and supersonic Euler flow (v > c) are such cases."""
+    n = 20
+    u = _zigzag(n, 0.5, 0.25)[None, :]
+    pr = oracle.Problem(flux=oracle.LINEAR, P=1, nx=n, bc=0, lo_flux=2, adv=(0.8, 0.0))
+    dt = 0.3 * pr.dx
+    un, _, orders = oracle.step_1d(pr, u, dt)
+    assert np.all(orders == 1)
+    nu = 0.8 * dt / pr.dx
+    assert np.allclose(un, u - nu * (u - np.roll(u, 1, axis=1)), rtol=1e-13, atol=1e-13)
+    rho = _zigzag(n, 1.0, 0.2)
+    p = _zigzag(n, 0.5, -0.1)
+    vel = np.full(n, 3.0)  # c <= sqrt(1.4 * 0.6 / 0.8) ~ 1.02
+    u = W.prim_to_cons_1d(rho, vel, p)
+    pr = oracle.Problem(flux=oracle.EULER1D, P=1, nx=n, bc=0, lo_flux=2)
+    dt = 0.1 * pr.dx
+    un, _, orders = oracle.step_1d(pr, u, dt)
+    assert np.all(orders == 1)
+    rr, mm, EE = u
+    vv = mm / rr
+    pp = 0.4 * (EE - 0.5 * rr * vv * vv)
+    F = np.array([mm, mm * vv + pp, vv * (EE + pp)])
+    lam = dt / pr.dx
+    assert np.allclose(un, u - lam * (F - np.roll(F, 1, axis=1)), rtol=1e-13, atol=1e-13)
+
+
+def test_hll_transonic_burgers_value(oracle):
+    """Burgers with u_l = -1, u_r = 2: s_l = -1, s_r = 2, and the HLL flux is
+    (2 * 0.5 - (-1) * 2 + (-1)(2)(2 - (-1))) / 3 = -1 (worked by hand).
+    The interface is an FL-CAT2 one with psi^1 = 0: Roe speed 1/2 > 0 picks
+    r- = (u_i - u_{i-1}) / (u_{i+1} - u_i) = -1/3, superbee 0."""
+    u = np.array([[0.0, 0.0, -1.0, 2.0, 2.0, 2.0]])
+    u[0, 1] = 0.0  # u_{i-1} = 0: u_i - u_{i-1} = -1
+    pr = oracle.Problem(flux=oracle.BURGERS, P=1, nx=6, bc=1, lo_flux=2)
+    F, orders = oracle.fluxes_1d_at(pr, u, 1e-3, [3])
+    assert orders[0] == 1
+    assert F[0, 0] == -1.0
+
+
+def test_rusanov_default_unchanged(oracle):
+    """lo_flux = 0 is the Rusanov flux: on transport with a > 0 it is also the
+    upwind flux a u_l."""
+    n = 16
+    u = _zigzag(n, 0.5, 0.25)[None, :]
+    pr = oracle.Problem(flux=oracle.LINEAR, P=1, nx=n, bc=0, adv=(0.8, 0.0))
+    dt = 0.3 * pr.dx
+    un, _, _ = oracle.step_1d(pr, u, dt)
+    nu = 0.8 * dt / pr.dx
+    assert np.allclose(un, u - nu * (u - np.roll(u, 1, axis=1)), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("lo_flux", [1, 2])
+def test_2d_variants_reduce_to_1d(oracle, lo_flux):
+    """x-only 2D Euler data: the 2D step with the F^lo variant equals the 1D
+    step with the same variant (y-fluxes cancel, F^lo uses h = dx in x)."""
+    N, NY = 32, 4
+    c1 = W.riemann_1d("sod", N, P=2)
+    pr1 = oracle.Problem(**c1.problem_kwargs(), lo_flux=lo_flux, psi2_mod=1)
+    rho, vel, pre = W.cons_to_prim_1d(c1.u0)
+    u2 = W.prim_to_cons_2d(*(np.repeat(a[None, :], NY, axis=0) for a in (rho, vel, 0 * vel, pre)))
+    pr2 = oracle.Problem(flux=oracle.EULER2D, P=2, nx=N, ny=NY, bc=1, cfl=0.8, lo_flux=lo_flux, psi2_mod=1)
+    dt = 0.4 * pr1.dx / 2.5
+    un1, _, o1 = oracle.step_1d(pr1, c1.u0, dt)
+    un2, _, ox, oy = oracle.step_2d(pr2, u2, dt)
+    assert np.any(o1 == 1)
+    for row in range(NY):
+        assert np.allclose(un2[0, row], un1[0], rtol=1e-13, atol=1e-13)
+        assert np.allclose(un2[1, row], un1[1], rtol=1e-13, atol=1e-13)
+        assert np.allclose(un2[3, row], un1[2], rtol=1e-13, atol=1e-13)
+        assert np.array_equal(ox[row], o1)

@@ -48,6 +48,8 @@ typedef struct acat_ctx acat_ctx; /* opaque, owned by the library */
 enum { ACAT_FLUX_LINEAR = 0, ACAT_FLUX_BURGERS = 1, ACAT_FLUX_EULER1D = 2, ACAT_FLUX_EULER2D = 3 };
 enum { ACAT_BC_PERIODIC = 0, ACAT_BC_TRANSMISSIVE = 1 };
 enum { ACAT_PREC_F64 = 0, ACAT_PREC_F32 = 1 };
+/* robust first-order flux F^lo of FL-CAT2 (Eq. 3.4 leaves it open) */
+enum { ACAT_LO_RUSANOV = 0, ACAT_LO_GLOBAL_LF = 1, ACAT_LO_HLL = 2 };
 
 enum {
   ACAT_OK = 0,
@@ -82,7 +84,15 @@ enum {
  *   tau_factorial 1 (default): tau_p = ((2p-1)! Delta^{2p-1})^2 as printed
  *                 in Eq. 3.12; 0 drops the factorial.
  *   limiter_form  0 (default): Roe-speed side for scalar laws (Eq. 3.6),
- *                 min form for systems (Eq. 3.7); 1: min form everywhere. */
+ *                 min form for systems (Eq. 3.7); 1: min form everywhere.
+ *   psi2_mod      1: the modified indicator psi~^2 of Sec. 3.2 (the larger of
+ *                 the two lateral-weight splits that keep the central
+ *                 difference) in place of psi^2; 0 (default): Eq. 3.12.
+ *   lo_flux       F^lo of FL-CAT2: ACAT_LO_RUSANOV (default, local LF with
+ *                 the larger spectral radius), ACAT_LO_GLOBAL_LF (alpha =
+ *                 dx / dt), ACAT_LO_HLL (wave-speed bounds: the smaller of the
+ *                 two states' smallest eigenvalues, the larger of their
+ *                 largest). The adjoint supports ACAT_LO_RUSANOV only. */
 typedef struct {
   int flux;
   int P;
@@ -91,6 +101,8 @@ typedef struct {
   int precision;
   int tau_factorial;
   int limiter_form;
+  int psi2_mod;
+  int lo_flux;
   double gamma;
   double adv[2];
   double cfl;
@@ -166,7 +178,8 @@ int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int ns
  * FP32 reverse sweep runs in float, FL-CAT2 interfaces in FP64 on hi + lo).
  * ubar_n must not alias ubar_np1. Uses a context-owned scratch array
  * ((nx+1) x max(2P,4) x s doubles, allocated on first use).
- * Errors: INVALID_ARG, UNSUPPORTED (2D or batched contexts), NOMEM, CUDA. */
+ * Errors: INVALID_ARG, UNSUPPORTED (2D or batched contexts, lo_flux other than
+ * ACAT_LO_RUSANOV), NOMEM, CUDA. */
 int acat_adjoint_step(acat_ctx *ctx, const void *u_n_dev, double dt, const void *ubar_np1_dev,
                       void *ubar_n_dev, void *stream);
 

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libacat.so")
 LINEAR, BURGERS, EULER1D, EULER2D = 0, 1, 2, 3
 PERIODIC, TRANSMISSIVE = 0, 1
 PREC_F64, PREC_F32 = 0, 1
+LO_RUSANOV, LO_GLOBAL_LF, LO_HLL = 0, 1, 2
 STATUS_NONPHYSICAL, STATUS_BAD_DT = 1, 2
 
 
@@ -30,7 +31,8 @@ class acat_params(ctypes.Structure):
     _fields_ = [
         ("flux", ctypes.c_int), ("P", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("tau_factorial", ctypes.c_int),
-        ("limiter_form", ctypes.c_int), ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2),
+        ("limiter_form", ctypes.c_int), ("psi2_mod", ctypes.c_int), ("lo_flux", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2),
         ("cfl", ctypes.c_double), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
         ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("psi_tol", ctypes.c_double),
         ("eps", ctypes.c_double),

@@ -35,6 +35,8 @@ struct Step1DArgs {
   int N;                      // cells
   int bc;                     // ACAT_BC_*
   int limiter_form;
+  int psi2_mod;               // 1: psi~^2 in place of psi^2
+  int lo_flux;                // F^lo: ACAT_LO_*
   int slot;                   // step index mod 3 (dt-reduction slots)
   double dx, cfl;
   double dt_fixed;            // > 0: imposed dt
@@ -86,6 +88,8 @@ struct Step2DArgs {
   int NX, NY;
   int bc;
   int limiter_form;
+  int psi2_mod;
+  int lo_flux;
   int slot;                   // step index mod 3
   double dx, dy, cfl;
   double dt_fixed, t_end;

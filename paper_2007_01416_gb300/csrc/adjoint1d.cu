@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(NWF * 32) k_adj1d(const Step1DArgs a, const do
   const int ic = il - 1 + TL::GH;
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int ps = select_order<P, S, false>(&tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l, grp,
-                                           active, valid, FC, a.eps, a.thr, a.fact_tau);
+                                           active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
   if (!active) return;
   double Fb[S];
 #pragma unroll
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(NWF * 32) k_adj1d_f32(const Step1DArgs a, cons
   const int icv = valid ? ic : 0;
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int ps = select_order<P, S, true>(nullptr, &thi[0][icv], &tlo[0][icv], TL::TW, l, grp, active, valid,
-                                          FC, a.eps, a.thr, a.fact_tau);
+                                          FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
   if (!active) return;
   // Fbar_m = lambda (ubar_m - ubar_{m-1}), cells outside 0..N-1 contribute nothing
   float Fb[S];

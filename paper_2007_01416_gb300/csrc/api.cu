@@ -75,6 +75,8 @@ int check_params(const acat_params *p) {
   if (!(p->x1 > p->x0) || !(p->y1 > p->y0)) return ACAT_ERR_INVALID_ARG;
   if (!(p->psi_tol >= 0.0 && p->psi_tol < 1.0)) return ACAT_ERR_INVALID_ARG;
   if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return ACAT_ERR_INVALID_ARG;
+  if (p->psi2_mod != 0 && p->psi2_mod != 1) return ACAT_ERR_INVALID_ARG;
+  if (p->lo_flux < ACAT_LO_RUSANOV || p->lo_flux > ACAT_LO_HLL) return ACAT_ERR_INVALID_ARG;
   if ((p->flux == ACAT_FLUX_EULER1D || p->flux == ACAT_FLUX_EULER2D) && !(p->gamma > 1.0))
     return ACAT_ERR_INVALID_ARG;
   const bool is2d = p->ny > 1 || p->flux == ACAT_FLUX_EULER2D;
@@ -96,6 +98,8 @@ Step1DArgs base_args(acat_ctx *c) {
   a.N = p.nx;
   a.bc = p.bc;
   a.limiter_form = p.limiter_form;
+  a.psi2_mod = p.psi2_mod;
+  a.lo_flux = p.lo_flux;
   a.dx = (p.x1 - p.x0) / (double)p.nx;
   a.cfl = p.cfl;
   a.dt_fixed = -1.0;
@@ -128,6 +132,8 @@ Step2DArgs base_args2(acat_ctx *c) {
   a.NY = p.ny;
   a.bc = p.bc;
   a.limiter_form = p.limiter_form;
+  a.psi2_mod = p.psi2_mod;
+  a.lo_flux = p.lo_flux;
   a.dx = (p.x1 - p.x0) / (double)p.nx;
   a.dy = (p.y1 - p.y0) / (double)p.ny;
   a.cfl = p.cfl;
@@ -593,7 +599,7 @@ int adjoint_launch(acat_ctx *c, const void *u_n, double dt, const double *dt_dev
   return e ? ACAT_ERR_CUDA : ACAT_OK;
 }
 
-bool adjoint_ctx(const acat_ctx *c) { return c->dim == 1 && !c->batched; }
+bool adjoint_ctx(const acat_ctx *c) { return c->dim == 1 && !c->batched && c->p.lo_flux == ACAT_LO_RUSANOV; }
 
 }  // namespace
 

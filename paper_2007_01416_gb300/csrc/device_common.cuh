@@ -98,6 +98,26 @@ __device__ __forceinline__ double psi_p_comp_g(Get q, int p, double eps, double 
   return __ddiv_rn(I, __dadd_rn(I, tau));
 }
 
+// Modified indicator psi~^2 (Sec. 3.2): the two splits of the three
+// differences of S_2 into lateral weights that keep the central one,
+// I^1 = (d_-^2 + eps, d_0^2 + d_+^2 + eps), I^2 = (d_-^2 + d_0^2 + eps, d_+^2 + eps),
+// and the larger of I^j / (I^j + tau_2), in the order of the definition.
+template <class Get>
+__device__ __forceinline__ double psi2m_comp_g(Get q, double eps, double fact) {
+  const double dm = __dsub_rn(q(0), q(-1)), d0 = __dsub_rn(q(1), q(0)), dp = __dsub_rn(q(2), q(1));
+  const double sm = __dmul_rn(dm, dm), s0 = __dmul_rn(d0, d0), sp = __dmul_rn(dp, dp);
+  const double I1L = __dadd_rn(sm, eps), I1R = __dadd_rn(__dadd_rn(s0, sp), eps);
+  const double I2L = __dadd_rn(__dadd_rn(sm, s0), eps), I2R = __dadd_rn(sp, eps);
+  const double I1 = __ddiv_rn(__dmul_rn(I1L, I1R), __dadd_rn(I1L, I1R));
+  const double I2 = __ddiv_rn(__dmul_rn(I2L, I2R), __dadd_rn(I2L, I2R));
+  double S = 0.0;
+  for (int j = -1; j <= 2; j++) S = __dadd_rn(S, __dmul_rn(c_tab.gd[2][j + 1], q(j)));
+  const double D = __dmul_rn(fact, S);
+  const double tau = __dmul_rn(D, D);
+  const double a = __ddiv_rn(I1, __dadd_rn(I1, tau)), b = __ddiv_rn(I2, __dadd_rn(I2, tau));
+  return a > b ? a : b;
+}
+
 __device__ __forceinline__ double psi_p_comp(const double *q, int st, int p, double eps, double fact) {
   return psi_p_comp_g([=](int j) { return q[j * st]; }, p, eps, fact);
 }
@@ -174,6 +194,37 @@ __device__ __forceinline__ int psi_filter(const float *d, const float *e, float 
   return -1;
 }
 
+// The filtered decision for psi~^2 (differences d_0..d_2 of S_2 with bounds
+// e): accept when either split's I certainly reaches r tau, reject when
+// neither can, else undecided; the bounds are those of psi_filter.
+__device__ __forceinline__ int psi2m_filter(const float *d, const float *e, float eps, float r, float fact) {
+  const float sm = d[0] * d[0], s0 = d[1] * d[1], sp = d[2] * d[2];
+  const float I1L = sm + eps, I1R = (s0 + sp) + eps, I2L = (sm + s0) + eps, I2R = sp + eps;
+  const float mn = fminf(fminf(I1L, I1R), fminf(I2L, I2R)), mx = fmaxf(fmaxf(I1L, I1R), fmaxf(I2L, I2R));
+  if (!(mn > 1e-30f) || !(mx < 1e30f)) return -1;
+  const float I1 = I1L * I1R / (I1L + I1R), I2 = I2L * I2R / (I2L + I2R);
+  float t[3], b[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    t[k] = d[k];
+    b[k] = e[k];
+  }
+#pragma unroll
+  for (int lev = 1; lev < 3; lev++)
+#pragma unroll
+    for (int k = 0; k < 3 - lev; k++) {
+      t[k] = t[k + 1] - t[k];
+      b[k] = (b[k + 1] + b[k]) + 5.97e-8f * fabsf(t[k]) + 1e-44f;
+    }
+  const float S = fabsf(t[0]), eS = 1.01f * b[0];
+  const float Dhi = (S + eS) * fact * 1.0000005f;
+  const float Dlo = fmaxf(S - eS, 0.0f) * fact * 0.9999995f;
+  const float thi = r * (Dhi * Dhi) * 1.00001f, tlo = r * (Dlo * Dlo) * 0.99999f;
+  if (I1 * (1.0f - 4e-6f) > thi || I2 * (1.0f - 4e-6f) > thi) return 1;
+  if (I1 * (1.0f + 4e-6f) < tlo && I2 * (1.0f + 4e-6f) < tlo) return 0;
+  return -1;
+}
+
 // Float constants of the filter.
 struct FiltConst {
   float eps, r;
@@ -228,19 +279,55 @@ __device__ __forceinline__ bool admit32(const float *hi, const float *lo, int st
   return first ? (v >= thr) : !(v < thr);
 }
 
-// Dispatch on a runtime p in 2..4 (lanes of one warp may hold different p).
+// psi~^2 admissibility of one component (FP64 state, then the compensated one).
+__device__ __forceinline__ bool admit64_2m(const double *q, int st, bool first, const FiltConst &F,
+                                           double eps, double thr, double fact) {
+  float d[3], e[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    d[k] = (float)__dsub_rn(q[k * st], q[(k - 1) * st]);
+    e[k] = 6.0e-8f * fabsf(d[k]) + 1e-44f;
+  }
+  const int dec = psi2m_filter(d, e, F.eps, F.r, F.fact[2]);
+  if (dec >= 0) return dec == 1;
+  const double v = psi2m_comp_g([=](int j) { return q[j * st]; }, eps, fact);
+  return first ? (v >= thr) : !(v < thr);
+}
+__device__ __forceinline__ bool admit32_2m(const float *hi, const float *lo, int st, bool first,
+                                           const FiltConst &F, double eps, double thr, double fact) {
+  float d[3], e[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float h1 = hi[k * st], h0 = hi[(k - 1) * st];
+    d[k] = (h1 - h0) + (lo[k * st] - lo[(k - 1) * st]);
+    e[k] = 1.2e-7f * fabsf(d[k]) + 1.5e-14f * (fabsf(h1) + fabsf(h0)) + 1e-44f;
+  }
+  const int dec = psi2m_filter(d, e, F.eps, F.r, F.fact[2]);
+  if (dec >= 0) return dec == 1;
+  const double v =
+      psi2m_comp_g([=](int j) { return (double)hi[j * st] + (double)lo[j * st]; }, eps, fact);
+  return first ? (v >= thr) : !(v < thr);
+}
+
+// Dispatch on a runtime p in 2..4 (lanes of one warp may hold different p);
+// psi2_mod selects psi~^2 for p = 2.
 __device__ __forceinline__ bool admit64_p(int p, const double *q, int st, bool first,
-                                          const FiltConst &F, double eps, double thr, double fact) {
+                                          const FiltConst &F, double eps, double thr, double fact,
+                                          int psi2_mod) {
   switch (p) {
-  case 2: return admit64<2>(q, st, first, F, eps, thr, fact);
+  case 2:
+    return psi2_mod ? admit64_2m(q, st, first, F, eps, thr, fact) : admit64<2>(q, st, first, F, eps, thr, fact);
   case 3: return admit64<3>(q, st, first, F, eps, thr, fact);
   default: return admit64<4>(q, st, first, F, eps, thr, fact);
   }
 }
 __device__ __forceinline__ bool admit32_p(int p, const float *hi, const float *lo, int st, bool first,
-                                          const FiltConst &F, double eps, double thr, double fact) {
+                                          const FiltConst &F, double eps, double thr, double fact,
+                                          int psi2_mod) {
   switch (p) {
-  case 2: return admit32<2>(hi, lo, st, first, F, eps, thr, fact);
+  case 2:
+    return psi2_mod ? admit32_2m(hi, lo, st, first, F, eps, thr, fact)
+                    : admit32<2>(hi, lo, st, first, F, eps, thr, fact);
   case 3: return admit32<3>(hi, lo, st, first, F, eps, thr, fact);
   default: return admit32<4>(hi, lo, st, first, F, eps, thr, fact);
   }

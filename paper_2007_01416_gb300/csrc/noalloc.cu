@@ -49,6 +49,8 @@ int validate(const acat_params *p) {
   if (!(p->x1 > p->x0)) return ACAT_ERR_INVALID_ARG;
   if (!(p->psi_tol >= 0.0 && p->psi_tol < 1.0)) return ACAT_ERR_INVALID_ARG;
   if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return ACAT_ERR_INVALID_ARG;
+  if (p->psi2_mod != 0 && p->psi2_mod != 1) return ACAT_ERR_INVALID_ARG;
+  if (p->lo_flux < ACAT_LO_RUSANOV || p->lo_flux > ACAT_LO_HLL) return ACAT_ERR_INVALID_ARG;
   if (p->flux == ACAT_FLUX_EULER1D && !(p->gamma > 1.0)) return ACAT_ERR_INVALID_ARG;
   if (p->ny != 1 || p->flux == ACAT_FLUX_EULER2D || p->precision != ACAT_PREC_F64)
     return ACAT_ERR_UNSUPPORTED;
@@ -99,6 +101,8 @@ extern "C" int acat_run_noalloc(const acat_params *p, void *u_dev, int nsteps, d
   a.N = p->nx;
   a.bc = p->bc;
   a.limiter_form = p->limiter_form;
+  a.psi2_mod = p->psi2_mod;
+  a.lo_flux = p->lo_flux;
   a.dx = (p->x1 - p->x0) / (double)p->nx;
   a.cfl = p->cfl;
   a.dt_fixed = -1.0;

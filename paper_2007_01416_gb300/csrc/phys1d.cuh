@@ -21,6 +21,8 @@ struct Phys<ACAT_FLUX_LINEAR> {
     ok = isfinite(u[0]);
     return fabs(a);
   }
+  template <typename R>
+  __device__ static __forceinline__ void eig(const R *, R a, R, R &lmin, R &lmax) { lmin = lmax = a; }
 };
 
 template <>
@@ -32,6 +34,8 @@ struct Phys<ACAT_FLUX_BURGERS> {
     ok = isfinite(u[0]);
     return fabs(u[0]);
   }
+  template <typename R>
+  __device__ static __forceinline__ void eig(const R *u, R, R, R &lmin, R &lmax) { lmin = lmax = u[0]; }
 };
 
 template <>
@@ -55,7 +59,38 @@ struct Phys<ACAT_FLUX_EULER1D> {
     ok = (u[0] > 0.0) && (p > 0.0) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
     return __dadd_rn(fabs(v), __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), u[0])));
   }
+  // smallest and largest eigenvalue v -/+ c (HLL wave-speed bounds)
+  template <typename R>
+  __device__ static __forceinline__ void eig(const R *u, R, R gamma, R &lmin, R &lmax) {
+    const R v = u[1] / u[0];
+    const R p = (gamma - R(1)) * (u[2] - R(0.5) * u[1] * v);
+    const R c = sqrt(gamma * p / u[0]);
+    lmin = v - c;
+    lmax = v + c;
+  }
 };
+
+// F^lo of Eq. 3.4 between the states u0 | u1 with fluxes f0, f1 (ACAT_LO_*):
+// Rusanov with the larger of the spectral radii s0, s1; global LF with
+// alpha = 1 / lambda (= dx / dt); HLL with the bounds min(n0, n1), max(x0, x1)
+// of the states' eigenvalues.
+template <int S, typename R>
+__device__ __forceinline__ void flux_lo(int lo_flux, const R *u0, const R *u1, const R *f0, const R *f1, R s0,
+                                        R s1, R n0, R x0, R n1, R x1, R lam, R *Flo) {
+  if (lo_flux == ACAT_LO_HLL) {
+    const R sl = n1 < n0 ? n1 : n0, sr = x1 > x0 ? x1 : x0;
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      if (sl >= R(0)) Flo[c] = f0[c];
+      else if (sr <= R(0)) Flo[c] = f1[c];
+      else Flo[c] = (sr * f0[c] - sl * f1[c] + sl * sr * (u1[c] - u0[c])) / (sr - sl);
+    }
+    return;
+  }
+  const R alpha = lo_flux == ACAT_LO_GLOBAL_LF ? R(1) / lam : (s1 > s0 ? s1 : s0);
+#pragma unroll
+  for (int c = 0; c < S; c++) Flo[c] = R(0.5) * (f0[c] + f1[c]) - R(0.5) * alpha * (u1[c] - u0[c]);
+}
 
 // psi^1 of a 1D interface (cells consecutive in the tile).
 template <int FLUX>
@@ -91,7 +126,7 @@ template <int P, int S, bool F32>
 __device__ __forceinline__ int select_order(const double *t0, const float *h0, const float *l0, int cs,
                                             int l, int grp, bool active, bool valid,
                                             const FiltConst &FC, double eps, double thr,
-                                            const double *fact) {
+                                            const double *fact, int psi2_mod) {
   using TL = Tiling<P>;
   if (P < 2) return 1;
   constexpr int NPAIR = (P - 1) * S;
@@ -101,9 +136,9 @@ __device__ __forceinline__ int select_order(const double *t0, const float *h0, c
       const int p = 2 + q / S, c = q - (q / S) * S;
       bool ok;
       if constexpr (F32)
-        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
+        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, 1, c == 0, FC, eps, thr, fact[p], psi2_mod);
       else
-        ok = admit64_p(p, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p]);
+        ok = admit64_p(p, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p], psi2_mod);
       if (!ok) rej |= 1u << (p - 2);
     }
   }

@@ -125,7 +125,8 @@ __device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R 
 // the limiter's ratios are spread over the group. Every lane returns F.
 template <int FLUX, int L>
 __device__ __forceinline__ void flcat2_flux(const double *q, int cs, int l, unsigned gmask, double lam,
-                                            double adv, double gamma, int limiter_form, double *F) {
+                                            double adv, double gamma, int limiter_form, int lo_flux,
+                                            double *F) {
   constexpr int S = Phys<FLUX>::S;
   const double gm1 = gamma - 1.0;
   const int me = l & 1;  // node i + me
@@ -154,14 +155,24 @@ __device__ __forceinline__ void flcat2_flux(const double *q, int cs, int l, unsi
     t0[c] = me ? o : t[c];
     t1[c] = me ? t[c] : o;
   }
-  const double alpha = s1 > s0 ? s1 : s0;
+  double n0 = 0.0, x0 = 0.0, n1 = 0.0, x1 = 0.0;
+  if (lo_flux == ACAT_LO_HLL) {
+    double n, x;
+    Phys<FLUX>::eig(u, adv, gamma, n, x);
+    const double no = __shfl_xor_sync(gmask, n, 1), xo = __shfl_xor_sync(gmask, x, 1);
+    n0 = me ? no : n;
+    x0 = me ? xo : x;
+    n1 = me ? n : no;
+    x1 = me ? x : xo;
+  }
+  double Flo[S];
+  flux_lo<S, double>(lo_flux, u0, u1, f0, f1, s0, s1, n0, x0, n1, x1, lam, Flo);
   const double w = psi1_group<S, L>([=](int c, int k) { return q[c * cs + k]; },
                                     FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, adv, l, gmask);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const double F1 = 0.5 * (f0[c] + f1[c]) + 0.25 * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
-    const double Flo = 0.5 * (f0[c] + f1[c]) - 0.5 * alpha * (u1[c] - u0[c]);
-    F[c] = w * F1 + (1.0 - w) * Flo;
+    F[c] = w * F1 + (1.0 - w) * Flo[c];
   }
 }
 
@@ -336,11 +347,12 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
 // the lanes, every lane returns G). With D1 = f(u_{i+1}) -
 // f(u_i), U = -lambda D1, T0 = df(u_i; U), T1 = df(u_i; u_{i+1} - u_i + U):
 //   CAT2:    F1 - f(u_i) = (T0 + T1 + D1) / 4
-//   Rusanov: Flo - f(u_i) = D1 / 2 - alpha (u_{i+1} - u_i) / 2
+//   Rusanov, global LF: Flo - f(u_i) = D1 / 2 - alpha (u_{i+1} - u_i) / 2
+//   HLL: 0 (s_l >= 0), D1 (s_r <= 0), s_l (s_r (u_{i+1} - u_i) - D1) / (s_r - s_l)
 template <int FLUX, int L>
 __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, int cs, int l, unsigned gmask,
                                              float lam, float adv, float gamma, double advd,
-                                             int limiter_form, float *G) {
+                                             int limiter_form, int lo_flux, float *G) {
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
   const float gm1 = gamma - 1.0f;
@@ -361,7 +373,15 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
   DP::dflux(b0, U, T0);
   DP::dflux(b0, d1, T1);
   const float s0 = DP::speed(u0, adv, gamma), s1 = DP::speed(u1, adv, gamma);
-  const float alpha = s1 > s0 ? s1 : s0;
+  const float alpha = lo_flux == ACAT_LO_GLOBAL_LF ? 1.0f / lam : (s1 > s0 ? s1 : s0);
+  float sl = 0.0f, sr = 0.0f;
+  if (lo_flux == ACAT_LO_HLL) {
+    float n0, x0, n1, x1;
+    Phys<FLUX>::eig(u0, adv, gamma, n0, x0);
+    Phys<FLUX>::eig(u1, adv, gamma, n1, x1);
+    sl = n1 < n0 ? n1 : n0;
+    sr = x1 > x0 ? x1 : x0;
+  }
   // scalar laws with the Roe-speed side: the side decision in FP64 on hi + lo;
   // systems (and the min form): float-float ratios
   const float w =
@@ -372,7 +392,11 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const float G1 = 0.25f * (T0[c] + T1[c] + D1[c]);
-    const float Glo = 0.5f * D1[c] - 0.5f * alpha * du[c];
+    float Glo;
+    if (lo_flux == ACAT_LO_HLL)
+      Glo = sl >= 0.0f ? 0.0f : (sr <= 0.0f ? D1[c] : sl * (sr * du[c] - D1[c]) / (sr - sl));
+    else
+      Glo = 0.5f * D1[c] - 0.5f * alpha * du[c];
     G[c] = fmaf(w, G1 - Glo, Glo);
   }
 }
@@ -497,7 +521,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
 
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int ps = select_order<P, S, false>(&sm.tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l,
-                                           grp, active, valid, FC, a.eps, a.thr, a.fact_tau);
+                                           grp, active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
 
   double F[S];
   const int base = grp * TL::L;
@@ -511,7 +535,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
       if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else {
       flcat2_flux<FLUX, TL::L>(q0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, a.adv, a.gamma,
-                               a.limiter_form, F);
+                               a.limiter_form, a.lo_flux, F);
     }
     if (l == 0) {
 #pragma unroll
@@ -579,7 +603,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int icv = valid ? ic : 0;
   const int ps = select_order<P, S, true>(nullptr, &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW, l, grp,
-                                          active, valid, FC, a.eps, a.thr, a.fact_tau);
+                                          active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
 
   float G[S];
   const int base = grp * TL::L;
@@ -593,7 +617,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
       if constexpr (P >= 2) if (l < 4) cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
     } else {
       flcat2_delta<FLUX, TL::L>(h0, l0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, adv, gam, a.adv,
-                                a.limiter_form, G);
+                                a.limiter_form, a.lo_flux, G);
     }
     if (l == 0) {
 #pragma unroll
@@ -711,7 +735,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
   const int ic = il - 1 + TL::GH;
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int ps = select_order<P, S, false>(&tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l, grp,
-                                           active, valid, FC, a.eps, a.thr, a.fact_tau);
+                                           active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
   if (active) {
     double F[S];
     const int base = grp * TL::L;
@@ -724,7 +748,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
       if constexpr (P >= 2) if (l < 4) cat_flux<2, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else {
       flcat2_flux<FLUX, TL::L>(q0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, a.adv, a.gamma,
-                               a.limiter_form, F);
+                               a.limiter_form, a.lo_flux, F);
     }
     if (l == 0) {
 #pragma unroll

@@ -49,6 +49,10 @@ struct Phys2<ACAT_FLUX_LINEAR> {
     sy = fabs(ay);
     ok = isfinite(u[0]);
   }
+  template <typename R>
+  __device__ static __forceinline__ void eig2(const R *, R ax, R ay, R, int dir, R &lmin, R &lmax) {
+    lmin = lmax = dir == 0 ? ax : ay;
+  }
   struct Base {
     float ax, ay;
   };
@@ -94,6 +98,16 @@ struct Phys2<ACAT_FLUX_EULER2D> {
     sy = __dadd_rn(fabs(w), c);
     ok = (u[0] > 0.0) && (p > 0.0) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) &&
          isfinite(u[3]);
+  }
+  // smallest and largest eigenvalue v_n -/+ c in direction dir (HLL bounds)
+  template <typename R>
+  __device__ static __forceinline__ void eig2(const R *u, R, R, R gamma, int dir, R &lmin, R &lmax) {
+    const R v = u[1] / u[0], w = u[2] / u[0];
+    const R p = (gamma - R(1)) * (u[3] - R(0.5) * (u[1] * v + u[2] * w));
+    const R c = sqrt(gamma * p / u[0]);
+    const R vn = dir == 0 ? v : w;
+    lmin = vn - c;
+    lmax = vn + c;
   }
   struct Base {
     float mx, my, v, w, H, rho, gm1;
@@ -329,13 +343,35 @@ __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int 
   }
 }
 
+// F^lo of Eq. 3.4 along one direction (ACAT_LO_*), as in 1D: Rusanov with the
+// larger spectral radius, global LF with alpha = 1 / lambda_dir, HLL with the
+// states' eigenvalue bounds.
+template <int S, typename R>
+__device__ __forceinline__ void flux_lo2(int lo_flux, const R *u0, const R *u1, const R *f0, const R *f1, R s0,
+                                         R s1, R n0, R x0, R n1, R x1, R lam, R *Flo) {
+  if (lo_flux == ACAT_LO_HLL) {
+    const R sl = n1 < n0 ? n1 : n0, sr = x1 > x0 ? x1 : x0;
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      if (sl >= R(0)) Flo[c] = f0[c];
+      else if (sr <= R(0)) Flo[c] = f1[c];
+      else Flo[c] = (sr * f0[c] - sl * f1[c] + sl * sr * (u1[c] - u0[c])) / (sr - sl);
+    }
+    return;
+  }
+  const R alpha = lo_flux == ACAT_LO_GLOBAL_LF ? R(1) / lam : (s1 > s0 ? s1 : s0);
+#pragma unroll
+  for (int c = 0; c < S; c++) Flo[c] = R(0.5) * (f0[c] + f1[c]) - R(0.5) * alpha * (u1[c] - u0[c]);
+}
+
 // FP64 FL-CAT2 in 2D (one lane): the 2D CAT2 fluxes of Eqs. 4.3-4.4 on the
 // 2 x 2 block at the anchor, blended with Rusanov by psi^1 of the row (F) or
 // the column (G) as in Eqs. 4.7-4.8.
 template <int FLUX>
 __device__ __forceinline__ void flcat2_2d_f64(const double *q, int cs, int rs, bool wantF, bool wantG,
                                               double lx, double ly, double ax, double ay,
-                                              double gamma, int limiter_form, double *F, double *G) {
+                                              double gamma, int limiter_form, int lo_flux, double *F,
+                                              double *G) {
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   const double gm1 = gamma - 1.0;
@@ -366,13 +402,18 @@ __device__ __forceinline__ void flcat2_2d_f64(const double *q, int cs, int rs, b
     bool ok;
     PH::speed2(u00, ax, ay, gamma, sx0, sy0, ok);
     PH::speed2(u10, ax, ay, gamma, sx1, sy1, ok);
-    const double alpha = sx1 > sx0 ? sx1 : sx0;
+    double n0 = 0.0, x0 = 0.0, n1 = 0.0, x1 = 0.0;
+    if (lo_flux == ACAT_LO_HLL) {
+      PH::eig2(u00, ax, ay, gamma, 0, n0, x0);
+      PH::eig2(u10, ax, ay, gamma, 0, n1, x1);
+    }
+    double Flo[S];
+    flux_lo2<S, double>(lo_flux, u00, u10, f00, f10, sx0, sx1, n0, x0, n1, x1, lx, Flo);
     const double w = psi1_line<S>(q, cs, 1, kind, limiter_form, ax);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const double F1 = 0.25 * (t0[c] + t1[c] + f00[c] + f10[c]);
-      const double Flo = 0.5 * (f00[c] + f10[c]) - 0.5 * alpha * (u10[c] - u00[c]);
-      F[c] = w * F1 + (1.0 - w) * Flo;
+      F[c] = w * F1 + (1.0 - w) * Flo[c];
     }
   }
   if (wantG) {
@@ -388,13 +429,18 @@ __device__ __forceinline__ void flcat2_2d_f64(const double *q, int cs, int rs, b
     bool ok;
     PH::speed2(u00, ax, ay, gamma, sx0, sy0, ok);
     PH::speed2(u01, ax, ay, gamma, sx1, sy1, ok);
-    const double alpha = sy1 > sy0 ? sy1 : sy0;
+    double n0 = 0.0, x0 = 0.0, n1 = 0.0, x1 = 0.0;
+    if (lo_flux == ACAT_LO_HLL) {
+      PH::eig2(u00, ax, ay, gamma, 1, n0, x0);
+      PH::eig2(u01, ax, ay, gamma, 1, n1, x1);
+    }
+    double Glo[S];
+    flux_lo2<S, double>(lo_flux, u00, u01, g00, g01, sy0, sy1, n0, x0, n1, x1, ly, Glo);
     const double w = psi1_line<S>(q, cs, rs, kind, limiter_form, ay);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const double G1 = 0.25 * (t0[c] + t1[c] + g00[c] + g01[c]);
-      const double Glo = 0.5 * (g00[c] + g01[c]) - 0.5 * alpha * (u01[c] - u00[c]);
-      G[c] = w * G1 + (1.0 - w) * Glo;
+      G[c] = w * G1 + (1.0 - w) * Glo[c];
     }
   }
 }
@@ -404,7 +450,7 @@ template <int FLUX>
 __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, int cs, int rs,
                                               bool wantF, bool wantG, float lx,
                                               float ly, float ax, float ay, float gamma, float gm1,
-                                              int limiter_form, float *GF, float *GG) {
+                                              int limiter_form, int lo_flux, float *GF, float *GG) {
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   const bool roe_linear = FLUX == ACAT_FLUX_LINEAR && limiter_form == 0;
@@ -435,13 +481,26 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
     for (int c = 0; c < S; c++) x1[c] = d10[c] + (-lx * Df10[c] - ly * (Dg11[c] - Dg10[c]));
     PH::dflux2(B, x1, ef, eg);  // f(u10 + U10) - f(u_a)
     const float s0 = PH::fspeed(ua, ax, ay, gamma, 0), s1 = PH::fspeed(u10, ax, ay, gamma, 0);
-    const float alpha = s1 > s0 ? s1 : s0;
+    const float alpha = lo_flux == ACAT_LO_GLOBAL_LF ? 1.0f / lx : (s1 > s0 ? s1 : s0);
+    float sl = 0.0f, sr = 0.0f;
+    if (lo_flux == ACAT_LO_HLL) {
+      float n0, x0, n1, x1;
+      PH::eig2(ua, ax, ay, gamma, 0, n0, x0);
+      PH::eig2(u10, ax, ay, gamma, 0, n1, x1);
+      sl = n1 < n0 ? n1 : n0;
+      sr = x1 > x0 ? x1 : x0;
+    }
     const float w = psi1_line_ff<S>(hi, lo, cs, 1, roe_linear, ax);
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      // F1 - f(a) = Df10/2 + (e00 + (ef - Df10))/4 ; Flo - f(a) = Df10/2 - alpha d10/2
+      // F1 - f(a) = Df10/2 + (e00 + (ef - Df10))/4 ; Flo - f(a) = Df10/2 - alpha d10/2 (LF
+      // forms), HLL: 0, Df10 or sl (sr d10 - Df10) / (sr - sl)
       const float G1 = 0.5f * Df10[c] + 0.25f * (e00f[c] + ef[c] - Df10[c]);
-      const float Glo = 0.5f * Df10[c] - 0.5f * alpha * d10[c];
+      float Glo;
+      if (lo_flux == ACAT_LO_HLL)
+        Glo = sl >= 0.0f ? 0.0f : (sr <= 0.0f ? Df10[c] : sl * (sr * d10[c] - Df10[c]) / (sr - sl));
+      else
+        Glo = 0.5f * Df10[c] - 0.5f * alpha * d10[c];
       GF[c] = fmaf(w, G1 - Glo, Glo);
     }
   }
@@ -451,12 +510,24 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
     for (int c = 0; c < S; c++) x1[c] = d01[c] + (-lx * (Df11[c] - Df01[c]) - ly * Dg01[c]);
     PH::dflux2(B, x1, ef, eg);  // g(u01 + U01) - g(u_a)
     const float s0 = PH::fspeed(ua, ax, ay, gamma, 1), s1 = PH::fspeed(u01, ax, ay, gamma, 1);
-    const float alpha = s1 > s0 ? s1 : s0;
+    const float alpha = lo_flux == ACAT_LO_GLOBAL_LF ? 1.0f / ly : (s1 > s0 ? s1 : s0);
+    float sl = 0.0f, sr = 0.0f;
+    if (lo_flux == ACAT_LO_HLL) {
+      float n0, x0, n1, x1;
+      PH::eig2(ua, ax, ay, gamma, 1, n0, x0);
+      PH::eig2(u01, ax, ay, gamma, 1, n1, x1);
+      sl = n1 < n0 ? n1 : n0;
+      sr = x1 > x0 ? x1 : x0;
+    }
     const float w = psi1_line_ff<S>(hi, lo, cs, rs, roe_linear, ay);
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const float G1 = 0.5f * Dg01[c] + 0.25f * (e00g[c] + eg[c] - Dg01[c]);
-      const float Glo = 0.5f * Dg01[c] - 0.5f * alpha * d01[c];
+      float Glo;
+      if (lo_flux == ACAT_LO_HLL)
+        Glo = sl >= 0.0f ? 0.0f : (sr <= 0.0f ? Dg01[c] : sl * (sr * d01[c] - Dg01[c]) / (sr - sl));
+      else
+        Glo = 0.5f * Dg01[c] - 0.5f * alpha * d01[c];
       GG[c] = fmaf(w, G1 - Glo, Glo);
     }
   }
@@ -566,9 +637,10 @@ __global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
         bool ok;
         if constexpr (F32)
           ok = admit32_p(p, &thi[c][ty][tx], &tlo[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps,
-                         a.thr, a.fact_tau[p]);
+                         a.thr, a.fact_tau[p], a.psi2_mod);
         else
-          ok = admit64_p(p, q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau[p]);
+          ok = admit64_p(p, q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau[p],
+                         a.psi2_mod);
         if (!ok) rej |= 1u << (dir * (P - 1) + (p - 2));
       }
       rej = __reduce_or_sync(gmask, rej);
@@ -597,10 +669,10 @@ __global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
       R F1[S], G1[S];
       if constexpr (F32) {
         flcat2_2d_f32<FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, flF, flG, s_lxf, s_lyf, a.advf[0],
-                            a.advf[1], a.gammaf, a.gm1f, a.limiter_form, F1, G1);
+                            a.advf[1], a.gammaf, a.gm1f, a.limiter_form, a.lo_flux, F1, G1);
       } else {
         flcat2_2d_f64<FLUX>(q64, CS, RS, flF, flG, lxd, lyd, a.adv[0], a.adv[1], a.gamma,
-                            a.limiter_form, F1, G1);
+                            a.limiter_form, a.lo_flux, F1, G1);
       }
 #pragma unroll
       for (int c = 0; c < S; c++) {

@@ -234,9 +234,9 @@ def order_hist(ctx, torch, u0, steps, nx, probes=5):
 
 
 def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_clocks, dev_index,
-            world=1):
+            world=1, extra=None):
     c = W.euler1d_riemann_entropy(nx=nx, seed=SEED, P=P, steps=acat_steps, cfl=CFL)
-    ctx = acat.Context(**c.problem_kwargs(), precision=prec)
+    ctx = acat.Context(**c.problem_kwargs(), precision=prec, **(extra or {}))
     host = acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()
     u0 = torch.from_numpy(host).cuda()
     u = torch.empty_like(u0)
@@ -567,6 +567,14 @@ def run_ours(args):
                     False, dev_index)
         vms = sum(v["ms"]) / 2
         variants["P2_f64"] = {
+            "value": cells_steps / (vms * 1e-3), "unit": UNIT, "ms_per_step": vms,
+            "roofline_frac": v["flops_per_step"] / (vms / args.acat_steps * 1e-3) / peak64,
+            "order_mix": v["order_mix"]}
+        # the switchable variants of FL-CAT2 and the p = 2 indicator: psi~^2 and HLL
+        v = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F64, args.acat_steps, 2, 1, flush,
+                    False, dev_index, extra={"psi2_mod": 1, "lo_flux": acat.LO_HLL})
+        vms = sum(v["ms"]) / 2
+        variants["P4_f64_psi2mod_hll"] = {
             "value": cells_steps / (vms * 1e-3), "unit": UNIT, "ms_per_step": vms,
             "roofline_frac": v["flops_per_step"] / (vms / args.acat_steps * 1e-3) / peak64,
             "order_mix": v["order_mix"]}

@@ -841,6 +841,274 @@ __global__ void __launch_bounds__(NT) k_smax2d(const Step2DArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// 2D step for P = 3, 4 (FP64). Blocks of 2p x 2p nodes exceed a warp for
+// p >= 3, so the block recursion (Eqs. 4.5-4.6) runs with one thread per node
+// and the F^(k), G^(k) of the nodes exchanged through shared memory. A CTA
+// owns TXH x TXH cells and their (TXH+1)^2 anchors:
+//   1. dt, staging of the cells with a halo of P;
+//   2. the order decisions of every (anchor, direction, p, component),
+//      spread over all threads (filtered / literal as in 1D);
+//   3. per anchor: the orders p_1 (row) and p_2 (column); a block task for
+//      p_1 = p_2 (serving F and G), else one task per direction with p >= 2
+//      (square blocks S_{p_1}, S_{p_2}); FL-CAT2 directions done in place;
+//   4. for p = 2..P, the tasks of that p in rounds that pack NT / (2p)^2
+//      blocks densely onto the threads, every round in lockstep;
+//   5. the conservative update (Eq. 4.9) and the wave speeds for the next dt.
+// ---------------------------------------------------------------------------
+constexpr int TXH = 12;        // cells per CTA side
+constexpr int NAH = TXH + 1;   // anchors per CTA side
+constexpr unsigned WANT_F = 1u << 8, WANT_G = 1u << 9;
+
+template <int P, int FLUX>
+struct Smem2H {
+  static constexpr int S = Phys2<FLUX>::S;
+  static constexpr int TW = TXH + 2 * P;
+  double tile[S][TW][TW];
+  double Fx[TXH][TXH + 1][S];
+  double Gy[TXH + 1][TXH][S];
+  double X[NT][S], Y[NT][S];  // F^(k), G^(k) of the nodes of a round
+  unsigned rej[NAH * NAH];    // rejected orders: bit dir * (P - 1) + (p - 2)
+  unsigned short task[P + 1][2 * NAH * NAH];
+  int ntask[P + 1];
+  double lx, ly;
+};
+
+// The block tasks of order p, NT / (2p)^2 per round (node (ia, ib) of task ti
+// on thread ti (2p)^2 + ib 2p + ia).
+template <int p, int P, int FLUX>
+__device__ __forceinline__ void block_tasks(Smem2H<P, FLUX> &sm, const Step2DArgs &a, double lx, double ly) {
+  using TB = Tab<double>;
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  constexpr int n = 2 * p, nn = n * n, per = NT / nn, z = p - 1;
+  const double gm1 = a.gamma - 1.0, axv = a.adv[0], ayv = a.adv[1];
+  const int nt = sm.ntask[p];
+  const int tid = threadIdx.x, ti = tid / nn, node = tid - ti * nn;
+  const int ia = node % n, ib = node / n;
+  double gx[n], gy[n];
+#pragma unroll
+  for (int r = 0; r < n; r++) {
+    gx[r] = TB::g1(p, ia, r);
+    gy[r] = TB::g1(p, ib, r);
+  }
+  for (int base = 0; base < nt; base += per) {
+    const bool act = ti < per && base + ti < nt;
+    const unsigned tk = act ? sm.task[p][base + ti] : 0u;
+    const int an = (int)(tk & 0xffu);
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    double u[S], f0[S], g0[S], Fs[S], Gs[S], arg[n][S];
+    if (act) {
+      const int tx = ax + P - p + 1 + ia, ty = ay + P - p + 1 + ib;
+#pragma unroll
+      for (int c = 0; c < S; c++) u[c] = sm.tile[c][ty][tx];
+      PH::flux2(u, f0, g0, axv, ayv, gm1);
+    } else {
+#pragma unroll
+      for (int c = 0; c < S; c++) u[c] = f0[c] = g0[c] = 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      Fs[c] = f0[c];
+      Gs[c] = g0[c];
+      sm.X[tid][c] = f0[c];
+      sm.Y[tid][c] = g0[c];
+    }
+#pragma unroll
+    for (int rr = 0; rr < n; rr++)
+#pragma unroll
+      for (int c = 0; c < S; c++) arg[rr][c] = u[c];
+#pragma unroll 1
+    for (int k = 2; k <= n; k++) {
+      __syncthreads();
+      double U[S];
+      if (act) {
+        double Ux[S], Uy[S];
+#pragma unroll
+        for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0;
+#pragma unroll
+        for (int r = 0; r < n; r++)
+#pragma unroll
+          for (int c = 0; c < S; c++) {
+            Ux[c] = fma(gx[r], sm.X[ti * nn + ib * n + r][c], Ux[c]);
+            Uy[c] = fma(gy[r], sm.Y[ti * nn + r * n + ia][c], Uy[c]);
+          }
+#pragma unroll
+        for (int c = 0; c < S; c++) U[c] = -(lx * Ux[c]) - ly * Uy[c];
+      }
+      __syncthreads();
+      if (act) {
+        double af[S], ag[S];
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          af[c] = TB::gk(p, k - 1, z) * f0[c];
+          ag[c] = TB::gk(p, k - 1, z) * g0[c];
+        }
+#pragma unroll
+        for (int rr = 0; rr < n; rr++) {
+          if (rr == z) continue;
+          const double cr = TB::taylor(p, rr, k - 1), wk = TB::gk(p, k - 1, rr);
+          double fr[S], gr[S];
+#pragma unroll
+          for (int c = 0; c < S; c++) arg[rr][c] = fma(cr, U[c], arg[rr][c]);
+          PH::flux2(arg[rr], fr, gr, axv, ayv, gm1);
+#pragma unroll
+          for (int c = 0; c < S; c++) {
+            af[c] = fma(wk, fr[c], af[c]);
+            ag[c] = fma(wk, gr[c], ag[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          sm.X[tid][c] = af[c];
+          sm.Y[tid][c] = ag[c];
+          Fs[c] = fma(TB::invfact(k), af[c], Fs[c]);
+          Gs[c] = fma(TB::invfact(k), ag[c], Gs[c]);
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if (ib == z) sm.X[tid][c] = TB::gh(p, ia) * Fs[c];
+        if (ia == z) sm.Y[tid][c] = TB::gh(p, ib) * Gs[c];
+      }
+    }
+    __syncthreads();
+    if (act && node == 0) {
+      if (tk & WANT_F)
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          double t = 0.0;
+#pragma unroll
+          for (int r = 0; r < n; r++) t += sm.X[ti * nn + z * n + r][c];
+          sm.Fx[ay][ax + 1][c] = t;
+        }
+      if (tk & WANT_G)
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          double t = 0.0;
+#pragma unroll
+          for (int r = 0; r < n; r++) t += sm.Y[ti * nn + r * n + z][c];
+          sm.Gy[ay + 1][ax][c] = t;
+        }
+    }
+    __syncthreads();
+  }
+}
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  constexpr int TW = Smem2H<P, FLUX>::TW;
+  constexpr int CELLS = TW * TW;
+  __shared__ Smem2H<P, FLUX> sm;
+  const int tid = threadIdx.x;
+  const long NXl = a.NX, NYl = a.NY;
+  const long x0 = (long)blockIdx.x * TXH, y0 = (long)blockIdx.y * TXH;
+  if (tid == 0) {
+    const double dt = step_dt2(a);
+    sm.lx = dt / a.dx;
+    sm.ly = dt / a.dy;
+  }
+  if (tid <= P) sm.ntask[tid] = 0;
+  for (int q = tid; q < NAH * NAH; q += NT) sm.rej[q] = 0u;
+  const double *uin = static_cast<const double *>(a.u_in);
+  for (int q = tid; q < S * CELLS; q += NT) {
+    const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW, xx = rem - yy * TW;
+    const long gx = bc2(x0 - P + xx, NXl, a.bc), gy = bc2(y0 - P + yy, NYl, a.bc);
+    sm.tile[c][yy][xx] = uin[((long)c * NYl + gy) * NXl + gx];
+  }
+  __syncthreads();
+  const double lx = sm.lx, ly = sm.ly;
+  // --- order decisions of every (anchor, direction, p, component) ----------
+  constexpr int NPAIR = 2 * (P - 1) * S;
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  for (int q = tid; q < NAH * NAH * NPAIR; q += NT) {
+    const int an = q / NPAIR, pr = q - an * NPAIR;
+    const int dir = pr / ((P - 1) * S), rem = pr - dir * (P - 1) * S;
+    const int p = 2 + rem / S, c = rem - (rem / S) * S;
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    const bool inside = x0 + ax < NXl && y0 + ay < NYl;
+    if (!inside || (dir == 0 ? ay < 0 : ax < 0)) continue;
+    const bool ok = admit64_p(p, &sm.tile[c][ay + P][ax + P], dir == 0 ? 1 : TW, c == 0, FC, a.eps, a.thr,
+                              a.fact_tau[p], a.psi2_mod);
+    if (!ok) atomicOr(&sm.rej[an], 1u << (dir * (P - 1) + (p - 2)));
+  }
+  __syncthreads();
+  // --- orders, block tasks, FL-CAT2 directions -----------------------------
+  for (int an = tid; an < NAH * NAH; an += NT) {
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    const long gxa = x0 + ax, gya = y0 + ay;
+    const bool inside = gxa < NXl && gya < NYl;
+    const bool needF = inside && ay >= 0, needG = inside && ax >= 0;
+    const unsigned rej = sm.rej[an], all = (1u << (P - 1)) - 1u;
+    const unsigned accx = ~rej & all, accy = ~(rej >> (P - 1)) & all;
+    const int px = accx ? (32 - __clz(accx)) + 1 : 1, py = accy ? (32 - __clz(accy)) + 1 : 1;
+    if (needF && a.ord_x && (ax >= 0 || gxa == -1)) a.ord_x[gya * (NXl + 1) + (gxa + 1)] = (int8_t)px;
+    if (needG && a.ord_y && (ay >= 0 || gya == -1)) a.ord_y[(gya + 1) * NXl + gxa] = (int8_t)py;
+    const bool bF = needF && px >= 2, bG = needG && py >= 2;
+    if (bF && bG && px == py) {
+      sm.task[px][atomicAdd(&sm.ntask[px], 1)] = (unsigned short)(an | WANT_F | WANT_G);
+    } else {
+      if (bF) sm.task[px][atomicAdd(&sm.ntask[px], 1)] = (unsigned short)(an | WANT_F);
+      if (bG) sm.task[py][atomicAdd(&sm.ntask[py], 1)] = (unsigned short)(an | WANT_G);
+    }
+    const bool flF = needF && px < 2, flG = needG && py < 2;
+    if (flF || flG) {
+      double F1[S], G1[S];
+      flcat2_2d_f64<FLUX>(&sm.tile[0][ay + P][ax + P], CELLS, TW, flF, flG, lx, ly, a.adv[0], a.adv[1],
+                          a.gamma, a.limiter_form, a.lo_flux, F1, G1);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if (flF) sm.Fx[ay][ax + 1][c] = F1[c];
+        if (flG) sm.Gy[ay + 1][ax][c] = G1[c];
+      }
+    }
+  }
+  __syncthreads();
+  // --- block recursions, one order at a time ------------------------------
+  block_tasks<2, P, FLUX>(sm, a, lx, ly);
+  if constexpr (P >= 3) block_tasks<3, P, FLUX>(sm, a, lx, ly);
+  if constexpr (P >= 4) block_tasks<4, P, FLUX>(sm, a, lx, ly);
+  // --- update and wave-speed epilogue (Eq. 4.9) ---------------------------
+  double mx = 0.0, my = 0.0;
+  bool bad = false;
+  double *uo = static_cast<double *>(a.u_out);
+  for (int t = tid; t < TXH * TXH; t += NT) {
+    const int cy = t / TXH, cx = t - cy * TXH;
+    const long gx = x0 + cx, gy = y0 + cy;
+    if (gx >= NXl || gy >= NYl) continue;
+    double un[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      un[c] = sm.tile[c][cy + P][cx + P] + lx * (sm.Fx[cy][cx][c] - sm.Fx[cy][cx + 1][c]) +
+              ly * (sm.Gy[cy][cx][c] - sm.Gy[cy + 1][cx][c]);
+      uo[((long)c * NYl + gy) * NXl + gx] = un[c];
+    }
+    double sx, sy;
+    bool ok;
+    PH::speed2(un, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
+    bad |= !ok;
+    mx = fmax(mx, sx);
+    my = fmax(my, sy);
+  }
+  const int lane = tid & 31;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  if (lane == 0) {
+    const int zs = (a.slot + 1) % 3;
+    atomic_max_pos(&a.smax[zs * 2 + 0], mx);
+    atomic_max_pos(&a.smax[zs * 2 + 1], my);
+  }
+}
+
 template <int P, int FLUX, bool F32>
 int launch2(const Step2DArgs &a, cudaStream_t st) {
   dim3 grid((unsigned)((a.NX + TXY - 1) / TXY), (unsigned)((a.NY + TXY - 1) / TXY));
@@ -848,10 +1116,21 @@ int launch2(const Step2DArgs &a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+template <int P, int FLUX>
+int launch2_hi(const Step2DArgs &a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.NX + TXH - 1) / TXH), (unsigned)((a.NY + TXH - 1) / TXH));
+  k_step2d_hi<P, FLUX><<<grid, NT, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
 template <int FLUX, bool F32>
 int launch2_p(int P, const Step2DArgs &a, cudaStream_t st) {
   if (P == 1) return launch2<1, FLUX, F32>(a, st);
   if (P == 2) return launch2<2, FLUX, F32>(a, st);
+  if constexpr (!F32) {
+    if (P == 3) return launch2_hi<3, FLUX>(a, st);
+    if (P == 4) return launch2_hi<4, FLUX>(a, st);
+  }
   return (int)cudaErrorInvalidValue;
 }
 

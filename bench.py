@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "batch_f32", "adjoint", "adjoint_f32"],
+                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "batch_f32", "adjoint", "adjoint_f32"],
                     help="profiling runs: one short measurement of a single workload")
     return ap.parse_args()
 
@@ -315,6 +315,50 @@ def measure_2d(torch, acat, W, flops, n, prec, steps, K, flush, peak):
             "n": n, "roofline_frac": fl / (t / steps * 1e-3) / peak,
             "anchors_with_block": round(blk / (n * n), 4),
             "flcat2_directions": round(flc / (2 * n * (n + 1)), 4)}
+
+
+def measure_2d_hi(torch, acat, W, flops, n, P, steps, K, flush, peak):
+    """2D Euler P = 3, 4 (FP64) on smooth data with a contact (the high-order
+    2D step), n x n periodic, CFL 0.4."""
+    import numpy as np
+    c = W.euler2d_smooth(n=n, seed=SEED, P=P, steps=steps)
+    ctx = acat.Context(**c.problem_kwargs())
+    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    u.copy_(u0)
+    ctx.acat_run(u, 3)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        e0.record(stream)
+        ctx.acat_run(u, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    assert ctx.acat_status() == 0
+    orders = torch.zeros(n * (n + 1) * 2, dtype=torch.int8, device="cuda")
+    tmp = torch.empty_like(u)
+    ctx.acat_step(u, tmp, -1.0, None, None, orders)
+    torch.cuda.synchronize()
+    o = orders.cpu().numpy().astype(np.int64)
+    pF = o[:n * (n + 1)].reshape(n, n + 1)[:, 1:]
+    pG = o[n * (n + 1):].reshape(n + 1, n)[1:, :]
+    same = (pF == pG) & (pF >= 2)
+    blocks = {}
+    for p in range(2, P + 1):
+        blocks[p] = int((same & (pF == p)).sum() + (~same & (pF == p)).sum() + (~same & (pG == p)).sum())
+    flc = int((pF == 1).sum() + (pG == 1).sum())
+    fl = flops.step_flops_2d_tasks(blocks, flc, n * n, P, W.EULER2D, n * n)
+    t = min(ms)
+    ctx.close()
+    return {"value": n * n * steps / (t * 1e-3), "unit": UNIT, "ms_per_run": t, "steps": steps, "n": n,
+            "P": P, "roofline_frac": fl / (t / steps * 1e-3) / peak, "roofline_peak": "fp64",
+            "blocks_per_anchor": {str(p): round(blocks[p] / (n * n), 4) for p in blocks},
+            "flcat2_directions": round(flc / (2 * n * n), 4)}
 
 
 def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
@@ -610,6 +654,9 @@ def run_ours(args):
         v32["speedup_vs_f64_per_cell_update"] = v32["value"] / v64["value"]
         variants["2d_euler_P2_4096_f32"] = v32
         variants["2d_euler_P2_1024_f64"] = v64
+        # the high-order 2D step (square blocks, P = 3)
+        variants["2d_euler_P3_smooth_1024_f64"] = measure_2d_hi(torch, acat, W, flops, 1024, 3, 10, 2, flush,
+                                                                peak64)
         # batched: 4096 ragged instances (P = 3), 1000 steps in FP32, and 10 steps of
         # the plain FP64 step for the ratio
         b32 = measure_batch(torch, acat, W, flops, acat.PREC_F32, 1000, 1, flush, peak32)
@@ -677,6 +724,8 @@ def run_single(args):
     if args.workload == "f32_1d":
         m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F32, n, 1, 1, flush, False, 0)
         out = {"ms": m["ms"]}
+    elif args.workload == "2d_p3":
+        out = measure_2d_hi(torch, acat, W, flops, 1024, 3, n, 1, flush, 1.0)
     elif args.workload in ("2d_f32", "2d_f64"):
         f32 = args.workload == "2d_f32"
         out = measure_2d(torch, acat, W, flops, 4096 if f32 else 1024,

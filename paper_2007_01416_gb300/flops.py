@@ -86,3 +86,12 @@ def state_bytes_1d(cells: int, flux: int, prec: int = 0) -> int:
     """Compulsory HBM traffic of one step: read and write the state once
     (FP64, or the FP32 hi/lo pair: 8 bytes per value either way)."""
     return 2 * cells * NVARS[flux] * 8
+
+
+def step_flops_2d_tasks(blocks_by_p: dict, flcat: int, anchors: int, P: int, flux: int, cells: int) -> float:
+    """As step_flops_2d with the block recursions counted per order p
+    (blocks_by_p maps p to the number of 2p x 2p block recursions run)."""
+    S = NVARS[flux]
+    ind = 2 * sum(S * (6 * (p - 1) + 2 + 3 + 4 * p + 2 + 2) for p in range(2, P + 1))
+    return sum(cnt * cat2d_flops(p, flux) for p, cnt in blocks_by_p.items()) \
+        + flcat * flcat2_2d_flops(flux) + anchors * ind + cells * (5 * S + 14)

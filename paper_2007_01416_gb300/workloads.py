@@ -112,6 +112,26 @@ def euler2d_quadrants(n: int = 4096, seed: int = 0, P: int = 2, steps: int = 500
     return _quadrants(f"euler2d_quadrants", st, n, ny, P, steps, cfl)
 
 
+def euler2d_smooth(n: int = 1024, seed: int = 0, P: int = 3, steps: int = 10, cfl: float = 0.4,
+                   ny: int | None = None) -> Case:
+    """Smooth 2D Euler data with a contact, periodic on [0,1]^2, for the
+    high-order (P >= 3) 2D step: rho = 1 + a sin(2 pi x) sin(2 pi y) +
+    0.3 [x > x_c], u = 0.3 + 0.1 cos(2 pi y), v = -0.2 + 0.1 sin(2 pi x),
+    p = 1 + 0.1 cos(2 pi (x + y) + phi); a in [0.1, 0.3], x_c in [0.4, 0.7],
+    phi in [0, 2 pi) seeded."""
+    rng = np.random.default_rng(seed)
+    a, xc, phi = rng.uniform(0.1, 0.3), rng.uniform(0.4, 0.7), rng.uniform(0.0, 2.0 * math.pi)
+    ny = n if ny is None else ny
+    x = centres(n, 0.0, 1.0)[None, :]
+    y = centres(ny, 0.0, 1.0)[:, None]
+    rho = 1.0 + a * np.sin(2 * math.pi * x) * np.sin(2 * math.pi * y) + 0.3 * (x + 0 * y > xc)
+    u = 0.3 + 0.1 * np.cos(2 * math.pi * y) + 0 * x
+    v = -0.2 + 0.1 * np.sin(2 * math.pi * x) + 0 * y
+    p = 1.0 + 0.1 * np.cos(2 * math.pi * (x + y) + phi)
+    return Case("euler2d_smooth", EULER2D, P, n, ny, PERIODIC, cfl, 0.0, 1.0, 0.0, 1.0,
+                prim_to_cons_2d(rho, u, v, p), steps)
+
+
 def _quadrants(name, st, nx, ny, P, steps, cfl) -> Case:
     x = centres(nx, 0.0, 1.0)[None, :]
     y = centres(ny, 0.0, 1.0)[:, None]

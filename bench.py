@@ -138,7 +138,7 @@ def barrier_sync(world: int, cuda: bool = True):
         torch.cuda.synchronize()
 
 
-def cpu_baseline(budget_s: float = 12.0, max_steps: int = 200) -> dict:
+def cpu_baseline(budget_s: float = 12.0, max_steps: int = 4000) -> dict:
     """The CPU oracle as it stands, on a bounded sample of the workload:
     consecutive oracle steps from the seeded initial state."""
     import oracle as O

@@ -41,6 +41,32 @@ __device__ __forceinline__ float recip(float x) {
   return y;
 }
 
+// Packed pairs of floats (sm_100+ f32x2 instructions: one issue slot for two
+// lanes' worth of add, multiply or fused multiply-add, each rounded to
+// nearest exactly as the scalar instruction).
+__device__ __forceinline__ unsigned long long f2bits(float2 a) {
+  return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ float2 f2from(unsigned long long b) {
+  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)));
+  return f2from(d);
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)));
+  return f2from(d);
+}
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)), "l"(f2bits(c)));
+  return f2from(d);
+}
+__device__ __forceinline__ float2 f2dup(float a) { return make_float2(a, a); }
+
 // fused multiply-add in the arithmetic type of its arguments
 __device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }

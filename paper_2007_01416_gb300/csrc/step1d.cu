@@ -205,6 +205,10 @@ struct DPhys<ACAT_FLUX_LINEAR> {
   __device__ static __forceinline__ void dflux(const Base &b, const float *d, float *df) {
     df[0] = b.a * d[0];
   }
+  // two increments at once, packed in the lanes of float2 values
+  __device__ static __forceinline__ void dflux_x2(const Base &b, const float2 *d, float2 *df) {
+    df[0] = f2mul(f2dup(b.a), d[0]);
+  }
   __device__ static __forceinline__ float speed(const float *, float a, float) { return fabsf(a); }
   __device__ static __forceinline__ bool physical(const float *u, float) { return isfinite(u[0]); }
 };
@@ -219,6 +223,9 @@ struct DPhys<ACAT_FLUX_BURGERS> {
   // (u + d)^2/2 - u^2/2 = d (u + d/2)
   __device__ static __forceinline__ void dflux(const Base &b, const float *d, float *df) {
     df[0] = d[0] * fmaf(0.5f, d[0], b.u);
+  }
+  __device__ static __forceinline__ void dflux_x2(const Base &b, const float2 *d, float2 *df) {
+    df[0] = f2mul(d[0], f2fma(f2dup(0.5f), d[0], f2dup(b.u)));
   }
   __device__ static __forceinline__ float speed(const float *u, float, float) { return fabsf(u[0]); }
   __device__ static __forceinline__ bool physical(const float *u, float) { return isfinite(u[0]); }
@@ -254,6 +261,18 @@ struct DPhys<ACAT_FLUX_EULER1D> {
     df[1] = dmv + dp;
     df[2] = fmaf(dv, B.H, vn * (d[2] + dp));
   }
+  // the same for two increments packed in float2 lanes
+  __device__ static __forceinline__ void dflux_x2(const Base &B, const float2 *d, float2 *df) {
+    const float2 t = f2fma(f2dup(-B.v), d[0], d[1]);
+    const float2 den = f2add(f2dup(B.rho), d[0]);
+    const float2 dv = f2mul(t, make_float2(__frcp_rn(den.x), __frcp_rn(den.y)));
+    const float2 vn = f2add(f2dup(B.v), dv);
+    const float2 dmv = f2fma(f2dup(B.m), dv, f2mul(d[1], vn));
+    const float2 dp = f2mul(f2dup(B.gm1), f2fma(f2dup(-0.5f), dmv, d[2]));
+    df[0] = d[1];
+    df[1] = f2add(dmv, dp);
+    df[2] = f2fma(dv, f2dup(B.H), f2mul(vn, f2add(d[2], dp)));
+  }
   __device__ static __forceinline__ float speed(const float *u, float, float gamma) {
     const float v = u[1] / u[0];
     const float p = (gamma - 1.0f) * (u[2] - 0.5f * u[1] * v);
@@ -287,7 +306,12 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
     uj[c] = hi[c * cs + j];
     d0[c] = (hi[c * cs + j] - hi[c * cs]) + (lo[c * cs + j] - lo[c * cs]);
   }
-  float D[S], Fsum[S], Fprev[S], del[n][S];
+  // the 2p - 1 time levels r != 0 (level q <-> table row q < p - 1 ? q : q + 1)
+  // are worked in pairs packed in float2 lanes (p <= 3; at p = 4 the pairs
+  // would cost the registers of a fourth resident CTA), the last one alone
+  constexpr int NL = n - 1, NP = p <= 3 ? NL / 2 : 0;
+  float D[S], Fsum[S], Fprev[S], dels[NL - 2 * NP][S];
+  float2 del2[NP > 0 ? NP : 1][S];
   DP::dflux(DP::base(ui, adv, gm1), d0, D);  // f(u_j) - f(u_i)
   const typename DP::Base bj = DP::base(uj, adv, gm1);
 #pragma unroll
@@ -296,9 +320,13 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
     Fprev[c] = D[c];
   }
 #pragma unroll
-  for (int rr = 0; rr < n; rr++)
+  for (int q = 0; q < NL - 2 * NP; q++)
 #pragma unroll
-    for (int c = 0; c < S; c++) del[rr][c] = 0.0f;
+    for (int c = 0; c < S; c++) dels[q][c] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < NP; q++)
+#pragma unroll
+    for (int c = 0; c < S; c++) del2[q][c] = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int k = 2; k <= n; k++) {
     float U[S];
@@ -309,24 +337,38 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
 #pragma unroll
       for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
     float acc[S];
+    float2 acc2[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
       U[c] *= -lam;
       acc[c] = 0.0f;
+      acc2[c] = make_float2(0.0f, 0.0f);
     }
 #pragma unroll
-    for (int rr = 0; rr < n; rr++) {
-      if (rr == p - 1) continue;  // r = 0: no increment
-      const float cr = TB::taylor(p, rr, k - 1);
+    for (int q = 0; q < NP; q++) {
+      const int ra = 2 * q < p - 1 ? 2 * q : 2 * q + 1, rb = 2 * q + 1 < p - 1 ? 2 * q + 1 : 2 * q + 2;
+      const float2 cr = make_float2(TB::taylor(p, ra, k - 1), TB::taylor(p, rb, k - 1));
+      const float2 wk = make_float2(TB::gk(p, k - 1, ra), TB::gk(p, k - 1, rb));
+      float2 E2[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) del2[q][c] = f2fma(cr, f2dup(U[c]), del2[q][c]);
+      DP::dflux_x2(bj, del2[q], E2);
+#pragma unroll
+      for (int c = 0; c < S; c++) acc2[c] = f2fma(wk, E2[c], acc2[c]);
+    }
+#pragma unroll
+    for (int q = 2 * NP; q < NL; q++) {  // levels not paired
+      const int rs = q < p - 1 ? q : q + 1;
       float E[S];
 #pragma unroll
-      for (int c = 0; c < S; c++) del[rr][c] = fmaf(cr, U[c], del[rr][c]);
-      DP::dflux(bj, del[rr], E);
+      for (int c = 0; c < S; c++) dels[q - 2 * NP][c] = fmaf(TB::taylor(p, rs, k - 1), U[c], dels[q - 2 * NP][c]);
+      DP::dflux(bj, dels[q - 2 * NP], E);
 #pragma unroll
-      for (int c = 0; c < S; c++) acc[c] = fmaf(TB::gk(p, k - 1, rr), E[c], acc[c]);
+      for (int c = 0; c < S; c++) acc[c] = fmaf(TB::gk(p, k - 1, rs), E[c], acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < S; c++) {
+      acc[c] += acc2[c].x + acc2[c].y;
       Fprev[c] = acc[c];
       Fsum[c] = fmaf(TB::invfact(k), acc[c], Fsum[c]);
     }

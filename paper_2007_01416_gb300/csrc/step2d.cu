@@ -63,6 +63,10 @@ struct Phys2<ACAT_FLUX_LINEAR> {
     df[0] = B.ax * d[0];
     dg[0] = B.ay * d[0];
   }
+  __device__ static __forceinline__ void dflux2_x2(const Base &B, const float2 *d, float2 *df, float2 *dg) {
+    df[0] = f2mul(f2dup(B.ax), d[0]);
+    dg[0] = f2mul(f2dup(B.ay), d[0]);
+  }
   __device__ static __forceinline__ float fspeed(const float *, float ax, float ay, float, int dir) {
     return dir == 0 ? fabsf(ax) : fabsf(ay);
   }
@@ -145,6 +149,25 @@ struct Phys2<ACAT_FLUX_EULER2D> {
     dg[1] = dxy;
     dg[2] = dmw + dp;
     dg[3] = fmaf(dw, B.H, wn * dH);
+  }
+  // the same for two increments packed in float2 lanes
+  __device__ static __forceinline__ void dflux2_x2(const Base &B, const float2 *d, float2 *df, float2 *dg) {
+    const float2 den = f2add(f2dup(B.rho), d[0]);
+    const float2 ri = make_float2(recip(den.x), recip(den.y));
+    const float2 dv = f2mul(f2fma(f2dup(-B.v), d[0], d[1]), ri), dw = f2mul(f2fma(f2dup(-B.w), d[0], d[2]), ri);
+    const float2 vn = f2add(f2dup(B.v), dv), wn = f2add(f2dup(B.w), dw);
+    const float2 dmv = f2fma(f2dup(B.mx), dv, f2mul(d[1], vn)), dmw = f2fma(f2dup(B.my), dw, f2mul(d[2], wn));
+    const float2 dxy = f2fma(f2dup(B.mx), dw, f2mul(d[1], wn));
+    const float2 dp = f2mul(f2dup(B.gm1), f2fma(f2dup(-0.5f), f2add(dmv, dmw), d[3]));
+    const float2 dH = f2add(d[3], dp);
+    df[0] = d[1];
+    df[1] = f2add(dmv, dp);
+    df[2] = dxy;
+    df[3] = f2fma(dv, f2dup(B.H), f2mul(vn, dH));
+    dg[0] = d[2];
+    dg[1] = dxy;
+    dg[2] = f2add(dmw, dp);
+    dg[3] = f2fma(dw, f2dup(B.H), f2mul(wn, dH));
   }
   __device__ static __forceinline__ float fspeed(const float *u, float, float, float gamma, int dir) {
     const float v = u[1] / u[0], w = u[2] / u[0];
@@ -279,16 +302,20 @@ __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int 
   float Df[S], Dg[S];
   PH::dflux2(PH::base(ua, ax, ay, gm1), d0, Df, Dg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
   const typename PH::Base bj = PH::base(uj, ax, ay, gm1);
-  float Ff[S], Fg[S], Pf[S], Pg[S], del[n][S];
+  // the 2p - 1 levels r != 0 in pairs packed in float2 lanes, the last alone
+  constexpr int NL = n - 1, NP = NL / 2;
+  float Ff[S], Fg[S], Pf[S], Pg[S], dels[S];
+  float2 del2[NP][S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     Ff[c] = Pf[c] = Df[c];
     Fg[c] = Pg[c] = Dg[c];
+    dels[c] = 0.0f;
   }
 #pragma unroll
-  for (int rr = 0; rr < n; rr++)
+  for (int q = 0; q < NP; q++)
 #pragma unroll
-    for (int c = 0; c < S; c++) del[rr][c] = 0.0f;
+    for (int c = 0; c < S; c++) del2[q][c] = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int k = 2; k <= n; k++) {
     float Ux[S], Uy[S];
@@ -307,14 +334,31 @@ __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int 
       U[c] = -(lx * Ux[c]) - ly * Uy[c];
       af[c] = ag[c] = 0.0f;
     }
+    float2 af2[S], ag2[S];
 #pragma unroll
-    for (int rr = 0; rr < n; rr++) {
-      if (rr == p - 1) continue;
-      const float cr = TB::taylor(p, rr, k - 1), wk = TB::gk(p, k - 1, rr);
+    for (int c = 0; c < S; c++) af2[c] = ag2[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < NP; q++) {
+      const int ra = 2 * q < p - 1 ? 2 * q : 2 * q + 1, rb = 2 * q + 1 < p - 1 ? 2 * q + 1 : 2 * q + 2;
+      const float2 cr = make_float2(TB::taylor(p, ra, k - 1), TB::taylor(p, rb, k - 1));
+      const float2 wk = make_float2(TB::gk(p, k - 1, ra), TB::gk(p, k - 1, rb));
+      float2 ef[S], eg[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) del2[q][c] = f2fma(cr, f2dup(U[c]), del2[q][c]);
+      PH::dflux2_x2(bj, del2[q], ef, eg);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        af2[c] = f2fma(wk, ef[c], af2[c]);
+        ag2[c] = f2fma(wk, eg[c], ag2[c]);
+      }
+    }
+    {
+      constexpr int rs = NL - 1 < p - 1 ? NL - 1 : NL;  // the last level
+      const float cr = TB::taylor(p, rs, k - 1), wk = TB::gk(p, k - 1, rs);
       float ef[S], eg[S];
 #pragma unroll
-      for (int c = 0; c < S; c++) del[rr][c] = fmaf(cr, U[c], del[rr][c]);
-      PH::dflux2(bj, del[rr], ef, eg);
+      for (int c = 0; c < S; c++) dels[c] = fmaf(cr, U[c], dels[c]);
+      PH::dflux2(bj, dels, ef, eg);
 #pragma unroll
       for (int c = 0; c < S; c++) {
         af[c] = fmaf(wk, ef[c], af[c]);
@@ -323,6 +367,8 @@ __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int 
     }
 #pragma unroll
     for (int c = 0; c < S; c++) {
+      af[c] += af2[c].x + af2[c].y;
+      ag[c] += ag2[c].x + ag2[c].y;
       Pf[c] = af[c];
       Pg[c] = ag[c];
       Ff[c] = fmaf(TB::invfact(k), af[c], Ff[c]);

@@ -47,6 +47,8 @@ def parse():
                     help="ACAT steps per benchmark step (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--shape", default="",
+                    help="launch shape 'nw,lpn,cps' for the f32_1d and batch_f32 profiling workloads")
     ap.add_argument("--workload", default="main",
                     choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "batch_f32", "adjoint", "adjoint_f32"],
                     help="profiling runs: one short measurement of a single workload")
@@ -191,7 +193,7 @@ def run_reference(args):
 
 
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2007_01416_gb300", "csrc", f)
-                  for f in ("step1d.cu", "phys1d.cuh", "device_common.cuh")]
+                  for f in ("step1d.cu", "step1d_core.cuh", "phys1d.cuh", "device_common.cuh")]
 
 
 def sources_sha(paths) -> str:
@@ -234,13 +236,19 @@ def order_hist(ctx, torch, u0, steps, nx, probes=5):
 
 
 def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_clocks, dev_index,
-            world=1, extra=None):
+            world=1, extra=None, shape=None):
+    """shape: None (default launch shape), "auto" (the library's autotuner,
+    timed on a copy of the state before the warm-up) or (nw, lpn, cps)."""
     c = W.euler1d_riemann_entropy(nx=nx, seed=SEED, P=P, steps=acat_steps, cfl=CFL)
     ctx = acat.Context(**c.problem_kwargs(), precision=prec, **(extra or {}))
     host = acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()
     u0 = torch.from_numpy(host).cuda()
     u = torch.empty_like(u0)
     stream = torch.cuda.current_stream()
+    if shape == "auto":
+        ctx.acat_autotune(u0, 96)
+    elif shape is not None:
+        ctx.acat_set_launch_shape(*shape)
 
     def one():
         u.copy_(u0)
@@ -270,9 +278,11 @@ def measure(torch, acat, W, flops, nx, P, prec, acat_steps, K, Wm, flush, want_c
     hists = order_hist(ctx, torch, u0, acat_steps, nx)
     avg = [sum(h[k] for h in hists) / len(hists) for k in range(5)]
     fl = flops.step_flops_1d({k: avg[k] for k in range(1, 5)}, P, W.EULER1D, nx)
+    nw, lpn, cps = ctx.acat_launch_shape()
     res = dict(ms=ms, launches=launches, clocks=clk, flops_per_step=fl,
                order_mix={str(k): round(avg[k] / (nx + 1), 4) for k in range(1, 5)},
-               ctx=ctx, case=c, u0=u0)
+               ctx=ctx, case=c, u0=u0,
+               launch_shape={"warps_per_cta": nw, "lanes_per_node": lpn, "autotuned": shape == "auto"})
     return res
 
 
@@ -361,7 +371,7 @@ def measure_2d_hi(torch, acat, W, flops, n, P, steps, K, flush, peak):
             "flcat2_directions": round(flc / (2 * n * n), 4)}
 
 
-def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
+def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak, shape=None):
     """4096 independent 1D Euler instances, N uniform in [256, 16384], P = 3,
     one persistent launch per step."""
     import numpy as np
@@ -372,6 +382,13 @@ def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
     u0 = torch.from_numpy(acat.to_pair(u) if prec == acat.PREC_F32 else u).cuda()
     v = torch.empty_like(u0)
     stream = torch.cuda.current_stream()
+    # launch shape (tile width, CTAs per SM) from the library's autotuner,
+    # timed on a copy of the state before the measured runs
+    if shape is None:
+        nw, lpn, cps = ctx.acat_autotune(u0, 6)
+    else:
+        ctx.acat_set_launch_shape(*shape)
+        nw, lpn, cps = ctx.acat_launch_shape()
     v.copy_(u0)
     ctx.acat_run(v, 6)
     torch.cuda.synchronize()
@@ -397,6 +414,8 @@ def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak):
     ctx.close()
     return {"value": M * steps / (t * 1e-3), "unit": UNIT, "ms_per_run": t, "steps": steps,
             "instances": len(sizes), "cells": M, "roofline_frac": fl / (t / steps * 1e-3) / peak,
+            "launch_shape": {"warps_per_cta": nw, "lanes_per_node": lpn, "ctas_per_sm": cps,
+                             "autotuned": shape is None},
             "order_mix": {str(k): round(h[k] / (M + len(sizes)), 4) for k in range(1, 5)}}
 
 
@@ -624,7 +643,7 @@ def run_ours(args):
             "order_mix": v["order_mix"]}
         for P in (4, 2):
             v = measure(torch, acat, W, flops, NX, P, acat.PREC_F32, args.acat_steps, 3, 1, flush,
-                        False, dev_index)
+                        False, dev_index, shape="auto")
             vms = sum(v["ms"]) / 3
             # accuracy of the FP32 run against the FP64 run of the same workload
             # (the FP64 path matches the oracle within 1e-12 per step)
@@ -643,7 +662,7 @@ def run_ours(args):
                 / vms,
                 "l1_rel_vs_f64": float(diff.mean() / u64.abs().mean()),
                 "linf_rel_vs_f64": float(diff.max() / u64.abs().max()),
-                "order_mix": v["order_mix"]}
+                "launch_shape": v["launch_shape"], "order_mix": v["order_mix"]}
             c64.close()
         # 2D Euler, P = 2: 4096^2 x 500 steps in FP32 (the 2D configuration), and the
         # plain FP64 step at 1024^2 x 20 steps for the FP32 / FP64 ratio
@@ -721,8 +740,9 @@ def run_single(args):
     B.build()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     n = args.acat_steps
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
     if args.workload == "f32_1d":
-        m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F32, n, 1, 1, flush, False, 0)
+        m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F32, n, 1, 1, flush, False, 0, shape=shape)
         out = {"ms": m["ms"]}
     elif args.workload == "2d_p3":
         out = measure_2d_hi(torch, acat, W, flops, 1024, 3, n, 1, flush, 1.0)
@@ -734,7 +754,7 @@ def run_single(args):
         out = measure_adjoint(torch, acat, W, 1, flush, steps=n,
                               prec=acat.PREC_F32 if args.workload == "adjoint_f32" else acat.PREC_F64)
     else:
-        out = measure_batch(torch, acat, W, flops, acat.PREC_F32, n, 1, flush, 1.0)
+        out = measure_batch(torch, acat, W, flops, acat.PREC_F32, n, 1, flush, 1.0, shape=shape or (8, 1, 0))
     print(json.dumps({"workload": args.workload, **{k: v for k, v in out.items()
                                                      if isinstance(v, (int, float, list))}}))
     return 0

@@ -135,6 +135,50 @@ int acat_create(const acat_params *p, acat_ctx **out);
  * INVALID_ARG for a 2D problem or a too small instance. */
 int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_inst, acat_ctx **out);
 
+/* Launch shape of a 1D context's step kernel: warps per CTA (nw), lanes per
+ * stencil node (lpn) and CTAs per SM (cps).
+ *   - An interface is worked by a group of 2P x lpn lanes (Sec. 2.2: one
+ *     lane per node of its stencil S_P, or two that split the node's sums of
+ *     the recursion and its time levels). lpn = 2 exists for FP32 contexts
+ *     with P = 2 or 4. The two forms group the recursion's sums differently,
+ *     so they agree to float rounding (both within the FP32 parity bar), not
+ *     bit for bit.
+ *   - Batched contexts: the batch is cut into tiles of
+ *     T = nw * floor(32 / (2P lpn)) - 1 consecutive cells of one instance
+ *     (P = 3, nw = 8, lpn = 1: 39); one CTA of nw warps per tile at a time,
+ *     on a grid of (SM count) x cps CTAs that stride over the tile list
+ *     (cps = 0: the kernel's occupancy). nw in {4, 8, 16}. At a fixed lpn,
+ *     nw and cps only move work between CTAs: every interface flux, wave
+ *     speed and update is computed from the same values, so the states are
+ *     bit-identical.
+ *   - Single-instance contexts: nw is fixed (8; 2 for the small-CTA FP64
+ *     step) and cps is 0 (one CTA per tile); FP32 contexts may set lpn.
+ * Defaults: nw = 8, lpn = 1, cps = 0.
+ * acat_launch_shape returns the current shape (cps resolved to a number for
+ * a batch). acat_set_launch_shape sets one; for a batch, changing nw or lpn
+ * rebuilds the tile list (a device allocation and a device synchronisation);
+ * any change drops the captured step graph.
+ * Errors: INVALID_ARG (a shape that does not exist, cps above the
+ * occupancy), UNSUPPORTED (2D contexts; a single-instance nw or cps other
+ * than its own, lpn on an FP64 single instance), NOMEM, CUDA. */
+int acat_launch_shape(const acat_ctx *ctx, int *nw_out, int *lpn_out, int *cps_out);
+int acat_set_launch_shape(acat_ctx *ctx, int nw, int lpn, int cps);
+
+/* Autotuner of the launch shape (batched contexts, and single-instance 1D
+ * FP32 contexts). Times `steps` steps (acat_run) from u_dev for every
+ * candidate shape: batched: nw in {8, 4, 16} x lpn in {1, 2 where it exists}
+ * x cps in {occupancy, occupancy / 2}; single FP32: lpn in {1, 2 where it
+ * exists}. Each candidate runs on a context-allocated copy of u_dev (u_dev is
+ * only read), once untimed and once timed with CUDA events on `stream`. The
+ * fastest shape is kept (acat_set_launch_shape) and returned in *nw_out,
+ * *lpn_out, *cps_out (each nullable). Synchronises `stream` and the device;
+ * must not be called during stream capture. Its launches count in
+ * acat_launch_count.
+ * Errors: INVALID_ARG, UNSUPPORTED (2D, or a single-instance FP64 context),
+ * NOMEM, CUDA, with the previous shape restored. */
+int acat_autotune(acat_ctx *ctx, const void *u_dev, int steps, void *stream, int *nw_out, int *lpn_out,
+                  int *cps_out);
+
 /* Frees every device and host resource of ctx (synchronises first). */
 int acat_destroy(acat_ctx *ctx);
 

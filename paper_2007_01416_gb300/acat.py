@@ -69,6 +69,10 @@ def lib() -> ctypes.CDLL:
         L.acat_adjoint_step.argtypes = [vp, vp, d, vp, vp, vp]
         L.acat_run_record.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
         L.acat_adjoint_run.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.acat_autotune.argtypes = [vp, vp, i, vp, ip, ip, ip]
+        L.acat_launch_shape.argtypes = [vp, ip, ip, ip]
+        L.acat_set_launch_shape.argtypes = [vp, i, i, i]
         L.acat_measure_fma_peak.argtypes = [i, vp]
         L.acat_measure_fma_peak.restype = ctypes.c_double
         _lib = L
@@ -162,6 +166,7 @@ class Context:
         self.params = params if params is not None else make_params(**kw)
         h = ctypes.c_void_p()
         self.n_inst = 0
+        self.sizes = None if sizes is None else [int(v) for v in sizes]
         if sizes is None:
             _check(lib().acat_create(ctypes.byref(self.params), ctypes.byref(h)), "acat_create")
         else:
@@ -206,6 +211,23 @@ class Context:
         _check(lib().acat_adjoint_run(self._h, _ptr(ckpt), _ptr(dts), int(nsteps), int(every), _ptr(ubar_n),
                                       _ptr(ubar_0), _stream(stream)), "acat_adjoint_run")
 
+    def acat_autotune(self, u, steps: int = 3, stream=None) -> tuple[int, int, int]:
+        """Times the step's launch shapes on a copy of u and keeps the fastest;
+        returns (warps per CTA, lanes per stencil node, CTAs per SM)."""
+        nw, lpn, cps = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().acat_autotune(self._h, _ptr(u), int(steps), _stream(stream), ctypes.byref(nw),
+                                   ctypes.byref(lpn), ctypes.byref(cps)), "acat_autotune")
+        return nw.value, lpn.value, cps.value
+
+    def acat_launch_shape(self) -> tuple[int, int, int]:
+        nw, lpn, cps = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().acat_launch_shape(self._h, ctypes.byref(nw), ctypes.byref(lpn), ctypes.byref(cps)),
+               "acat_launch_shape")
+        return nw.value, lpn.value, cps.value
+
+    def acat_set_launch_shape(self, nw: int, lpn: int = 1, cps: int = 0) -> None:
+        _check(lib().acat_set_launch_shape(self._h, int(nw), int(lpn), int(cps)), "acat_set_launch_shape")
+
     def acat_status(self) -> int:
         f = ctypes.c_uint(0)
         rc = lib().acat_status(self._h, ctypes.byref(f))
@@ -235,3 +257,42 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def tuning_key(ctx: Context, device_name: str) -> str:
+    """Key of a context's tuned launch shape: the device, the fields of the
+    problem that select the kernel, the grid size (single instance) or a
+    digest of the instance sizes (the tile list and the load balance depend
+    on them)."""
+    import hashlib
+    p = ctx.params
+    sizes = ctx.sizes if ctx.sizes is not None else [p.nx]
+    digest = hashlib.sha256(",".join(map(str, sizes)).encode()).hexdigest()[:16]
+    return (f"{device_name}|flux={p.flux}|P={p.P}|prec={p.precision}|psi2_mod={p.psi2_mod}"
+            f"|lo_flux={p.lo_flux}|batched={int(ctx.sizes is not None)}|sizes={digest}")
+
+
+def autotune_cached(ctx: Context, u, cache_path: str, device_name: str, steps: int = 3,
+                    stream=None) -> tuple[int, int, int]:
+    """acat_autotune with its result kept in a JSON file: a key found in the
+    file is applied with acat_set_launch_shape without timing; otherwise the
+    shape is tuned and stored. Returns (warps per CTA, lanes per node, CTAs
+    per SM; 0 = occupancy when applied from the file)."""
+    import json
+    key = tuning_key(ctx, device_name)
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    if key in cache:
+        e = cache[key]
+        nw, lpn, cps = int(e["nw"]), int(e["lpn"]), int(e["cps"])
+        ctx.acat_set_launch_shape(nw, lpn, cps)
+        return nw, lpn, cps
+    nw, lpn, cps = ctx.acat_autotune(u, steps, stream)
+    cache[key] = {"nw": nw, "lpn": lpn, "cps": cps}
+    tmp = cache_path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return nw, lpn, cps

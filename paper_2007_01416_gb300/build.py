@@ -17,10 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libacat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["step1d.cu", "step2d.cu", "adjoint1d.cu", "api.cu", "peak.cu", "weights.cpp",
+SOURCES = ["step1d.cu", "batch1d.cu", "step2d.cu", "adjoint1d.cu", "api.cu", "peak.cu", "weights.cpp",
            "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "acat_internal.h"), os.path.join(CSRC, "device_common.cuh"),
-           os.path.join(CSRC, "phys1d.cuh"),
+           os.path.join(CSRC, "phys1d.cuh"), os.path.join(CSRC, "step1d_core.cuh"),
            os.path.join(ROOT, "include", "acat.h")]
 
 

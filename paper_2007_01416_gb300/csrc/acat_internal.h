@@ -38,6 +38,7 @@ struct Step1DArgs {
   int psi2_mod;               // 1: psi~^2 in place of psi^2
   int lo_flux;                // F^lo: ACAT_LO_*
   int slot;                   // step index mod 3 (dt-reduction slots)
+  int lpn;                    // FP32 1D: lanes per stencil node (1, or 2 for P = 2, 4)
   double dx, cfl;
   double dt_fixed;            // > 0: imposed dt
   const double *dt_in;        // device: imposed dt (nullable; takes precedence)
@@ -75,10 +76,20 @@ struct BatchArgs {
   double *t;                  // 3 x B time slots
   double *dt_out;             // B (nullable)
   int8_t *orders;             // M + B order codes (nullable), instance b at offs[b] + b
+  int nw;                     // warps per CTA (4, 8 or 16); tiles of acat_cells_per_tile_1d(P, nw, lpn) cells
+  int cps;                    // CTAs per SM (<= 0: the kernel's occupancy)
+  int lpn;                    // lanes per stencil node (1; FP32 with P = 2, 4: 1 or 2)
 };
 
 int acat_launch_batch1d(int P, int flux, int prec, const Step1DArgs &a, const BatchArgs &bt,
                         void *stream);
+// Cells per tile of the batched kernel with nw warps per CTA and lpn lanes
+// per stencil node (0: unsupported).
+int acat_cells_per_tile_1d(int P, int nw, int lpn);
+// Resident CTAs per SM of the batched kernel with nw warps and lpn lanes per
+// node (-1: unsupported shape).
+int acat_batch_occupancy(int P, int flux, int prec, int nw, int lpn);
+
 int acat_launch_smax_batch(int flux, int prec, const Step1DArgs &a, const BatchArgs &bt, void *stream);
 
 // Arguments of one 2D step launch (passed by value). State u[c][y][x].
@@ -110,6 +121,7 @@ int acat_launch_step2d(int P, int flux, int prec, const Step2DArgs &a, void *str
 int acat_launch_smax2d(int flux, int prec, const Step2DArgs &a, void *stream);
 int acat_upload_tables_1d(const AcatTables *T);
 int acat_upload_tables_adj(const AcatTables *T);
+int acat_upload_tables_batch(const AcatTables *T);
 int acat_adjoint_slots(int P);
 // Adjoint of one 1D step (a.u_in = u^n, dt from a.dt_in or a.dt_fixed): ubar0 from ubar1.
 // FP64: double states and cotangents, double contrib; FP32: compensated float pairs, float contrib.

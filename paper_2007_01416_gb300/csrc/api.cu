@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/acat.h"
 #include "acat_internal.h"
@@ -37,6 +38,10 @@ struct acat_ctx {
   long long *d_offs = nullptr;
   TileRef *d_tiles = nullptr;
   long long ntiles = 0;
+  std::vector<int32_t> sizes;             // cells of each instance
+  int bnw = 8;                            // warps per CTA of the batched kernel
+  int bcps = 0;                           // its CTAs per SM (0: occupancy)
+  int lpn = 1;                            // 1D FP32: lanes per stencil node
   unsigned long long *d_smaxb = nullptr;  // 3 x B
   double *d_tb = nullptr;                 // 3 x B
   double *d_contrib = nullptr;            // adjoint: per-interface node cotangents
@@ -63,6 +68,12 @@ int nvars(int flux) {
 }
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? ACAT_OK : ACAT_ERR_CUDA; }
+
+// Whether lpn lanes per stencil node exist for (P, precision): two lanes per
+// node only for the FP32 recursion at P = 2, 4.
+bool acat_lpn_ok(int P, int prec, int lpn) {
+  return lpn == 1 || (lpn == 2 && prec == ACAT_PREC_F32 && (P == 2 || P == 4));
+}
 
 int check_params(const acat_params *p) {
   if (!p) return ACAT_ERR_INVALID_ARG;
@@ -121,6 +132,7 @@ Step1DArgs base_args(acat_ctx *c) {
   a.status = c->d_status;
   a.flux_buf = c->d_flux;
   a.cnt = c->d_cnt;
+  a.lpn = c->lpn;
   return a;
 }
 
@@ -176,7 +188,46 @@ BatchArgs batch_args(acat_ctx *c) {
   bt.xlen = c->p.x1 - c->p.x0;
   bt.smax = c->d_smaxb;
   bt.t = c->d_tb;
+  bt.nw = c->bnw;
+  bt.cps = c->bcps;
+  bt.lpn = c->lpn;
   return bt;
+}
+
+// (Re)builds the batch's work list for tiles of the kernel with nw warps and
+// lpn lanes per node: one (instance, tile) entry per tile, instances in order.
+int build_tiles(acat_ctx *c, int nw, int lpn) {
+  const int T = acat_cells_per_tile_1d(c->p.P, nw, lpn);
+  if (T <= 0) return ACAT_ERR_INVALID_ARG;
+  long long ntiles = 0;
+  for (int32_t n : c->sizes) ntiles += (n + T - 1) / T;
+  if (ntiles > (1ll << 31)) return ACAT_ERR_TOO_LARGE;
+  std::vector<TileRef> tiles;
+  tiles.reserve((size_t)ntiles);
+  for (int b = 0; b < (int)c->sizes.size(); b++)
+    for (int k = 0; k < (c->sizes[b] + T - 1) / T; k++) tiles.push_back(TileRef{b, k});
+  TileRef *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(TileRef) * (size_t)ntiles);
+  if (e == cudaSuccess) e = cudaMemcpy(d, tiles.data(), sizeof(TileRef) * (size_t)ntiles, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
+  }
+  // the old list may still be read by queued work and by the captured chain
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(d);
+    return ACAT_ERR_CUDA;
+  }
+  if (c->chain) {
+    cudaGraphExecDestroy(c->chain);
+    c->chain = nullptr;
+  }
+  cudaFree(c->d_tiles);
+  c->d_tiles = d;
+  c->ntiles = ntiles;
+  c->bnw = nw;
+  c->lpn = lpn;
+  return ACAT_OK;
 }
 
 // Steps n..n+count-1 of a run on (u, work), dt slots n % 3.
@@ -345,15 +396,12 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
   *out = nullptr;
   if (p->ny != 1 || p->flux == ACAT_FLUX_EULER2D) return ACAT_ERR_INVALID_ARG;
   const int gh = p->P > 2 ? p->P : 2;
-  long long M = 0, ntiles = 0;
-  const int T = acat_cells_per_cta_1d(p->P, p->precision);
-  if (T <= 0) return ACAT_ERR_INVALID_ARG;
+  long long M = 0;
   for (int b = 0; b < n_inst; b++) {
     if (n_per_inst[b] < 2 * gh) return ACAT_ERR_INVALID_ARG;
     M += n_per_inst[b];
-    ntiles += (n_per_inst[b] + T - 1) / T;
   }
-  if (M > (1ll << 31) || ntiles > (1ll << 31)) return ACAT_ERR_TOO_LARGE;
+  if (M > (1ll << 31)) return ACAT_ERR_TOO_LARGE;
   acat_params q = *p;
   q.nx = n_per_inst[0];
   acat_ctx *c = nullptr;
@@ -369,41 +417,154 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
   c->batched = 1;
   c->B = n_inst;
   c->cells = M;
-  c->ntiles = ntiles;
-  long long *offs = (long long *)std::malloc(sizeof(long long) * (size_t)(n_inst + 1));
-  TileRef *tiles = (TileRef *)std::malloc(sizeof(TileRef) * (size_t)ntiles);
-  if (!offs || !tiles) {
-    std::free(offs);
-    std::free(tiles);
+  c->sizes.assign(n_per_inst, n_per_inst + n_inst);
+  std::vector<long long> offs((size_t)n_inst + 1, 0);
+  for (int b = 0; b < n_inst; b++) offs[b + 1] = offs[b] + n_per_inst[b];
+  rc = build_tiles(c, 8, 1);
+  if (rc) {
     acat_destroy(c);
-    return ACAT_ERR_NOMEM;
-  }
-  offs[0] = 0;
-  long long w = 0;
-  for (int b = 0; b < n_inst; b++) {
-    offs[b + 1] = offs[b] + n_per_inst[b];
-    const int nt = (n_per_inst[b] + T - 1) / T;
-    for (int k = 0; k < nt; k++) tiles[w++] = TileRef{b, k};
+    return rc;
   }
   cudaError_t e = cudaMalloc(&c->d_work, (size_t)acat_state_bytes(c));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_offs, sizeof(long long) * (size_t)(n_inst + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_tiles, sizeof(TileRef) * (size_t)ntiles);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_smaxb, 3 * sizeof(unsigned long long) * (size_t)n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_tb, 3 * sizeof(double) * (size_t)n_inst);
   if (e == cudaSuccess)
-    e = cudaMemcpy(c->d_offs, offs, sizeof(long long) * (size_t)(n_inst + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->d_tiles, tiles, sizeof(TileRef) * (size_t)ntiles, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(c->d_offs, offs.data(), sizeof(long long) * (size_t)(n_inst + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_smaxb, 0, 3 * sizeof(unsigned long long) * (size_t)n_inst);
   if (e == cudaSuccess) e = cudaMemset(c->d_tb, 0, 3 * sizeof(double) * (size_t)n_inst);
-  std::free(offs);
-  std::free(tiles);
   if (e != cudaSuccess) {
     acat_destroy(c);
     return e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA;
   }
   *out = c;
   return ACAT_OK;
+}
+
+int acat_launch_shape(const acat_ctx *c, int *nw, int *lpn, int *cps) {
+  if (!c) return ACAT_ERR_INVALID_ARG;
+  if (c->dim != 1) return ACAT_ERR_UNSUPPORTED;
+  int w = 8, k = 0;
+  if (c->batched) {
+    w = c->bnw;
+    k = c->bcps > 0 ? c->bcps : acat_batch_occupancy(c->p.P, c->p.flux, c->p.precision, c->bnw, c->lpn);
+  } else if (c->d_flux) {
+    w = 2;  // the small-CTA FP64 step
+  }
+  if (nw) *nw = w;
+  if (lpn) *lpn = c->lpn;
+  if (cps) *cps = k;
+  return ACAT_OK;
+}
+
+int acat_set_launch_shape(acat_ctx *c, int nw, int lpn, int cps) {
+  if (!c || cps < 0) return ACAT_ERR_INVALID_ARG;
+  if (c->dim != 1) return ACAT_ERR_UNSUPPORTED;
+  if (!c->batched) {
+    int w0 = 0, l0 = 0, k0 = 0;
+    acat_launch_shape(c, &w0, &l0, &k0);
+    if (nw != w0 || cps != 0) return ACAT_ERR_UNSUPPORTED;  // fixed for a single instance
+    if (lpn == c->lpn) return ACAT_OK;
+    if (c->p.precision != ACAT_PREC_F32) return ACAT_ERR_UNSUPPORTED;
+    if (!acat_lpn_ok(c->p.P, c->p.precision, lpn)) return ACAT_ERR_INVALID_ARG;
+    if (c->chain) {
+      if (cudaDeviceSynchronize() != cudaSuccess) return ACAT_ERR_CUDA;
+      cudaGraphExecDestroy(c->chain);
+      c->chain = nullptr;
+    }
+    c->lpn = lpn;
+    return ACAT_OK;
+  }
+  if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || acat_cells_per_tile_1d(c->p.P, nw, lpn) <= 0)
+    return ACAT_ERR_INVALID_ARG;
+  const int occ = acat_batch_occupancy(c->p.P, c->p.flux, c->p.precision, nw, lpn);
+  if (occ < 1) return ACAT_ERR_CUDA;
+  if (cps > occ) return ACAT_ERR_INVALID_ARG;
+  if (nw != c->bnw || lpn != c->lpn) {
+    int rc = build_tiles(c, nw, lpn);
+    if (rc) return rc;
+  }
+  if (cps != c->bcps && c->chain) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return ACAT_ERR_CUDA;
+    cudaGraphExecDestroy(c->chain);
+    c->chain = nullptr;
+  }
+  c->bcps = cps;
+  return ACAT_OK;
+}
+
+int acat_autotune(acat_ctx *c, const void *u_dev, int steps, void *stream, int *nw_out, int *lpn_out,
+                  int *cps_out) {
+  if (!c || !u_dev || steps < 1) return ACAT_ERR_INVALID_ARG;
+  if (c->dim != 1 || !(c->batched || c->p.precision == ACAT_PREC_F32)) return ACAT_ERR_UNSUPPORTED;
+  // candidate shapes: (warps per CTA, lanes per node, CTAs per SM; 0 = occupancy)
+  struct Shape {
+    int nw, lpn, cps;
+  };
+  std::vector<Shape> cands;
+  const int lpns[2] = {1, 2};
+  for (int lpn : lpns) {
+    if (!acat_lpn_ok(c->p.P, c->p.precision, lpn)) continue;
+    if (!c->batched) {
+      cands.push_back(Shape{8, lpn, 0});
+      continue;
+    }
+    const int nws[3] = {8, 4, 16};
+    for (int nw : nws) {
+      const int occ = acat_batch_occupancy(c->p.P, c->p.flux, c->p.precision, nw, lpn);
+      if (occ < 1) continue;
+      cands.push_back(Shape{nw, lpn, 0});
+      if (occ / 2 >= 1) cands.push_back(Shape{nw, lpn, occ / 2});
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sb = (size_t)acat_state_bytes(c);
+  void *trial = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&trial, sb);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int rc = e == cudaSuccess ? ACAT_OK : (e == cudaErrorMemoryAllocation ? ACAT_ERR_NOMEM : ACAT_ERR_CUDA);
+  Shape old{0, 0, 0};
+  if (rc == ACAT_OK) acat_launch_shape(c, &old.nw, &old.lpn, &old.cps);
+  old.cps = c->bcps;
+  Shape best = old;
+  float best_ms = 0.0f;
+  for (size_t i = 0; i < cands.size() && rc == ACAT_OK; i++) {
+    rc = acat_set_launch_shape(c, cands[i].nw, cands[i].lpn, cands[i].cps);
+    float ms = 0.0f;
+    // untimed pass (first launch of this shape), then the timed one
+    for (int pass = 0; pass < 2 && rc == ACAT_OK; pass++) {
+      if (cudaMemcpyAsync(trial, u_dev, sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaEventRecord(e0, st) != cudaSuccess) {
+        rc = ACAT_ERR_CUDA;
+        break;
+      }
+      rc = acat_run(c, trial, steps, -1.0, stream, nullptr);
+      if (rc == ACAT_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = ACAT_ERR_CUDA;
+    }
+    if (rc == ACAT_OK && (best_ms == 0.0f || ms < best_ms)) {
+      best_ms = ms;
+      best = cands[i];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == ACAT_OK) rc = ACAT_ERR_CUDA;
+  if (c->chain) {  // captured on the trial buffer
+    cudaGraphExecDestroy(c->chain);
+    c->chain = nullptr;
+  }
+  cudaFree(trial);
+  if (rc != ACAT_OK) {
+    if (old.nw) acat_set_launch_shape(c, old.nw, old.lpn, old.cps);
+    return rc;
+  }
+  rc = acat_set_launch_shape(c, best.nw, best.lpn, best.cps);
+  if (rc) return rc;
+  return acat_launch_shape(c, nw_out, lpn_out, cps_out);
 }
 
 int acat_destroy(acat_ctx *c) {

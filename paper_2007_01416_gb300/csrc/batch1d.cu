@@ -1,0 +1,242 @@
+// batch1d.cu -- the batched 1D step: independent instances of ragged sizes,
+// concatenated along the cell index, advanced in one persistent launch per
+// step. CTAs stride over an (instance, tile) work list; each tile is the
+// tile of the single-instance step (step1d_core.cuh) with the instance's own
+// dt, and per-instance wave speeds are reduced into per-instance slots for
+// the next step's dt.
+#include "step1d_core.cuh"
+
+namespace {
+
+// dt of instance b of a batch (1D CFL rule on the instance's own wave speed
+// and grid); the instance's first tile advances its time and recycles its
+// slot two steps ahead.
+__device__ double batch_dt(const Step1DArgs &a, const BatchArgs &bt, int b, bool leader, double dx) {
+  const long B = bt.B;
+  double dt;
+  if (a.dt_fixed > 0.0) {
+    dt = a.dt_fixed;
+  } else {
+    const double smax = __longlong_as_double((long long)bt.smax[a.slot * B + b]);
+    if (!(smax > 0.0) || !isfinite(smax)) {
+      if (leader) atomicOr(a.status, (unsigned)ACAT_STATUS_BAD_DT);
+      dt = 0.0;
+    } else {
+      dt = a.cfl * dx / smax;
+    }
+  }
+  const double t = bt.t[a.slot * B + b];
+  if (a.t_end > 0.0) {
+    if (t >= a.t_end) dt = 0.0;
+    else if (dt > a.t_end - t) dt = a.t_end - t;
+  }
+  if (leader) {
+    bt.t[((a.slot + 1) % 3) * B + b] = t + dt;
+    bt.smax[((a.slot + 2) % 3) * B + b] = 0ull;
+    if (bt.dt_out) bt.dt_out[b] = dt;
+  }
+  return dt;
+}
+
+// Persistent batched step: CTAs of NW warps stride over the (instance,
+// first cell) work list, whose tiles are Tiling<P, NW, LPN>::T cells wide;
+// every instance is advanced with its own dt. The register cap per thread is
+// that of the 8-warp kernels (MinCtas x 8 / NW resident CTAs).
+template <int P, int FLUX, bool F32, int NW, int LPN>
+__global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
+    k_batch1d(const Step1DArgs a, const BatchArgs bt) {
+  using SM =
+      typename std::conditional<F32, Smem32<P, Phys<FLUX>::S, NW, LPN>, Smem64<P, Phys<FLUX>::S, NW>>::type;
+  // FP32: two workspaces used alternately (tile_f32 ends without a barrier)
+  __shared__ SM sm[F32 ? 2 : 1];
+  __shared__ double s_lam;
+  __shared__ float s_lamf[2];
+  int par = 0;
+  for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
+    const int b = bt.tiles[w].b;
+    const long i0 = (long)bt.tiles[w].tile * Tiling<P, NW, LPN>::T;
+    const long off = bt.offs[b], N = bt.offs[b + 1] - off;
+    if (threadIdx.x == 0) {
+      const double dx = bt.xlen / (double)N;
+      const double l = batch_dt(a, bt, b, i0 == 0, dx) / dx;
+      if constexpr (F32) s_lamf[par] = (float)l;
+      else s_lam = l;
+    }
+    int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
+    unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
+    if constexpr (F32) {
+      tile_f32<P, FLUX, NW, LPN>(a, sm[par], static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out),
+                                 off, bt.M, N, i0, &s_lamf[par], ord, so);
+      par ^= 1;
+    } else {
+      __syncthreads();
+      tile_f64<P, FLUX, NW>(a, sm[0], static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
+                            off, bt.M, N, i0, s_lam, ord, so);
+    }
+  }
+}
+
+// Wave speed of every instance of a batch into its slot (one CTA per
+// instance); also sets the instances' time to 0.
+template <int FLUX, bool F32>
+__global__ void __launch_bounds__(NT) k_smax_batch(const Step1DArgs a, const BatchArgs bt) {
+  constexpr int S = Phys<FLUX>::S;
+  __shared__ double red[NT / 32];
+  for (long b = blockIdx.x; b < bt.B; b += gridDim.x) {
+    const long off = bt.offs[b], N = bt.offs[b + 1] - off;
+    double smax = 0.0;
+    bool bad = false;
+    for (long i = threadIdx.x; i < N; i += NT) {
+      double u[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if constexpr (F32) {
+          const float *p = static_cast<const float *>(a.u_in);
+          u[c] = (double)p[c * bt.M + off + i] + (double)p[(S + c) * bt.M + off + i];
+        } else {
+          u[c] = static_cast<const double *>(a.u_in)[c * bt.M + off + i];
+        }
+      }
+      bool ok;
+      smax = fmax(smax, Phys<FLUX>::speed(u, a.adv, a.gamma, ok));
+      bad |= !ok;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+    const double v = block_max(smax, red);
+    if (threadIdx.x == 0) {
+      atomic_max_pos(&bt.smax[a.slot * bt.B + b], v);
+      bt.t[a.slot * bt.B + b] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// Resident CTAs per SM of the batched kernel with NW warps and LPN lanes per
+// node, and its launch on sms x cps CTAs (cps <= 0 or above the occupancy:
+// the occupancy). With occ_out set, only the occupancy is returned.
+template <int P, int FLUX, bool F32, int NW, int LPN>
+int launch_batch_nw(const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st, int *occ_out) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch1d<P, FLUX, F32, NW, LPN>, NW * 32, 0);
+  if (occ < 1) occ = 1;
+  if (occ_out) {
+    *occ_out = occ;
+    return 0;
+  }
+  const int cps = (bt.cps > 0 && bt.cps < occ) ? bt.cps : occ;
+  k_batch1d<P, FLUX, F32, NW, LPN><<<(unsigned)(sms * cps), NW * 32, 0, st>>>(a, bt);
+  return (int)cudaGetLastError();
+}
+
+template <int P, int FLUX, bool F32, int LPN>
+int launch_batch_lpn(const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st, int *occ_out) {
+  switch (bt.nw) {
+  case 4: return launch_batch_nw<P, FLUX, F32, 4, LPN>(a, bt, st, occ_out);
+  case 8: return launch_batch_nw<P, FLUX, F32, 8, LPN>(a, bt, st, occ_out);
+  case 16: return launch_batch_nw<P, FLUX, F32, 16, LPN>(a, bt, st, occ_out);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <int P, int FLUX, bool F32>
+int launch_batch_p(const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st, int *occ_out) {
+  if constexpr (F32 && (P == 2 || P == 4)) {
+    if (bt.lpn == 2) return launch_batch_lpn<P, FLUX, F32, 2>(a, bt, st, occ_out);
+  }
+  if (bt.lpn != 1) return (int)cudaErrorInvalidValue;
+  return launch_batch_lpn<P, FLUX, F32, 1>(a, bt, st, occ_out);
+}
+
+template <int FLUX, bool F32>
+int launch_batch_f(int P, const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st, int *occ_out) {
+  switch (P) {
+  case 1: return launch_batch_p<1, FLUX, F32>(a, bt, st, occ_out);
+  case 2: return launch_batch_p<2, FLUX, F32>(a, bt, st, occ_out);
+  case 3: return launch_batch_p<3, FLUX, F32>(a, bt, st, occ_out);
+  case 4: return launch_batch_p<4, FLUX, F32>(a, bt, st, occ_out);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <bool F32>
+int launch_batch(int P, int flux, const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st, int *occ_out) {
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: return launch_batch_f<ACAT_FLUX_LINEAR, F32>(P, a, bt, st, occ_out);
+  case ACAT_FLUX_BURGERS: return launch_batch_f<ACAT_FLUX_BURGERS, F32>(P, a, bt, st, occ_out);
+  case ACAT_FLUX_EULER1D: return launch_batch_f<ACAT_FLUX_EULER1D, F32>(P, a, bt, st, occ_out);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <bool F32>
+int launch_smax_batch(int flux, const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st) {
+  const unsigned grid = (unsigned)(bt.B < 4096 ? bt.B : 4096);
+  switch (flux) {
+  case ACAT_FLUX_LINEAR: k_smax_batch<ACAT_FLUX_LINEAR, F32><<<grid, NT, 0, st>>>(a, bt); break;
+  case ACAT_FLUX_BURGERS: k_smax_batch<ACAT_FLUX_BURGERS, F32><<<grid, NT, 0, st>>>(a, bt); break;
+  case ACAT_FLUX_EULER1D: k_smax_batch<ACAT_FLUX_EULER1D, F32><<<grid, NT, 0, st>>>(a, bt); break;
+  default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int acat_launch_batch1d(int P, int flux, int prec, const Step1DArgs &a, const BatchArgs &bt,
+                        void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return prec == ACAT_PREC_F32 ? launch_batch<true>(P, flux, a, bt, st, nullptr)
+                               : launch_batch<false>(P, flux, a, bt, st, nullptr);
+}
+
+int acat_batch_occupancy(int P, int flux, int prec, int nw, int lpn) {
+  BatchArgs bt;
+  std::memset(&bt, 0, sizeof bt);
+  bt.nw = nw;
+  bt.lpn = lpn;
+  Step1DArgs a;
+  std::memset(&a, 0, sizeof a);
+  int occ = 0;
+  const int e = prec == ACAT_PREC_F32 ? launch_batch<true>(P, flux, a, bt, nullptr, &occ)
+                                      : launch_batch<false>(P, flux, a, bt, nullptr, &occ);
+  return e ? -1 : occ;
+}
+
+namespace {
+template <int NW, int LPN>
+int cells_per_tile(int P) {
+  switch (P) {
+  case 1: return Tiling<1, NW, LPN>::T;
+  case 2: return Tiling<2, NW, LPN>::T;
+  case 3: return Tiling<3, NW, LPN>::T;
+  case 4: return Tiling<4, NW, LPN>::T;
+  }
+  return 0;
+}
+template <int LPN>
+int cells_per_tile_nw(int P, int nw) {
+  switch (nw) {
+  case 4: return cells_per_tile<4, LPN>(P);
+  case 8: return cells_per_tile<8, LPN>(P);
+  case 16: return cells_per_tile<16, LPN>(P);
+  }
+  return 0;
+}
+}  // namespace
+
+int acat_cells_per_tile_1d(int P, int nw, int lpn) {
+  if (lpn == 1) return cells_per_tile_nw<1>(P, nw);
+  if (lpn == 2 && (P == 2 || P == 4)) return cells_per_tile_nw<2>(P, nw);
+  return 0;
+}
+
+int acat_launch_smax_batch(int flux, int prec, const Step1DArgs &a, const BatchArgs &bt, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return prec == ACAT_PREC_F32 ? launch_smax_batch<true>(flux, a, bt, st)
+                               : launch_smax_batch<false>(flux, a, bt, st);
+}
+
+int acat_upload_tables_batch(const AcatTables *T) { return (int)cudaMemcpyToSymbol(c_tab, T, sizeof *T); }

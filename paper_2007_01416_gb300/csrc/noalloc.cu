@@ -99,6 +99,7 @@ extern "C" int acat_run_noalloc(const acat_params *p, void *u_dev, int nsteps, d
   Step1DArgs a;
   std::memset(&a, 0, sizeof a);
   a.N = p->nx;
+  a.lpn = 1;
   a.bc = p->bc;
   a.limiter_form = p->limiter_form;
   a.psi2_mod = p->psi2_mod;

@@ -98,12 +98,13 @@ __device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form
   return psi1_line<Phys<FLUX>::S>(q, cs, 1, FLUX == ACAT_FLUX_LINEAR ? 0 : 1, limiter_form, adv);
 }
 
-// Interface tiling of a CTA of NW warps: groups of L = 2P lanes, one per
-// interface; a fused step tile updates T = NI - 1 cells, a flux-only tile
-// computes NI interfaces. TW cells are staged (GH ghosts each side).
-template <int P, int NW = NT / 32>
+// Interface tiling of a CTA of NW warps: groups of L = 2P x LPN lanes (LPN
+// lanes per stencil node), one per interface; a fused step tile updates
+// T = NI - 1 cells, a flux-only tile computes NI interfaces. TW cells are
+// staged (GH ghosts each side).
+template <int P, int NW = NT / 32, int LPN = 1>
 struct Tiling {
-  static constexpr int L = 2 * P;             // lanes per interface
+  static constexpr int L = 2 * P * LPN;       // lanes per interface
   static constexpr int GPW = 32 / L;          // interface groups per warp
   static constexpr int NI = NW * GPW;         // interfaces per CTA
   static constexpr int T = NI - 1;            // cells per CTA
@@ -121,13 +122,13 @@ constexpr int NWF = 2;
 // p_s = max A (1 when A is empty). A component's psi is admissible when
 // psi >= thr; as in a literal minimum over components taken from the first
 // component, a NaN in the first component rejects p and a NaN elsewhere is
-// ignored. Must be called by all 32 lanes.
-template <int P, int S, bool F32>
+// ignored. Groups have LPN lanes per node. Must be called by all 32 lanes.
+template <int P, int S, bool F32, int LPN = 1>
 __device__ __forceinline__ int select_order(const double *t0, const float *h0, const float *l0, int cs,
                                             int l, int grp, bool active, bool valid,
                                             const FiltConst &FC, double eps, double thr,
                                             const double *fact, int psi2_mod) {
-  using TL = Tiling<P>;
+  using TL = Tiling<P, NT / 32, LPN>;
   if (P < 2) return 1;
   constexpr int NPAIR = (P - 1) * S;
   unsigned rej = 0;

@@ -43,18 +43,29 @@ def _step32(env, ctx, pair, nx):
     return out.cpu().numpy(), float(dtv.item()), orders.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind,P,nx,bc", [("euler", 4, 16384, 1), ("euler", 3, 1001, 0),
-                                          ("euler", 2, 777, 1), ("burgers", 2, 400, 0),
-                                          ("burgers", 4, 513, 1), ("euler", 1, 64, 1)])
-def test_single_step_f32(env, kind, P, nx, bc):
+@pytest.mark.parametrize("kind,P,nx,bc,lpn", [("euler", 4, 16384, 1, 1), ("euler", 3, 1001, 0, 1),
+                                              ("euler", 2, 777, 1, 1), ("burgers", 2, 400, 0, 1),
+                                              ("burgers", 4, 513, 1, 1), ("euler", 1, 64, 1, 1),
+                                              ("euler", 4, 16384, 1, 2), ("euler", 4, 1001, 0, 2),
+                                              ("euler", 2, 777, 1, 2), ("burgers", 2, 400, 0, 2),
+                                              ("burgers", 4, 513, 1, 2), ("linear", 4, 300, 0, 2)])
+def test_single_step_f32(env, kind, P, nx, bc, lpn):
+    """lpn = 2: two lanes per stencil node (the node's sums split in two)."""
     torch, O, acat = env
-    c = W.burgers_sine(nx=nx, seed=2, P=P) if kind == "burgers" else \
-        W.euler1d_riemann_entropy(nx=nx, seed=2, P=P)
+    if kind == "linear":
+        c = W.burgers_sine(nx=nx, seed=2, P=P)
+        c.u0 = c.u0 + 0.5 * (W.centres(nx, c.x0, c.x1) > 0.3)[None, :]
+        c.flux, c.adv = W.LINEAR, (0.8, 0.0)
+    else:
+        c = W.burgers_sine(nx=nx, seed=2, P=P) if kind == "burgers" else \
+            W.euler1d_riemann_entropy(nx=nx, seed=2, P=P)
     c.bc = bc
     kw = c.problem_kwargs()
     pair = acat.to_pair(c.u0)
     x = acat.from_pair(pair)  # the exact value the GPU sees
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        ctx.acat_set_launch_shape(8, lpn, 0)
+        assert ctx.acat_launch_shape() == (8, lpn, 0)
         out, dt, orders = _step32(env, ctx, pair, nx)
         assert ctx.acat_status() == 0
     pr = O.Problem(**kw)
@@ -62,11 +73,12 @@ def test_single_step_f32(env, kind, P, nx, bc):
     ref, _, ord_ref = O.step_1d(pr, x, dt)
     assert np.array_equal(orders, ord_ref)
     err = np.abs(acat.from_pair(out) - ref).max() / max(1.0, np.abs(ref).max())
-    print(f"single step f32 {kind} P={P} nx={nx}: rel err {err:.2e}")
+    print(f"single step f32 {kind} P={P} nx={nx} lpn={lpn}: rel err {err:.2e}")
     assert err < STEP_TOL, err
 
 
-def test_teacher_forced_f32(env):
+@pytest.mark.parametrize("lpn", [1, 2])
+def test_teacher_forced_f32(env, lpn):
     torch, O, acat = env
     c = W.euler1d_riemann_entropy(nx=2048, seed=4, P=4)
     kw = c.problem_kwargs()
@@ -74,6 +86,7 @@ def test_teacher_forced_f32(env):
     pair = acat.to_pair(c.u0)
     worst = 0.0
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        ctx.acat_set_launch_shape(8, lpn, 0)
         for n in range(100):
             x = acat.from_pair(pair)
             out, dt, orders = _step32(env, ctx, pair, c.nx)
@@ -85,8 +98,8 @@ def test_teacher_forced_f32(env):
     assert worst < STEP_TOL, worst
 
 
-@pytest.mark.parametrize("P,nx,steps", [(4, 4096, 1000), (2, 4096, 1000)])
-def test_free_run_f32_against_oracle(env, P, nx, steps):
+@pytest.mark.parametrize("P,nx,steps,lpn", [(4, 4096, 1000, 1), (2, 4096, 1000, 1), (4, 4096, 1000, 2)])
+def test_free_run_f32_against_oracle(env, P, nx, steps, lpn):
     """Free-running FP32 and FP64 GPU runs of the 1D Euler workload shape
     against the oracle run: L1 and Linf of the final state.
 
@@ -104,6 +117,7 @@ def test_free_run_f32_against_oracle(env, P, nx, steps):
         ref, _, _ = O.step_1d(pr, ref)
     scale = np.abs(ref).max()
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        ctx.acat_set_launch_shape(8, lpn, 0)
         u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
         ctx.acat_run(u, steps)
         torch.cuda.synchronize()
@@ -118,7 +132,7 @@ def test_free_run_f32_against_oracle(env, P, nx, steps):
     li_32 = np.abs(got32 - ref).max() / scale
     l1_64 = np.abs(got64 - ref).mean() / np.abs(ref).mean()
     li_64 = np.abs(got64 - ref).max() / scale
-    print(f"P={P}: FP32 L1 {l1_32:.2e} Linf {li_32:.2e}; FP64 L1 {l1_64:.2e} Linf {li_64:.2e}")
+    print(f"P={P} lpn={lpn}: FP32 L1 {l1_32:.2e} Linf {li_32:.2e}; FP64 L1 {l1_64:.2e} Linf {li_64:.2e}")
     assert l1_32 < steps * STEP_TOL and l1_64 < 1e-5
     assert li_32 < 1e-2 and li_64 < 1e-2
 
@@ -134,3 +148,37 @@ def test_run_host_f32(env):
         ctx.acat_run_host(pair.pin_memory(), out, 41)
         torch.cuda.synchronize()
         assert torch.equal(out, u.cpu())
+
+
+def test_single_instance_shape_and_autotune(env):
+    """Single-instance shapes: FP32 may switch lanes per node (P = 2, 4); the
+    tile width and grid are fixed; FP64 and lpn = 2 at P = 3 are refused.
+    acat_autotune on a single FP32 instance keeps the state it reads."""
+    torch, O, acat = env
+    c = W.euler1d_riemann_entropy(nx=4096, seed=1, P=4)
+    kw = c.problem_kwargs()
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        assert ctx.acat_launch_shape() == (8, 1, 0)
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_set_launch_shape(4, 1, 0)
+        assert ei.value.code == -5
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_set_launch_shape(8, 3, 0)
+        assert ei.value.code == -1
+        u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
+        keep = u.clone()
+        nw, lpn, cps = ctx.acat_autotune(u, steps=50)
+        assert torch.equal(u, keep) and nw == 8 and lpn in (1, 2) and cps == 0
+        assert ctx.acat_launch_shape() == (8, lpn, 0)
+    with acat.Context(**{**kw, "P": 3}, precision=acat.PREC_F32) as ctx:
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_set_launch_shape(8, 2, 0)
+        assert ei.value.code == -1
+    with acat.Context(**kw) as ctx:
+        nw = ctx.acat_launch_shape()[0]
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_set_launch_shape(nw, 2, 0)
+        assert ei.value.code == -5
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_autotune(torch.from_numpy(c.u0).cuda())
+        assert ei.value.code == -5

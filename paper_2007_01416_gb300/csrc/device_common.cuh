@@ -144,16 +144,6 @@ __device__ __forceinline__ double psi2m_comp_g(Get q, double eps, double fact) {
   return a > b ? a : b;
 }
 
-__device__ __forceinline__ double psi_p_comp(const double *q, int st, int p, double eps, double fact) {
-  return psi_p_comp_g([=](int j) { return q[j * st]; }, p, eps, fact);
-}
-
-// The same on a compensated float state: the exact value hi + lo.
-__device__ __forceinline__ double psi_p_comp_pair(const float *hi, const float *lo, int st, int p,
-                                                  double eps, double fact) {
-  return psi_p_comp_g([=](int j) { return (double)hi[j * st] + (double)lo[j * st]; }, p, eps, fact);
-}
-
 __device__ __forceinline__ double lim_ratio(double upw, double loc) {
   if (loc == 0.0) {
     if (upw == 0.0) return 1.0;
@@ -179,50 +169,15 @@ __device__ __forceinline__ double superbee(double r) {
 //   I_L, I_R, I from the d_k (relative error below 4e-6),
 //   Delta^{2p-1} u = Delta^{2p-2} d by repeated differencing, its bound
 //   propagated as e' = e_{k+1} + e_k + 2^-24 |t'|,
-// and the decision is returned only when the bounds leave no doubt (with a
+// and the decision is taken only when the bounds leave no doubt (with a
 // further relative margin of 1e-5, far above the rounding of a literal FP64
-// evaluation). Otherwise the caller evaluates psi^p literally in FP64. Returns
-// 1 (accept), 0 (reject) or -1 (undecided). The same decision as the literal
-// FP64 evaluation results in every case.
+// evaluation). Otherwise it is undecided and the caller evaluates psi^p
+// literally in FP64. The same decision as the literal FP64 evaluation
+// results in every case.
 // ---------------------------------------------------------------------------
-template <int p>
-__device__ __forceinline__ int psi_filter(const float *d, const float *e, float eps, float r,
-                                          float fact) {
-  constexpr int n = 2 * p - 1;
-  float IL = 0.0f, IR = 0.0f;
-#pragma unroll
-  for (int k = 0; k < p - 1; k++) IL = fmaf(d[k], d[k], IL);
-#pragma unroll
-  for (int k = p; k < n; k++) IR = fmaf(d[k], d[k], IR);
-  IL += eps;
-  IR += eps;
-  if (!(IL > 1e-30f && IR > 1e-30f) || !(IL < 1e30f && IR < 1e30f)) return -1;
-  const float I = IL * IR / (IL + IR);
-  float t[n], b[n];
-#pragma unroll
-  for (int k = 0; k < n; k++) {
-    t[k] = d[k];
-    b[k] = e[k];
-  }
-#pragma unroll
-  for (int lev = 1; lev < n; lev++)
-#pragma unroll
-    for (int k = 0; k < n - lev; k++) {
-      t[k] = t[k + 1] - t[k];
-      b[k] = (b[k + 1] + b[k]) + 5.97e-8f * fabsf(t[k]) + 1e-44f;
-    }
-  const float S = fabsf(t[0]), eS = 1.01f * b[0];
-  const float Dhi = (S + eS) * fact * 1.0000005f;
-  const float Dlo = fmaxf(S - eS, 0.0f) * fact * 0.9999995f;
-  const float lo = I * (1.0f - 4e-6f), hi = I * (1.0f + 4e-6f);
-  if (lo > r * (Dhi * Dhi) * 1.00001f) return 1;
-  if (hi < r * (Dlo * Dlo) * 0.99999f) return 0;
-  return -1;
-}
-
 // The filtered decision for psi~^2 (differences d_0..d_2 of S_2 with bounds
 // e): accept when either split's I certainly reaches r tau, reject when
-// neither can, else undecided; the bounds are those of psi_filter.
+// neither can, else undecided; the bounds are those of psi_filter_all.
 __device__ __forceinline__ int psi2m_filter(const float *d, const float *e, float eps, float r, float fact) {
   const float sm = d[0] * d[0], s0 = d[1] * d[1], sp = d[2] * d[2];
   const float I1L = sm + eps, I1R = (s0 + sp) + eps, I2L = (sm + s0) + eps, I2R = sp + eps;
@@ -266,97 +221,123 @@ __device__ __forceinline__ FiltConst filt_const(float eps, float r, const float 
   return f;
 }
 
-// Admissibility of order p for one component of an FP64 state; values at
-// q[j*st], j = -p+1..p. `first`: the first component (a NaN there rejects, a
-// NaN in a later component is ignored, as in a minimum taken from the first
-// component).
-template <int p>
-__device__ __forceinline__ bool admit64(const double *q, int st, bool first, const FiltConst &F,
-                                        double eps, double thr, double fact) {
-  float d[2 * p - 1], e[2 * p - 1];
+// The filtered decision for every order p = 2..PM of one component at once.
+// The stencils S_2 c S_3 c ... c S_PM are nested around the same interface,
+// so their first differences are windows of those of S_PM:
+//   d_k = u_{k-PM+2} - u_{k-PM+1}, k = 0..2PM-2 (bounds e_k),
+// S_p taking d_{PM-p} .. d_{PM+p-2}. One differencing triangle over all d
+// holds Delta^{2p-2} d of the window of S_p at level 2p-2, entry PM-p: each
+// entry depends on its own window only, so it is the value (and bound) that
+// differencing that window alone would give. I_L and I_R grow outwards by
+// one square per order. Bit p-2 of *acc: accepted, of *und: undecided.
+template <int PM>
+__device__ __forceinline__ void psi_filter_all(const float *d, const float *e, float eps, float r,
+                                               const float *fact, unsigned *acc, unsigned *und) {
+  constexpr int n = 2 * PM - 1;
+  float t[n], b[n], S[PM + 1], eS[PM + 1];
 #pragma unroll
-  for (int k = 0; k < 2 * p - 1; k++) {
-    const int j = k - p + 1;
+  for (int k = 0; k < n; k++) {
+    t[k] = d[k];
+    b[k] = e[k];
+  }
+#pragma unroll
+  for (int lev = 1; lev < n; lev++) {
+#pragma unroll
+    for (int k = 0; k < n - lev; k++) {
+      t[k] = t[k + 1] - t[k];
+      b[k] = (b[k + 1] + b[k]) + 5.97e-8f * fabsf(t[k]) + 1e-44f;
+    }
+    if (lev % 2 == 0) {
+      const int p = lev / 2 + 1;
+      S[p] = fabsf(t[PM - p]);
+      eS[p] = 1.01f * b[PM - p];
+    }
+  }
+  unsigned a = 0, u = 0;
+  float il = 0.0f, ir = 0.0f;
+#pragma unroll
+  for (int p = 2; p <= PM; p++) {
+    const unsigned bit = 1u << (p - 2);
+    il = fmaf(d[PM - p], d[PM - p], il);
+    ir = fmaf(d[PM + p - 2], d[PM + p - 2], ir);
+    const float IL = il + eps, IR = ir + eps;
+    if (!(IL > 1e-30f && IR > 1e-30f) || !(IL < 1e30f && IR < 1e30f)) {
+      u |= bit;
+      continue;
+    }
+    const float I = IL * IR / (IL + IR);
+    const float Dhi = (S[p] + eS[p]) * fact[p] * 1.0000005f;
+    const float Dlo = fmaxf(S[p] - eS[p], 0.0f) * fact[p] * 0.9999995f;
+    if (I * (1.0f - 4e-6f) > r * (Dhi * Dhi) * 1.00001f) a |= bit;
+    else if (!(I * (1.0f + 4e-6f) < r * (Dlo * Dlo) * 0.99999f)) u |= bit;
+  }
+  *acc = a;
+  *und = u;
+}
+
+// The rejected orders p = 2..PM (bit p - 2) of one component, from the
+// filtered decisions of psi_filter_all (psi2m_filter for p = 2 when
+// psi2_mod) and, where a decision is undecided, the literal FP64 evaluation
+// of psi^p on q(j) (the FP64 value of cell i + j). `first`: the first
+// component (a NaN there rejects, a NaN in a later component is ignored, as
+// in a minimum taken from the first component). d, e: the differences of
+// S_PM and their bounds, as for psi_filter_all.
+template <int PM, class Get>
+__device__ __forceinline__ unsigned reject_set(const float *d, const float *e, Get q, bool first,
+                                               const FiltConst &F, double eps, double thr, const double *fact,
+                                               int psi2_mod) {
+  unsigned acc, und;
+  psi_filter_all<PM>(d, e, F.eps, F.r, F.fact, &acc, &und);
+  unsigned rej = 0;
+#pragma unroll
+  for (int p = 2; p <= PM; p++) {
+    const unsigned bit = 1u << (p - 2);
+    const bool mod = p == 2 && psi2_mod;
+    const int dec = mod ? psi2m_filter(d + PM - 2, e + PM - 2, F.eps, F.r, F.fact[2])
+                        : ((und & bit) ? -1 : ((acc & bit) ? 1 : 0));
+    bool ok;
+    if (dec >= 0) {
+      ok = dec == 1;
+    } else {
+      const double v = mod ? psi2m_comp_g(q, eps, fact[2]) : psi_p_comp_g(q, p, eps, fact[p]);
+      ok = first ? (v >= thr) : !(v < thr);
+    }
+    if (!ok) rej |= bit;
+  }
+  return rej;
+}
+
+// reject_set of one component of an FP64 state, values at q[j*st],
+// j = -PM+1..PM.
+template <int PM>
+__device__ __forceinline__ unsigned reject_set64(const double *q, int st, bool first, const FiltConst &F,
+                                                 double eps, double thr, const double *fact, int psi2_mod) {
+  float d[2 * PM - 1], e[2 * PM - 1];
+#pragma unroll
+  for (int k = 0; k < 2 * PM - 1; k++) {
+    const int j = k - PM + 1;
     d[k] = (float)__dsub_rn(q[(j + 1) * st], q[j * st]);
     e[k] = 6.0e-8f * fabsf(d[k]) + 1e-44f;
   }
-  const int dec = psi_filter<p>(d, e, F.eps, F.r, F.fact[p]);
-  if (dec >= 0) return dec == 1;
-  const double v = psi_p_comp(q, st, p, eps, fact);
-  return first ? (v >= thr) : !(v < thr);
+  return reject_set<PM>(d, e, [=](int j) { return q[j * st]; }, first, F, eps, thr, fact, psi2_mod);
 }
 
 // The same for a compensated float state hi + lo (the literal fallback reads
 // the exact value hi + lo).
-template <int p>
-__device__ __forceinline__ bool admit32(const float *hi, const float *lo, int st, bool first,
-                                        const FiltConst &F, double eps, double thr, double fact) {
-  float d[2 * p - 1], e[2 * p - 1];
+template <int PM>
+__device__ __forceinline__ unsigned reject_set32(const float *hi, const float *lo, int st, bool first,
+                                                 const FiltConst &F, double eps, double thr, const double *fact,
+                                                 int psi2_mod) {
+  float d[2 * PM - 1], e[2 * PM - 1];
 #pragma unroll
-  for (int k = 0; k < 2 * p - 1; k++) {
-    const int j = k - p + 1;
+  for (int k = 0; k < 2 * PM - 1; k++) {
+    const int j = k - PM + 1;
     const float h1 = hi[(j + 1) * st], h0 = hi[j * st];
     d[k] = (h1 - h0) + (lo[(j + 1) * st] - lo[j * st]);
     e[k] = 1.2e-7f * fabsf(d[k]) + 1.5e-14f * (fabsf(h1) + fabsf(h0)) + 1e-44f;
   }
-  const int dec = psi_filter<p>(d, e, F.eps, F.r, F.fact[p]);
-  if (dec >= 0) return dec == 1;
-  const double v = psi_p_comp_pair(hi, lo, st, p, eps, fact);
-  return first ? (v >= thr) : !(v < thr);
-}
-
-// psi~^2 admissibility of one component (FP64 state, then the compensated one).
-__device__ __forceinline__ bool admit64_2m(const double *q, int st, bool first, const FiltConst &F,
-                                           double eps, double thr, double fact) {
-  float d[3], e[3];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    d[k] = (float)__dsub_rn(q[k * st], q[(k - 1) * st]);
-    e[k] = 6.0e-8f * fabsf(d[k]) + 1e-44f;
-  }
-  const int dec = psi2m_filter(d, e, F.eps, F.r, F.fact[2]);
-  if (dec >= 0) return dec == 1;
-  const double v = psi2m_comp_g([=](int j) { return q[j * st]; }, eps, fact);
-  return first ? (v >= thr) : !(v < thr);
-}
-__device__ __forceinline__ bool admit32_2m(const float *hi, const float *lo, int st, bool first,
-                                           const FiltConst &F, double eps, double thr, double fact) {
-  float d[3], e[3];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const float h1 = hi[k * st], h0 = hi[(k - 1) * st];
-    d[k] = (h1 - h0) + (lo[k * st] - lo[(k - 1) * st]);
-    e[k] = 1.2e-7f * fabsf(d[k]) + 1.5e-14f * (fabsf(h1) + fabsf(h0)) + 1e-44f;
-  }
-  const int dec = psi2m_filter(d, e, F.eps, F.r, F.fact[2]);
-  if (dec >= 0) return dec == 1;
-  const double v =
-      psi2m_comp_g([=](int j) { return (double)hi[j * st] + (double)lo[j * st]; }, eps, fact);
-  return first ? (v >= thr) : !(v < thr);
-}
-
-// Dispatch on a runtime p in 2..4 (lanes of one warp may hold different p);
-// psi2_mod selects psi~^2 for p = 2.
-__device__ __forceinline__ bool admit64_p(int p, const double *q, int st, bool first,
-                                          const FiltConst &F, double eps, double thr, double fact,
-                                          int psi2_mod) {
-  switch (p) {
-  case 2:
-    return psi2_mod ? admit64_2m(q, st, first, F, eps, thr, fact) : admit64<2>(q, st, first, F, eps, thr, fact);
-  case 3: return admit64<3>(q, st, first, F, eps, thr, fact);
-  default: return admit64<4>(q, st, first, F, eps, thr, fact);
-  }
-}
-__device__ __forceinline__ bool admit32_p(int p, const float *hi, const float *lo, int st, bool first,
-                                          const FiltConst &F, double eps, double thr, double fact,
-                                          int psi2_mod) {
-  switch (p) {
-  case 2:
-    return psi2_mod ? admit32_2m(hi, lo, st, first, F, eps, thr, fact)
-                    : admit32<2>(hi, lo, st, first, F, eps, thr, fact);
-  case 3: return admit32<3>(hi, lo, st, first, F, eps, thr, fact);
-  default: return admit32<4>(hi, lo, st, first, F, eps, thr, fact);
-  }
+  return reject_set<PM>(d, e, [=](int j) { return (double)hi[j * st] + (double)lo[j * st]; }, first, F, eps, thr,
+                        fact, psi2_mod);
 }
 
 // psi^1 (Eqs. 3.5-3.7, superbee) at the interface between q[0] (cell i) and

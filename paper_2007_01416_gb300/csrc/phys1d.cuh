@@ -116,13 +116,14 @@ struct Tiling {
 // step's interfaces evenly over the SMs (no CTA-sized tail).
 constexpr int NWF = 2;
 
-// Order selection of the interface of lane group `grp`: the (p, component)
-// pairs p = 2..P are spread over the group's lanes, each lane evaluating
-// psi^p of one component; a group OR-reduction of the rejected orders gives
-// p_s = max A (1 when A is empty). A component's psi is admissible when
-// psi >= thr; as in a literal minimum over components taken from the first
-// component, a NaN in the first component rejects p and a NaN elsewhere is
-// ignored. Groups have LPN lanes per node. Must be called by all 32 lanes.
+// Order selection of the interface of lane group `grp`: lane c < S of the
+// group decides every order p = 2..P of component c (reject_set: the
+// filtered indicator decisions of all nested stencils at once); a group
+// OR-reduction of the rejected orders gives p_s = max A (1 when A is empty).
+// A component's psi is admissible when psi >= thr; as in a literal minimum
+// over components taken from the first component, a NaN in the first
+// component rejects p and a NaN elsewhere is ignored. Groups have LPN lanes
+// per node. Must be called by all 32 lanes.
 template <int P, int S, bool F32, int LPN = 1>
 __device__ __forceinline__ int select_order(const double *t0, const float *h0, const float *l0, int cs,
                                             int l, int grp, bool active, bool valid,
@@ -130,17 +131,14 @@ __device__ __forceinline__ int select_order(const double *t0, const float *h0, c
                                             const double *fact, int psi2_mod) {
   using TL = Tiling<P, NT / 32, LPN>;
   if (P < 2) return 1;
-  constexpr int NPAIR = (P - 1) * S;
+  static_assert(S <= 2 * P || P < 2, "one lane per component");
   unsigned rej = 0;
-  if (active) {
-    for (int q = l; q < NPAIR; q += TL::L) {
-      const int p = 2 + q / S, c = q - (q / S) * S;
-      bool ok;
+  if (active && l < S) {
+    if constexpr (P >= 2) {
       if constexpr (F32)
-        ok = admit32_p(p, h0 + c * cs, l0 + c * cs, 1, c == 0, FC, eps, thr, fact[p], psi2_mod);
+        rej = reject_set32<P>(h0 + l * cs, l0 + l * cs, 1, l == 0, FC, eps, thr, fact, psi2_mod);
       else
-        ok = admit64_p(p, t0 + c * cs, 1, c == 0, FC, eps, thr, fact[p], psi2_mod);
-      if (!ok) rej |= 1u << (p - 2);
+        rej = reject_set64<P>(t0 + l * cs, 1, l == 0, FC, eps, thr, fact, psi2_mod);
     }
   }
   constexpr unsigned spare = (TL::GPW * TL::L >= 32) ? 0u : (0xffffffffu << (TL::GPW * TL::L));

@@ -6,14 +6,15 @@
 // [i0 - GH, i0 + T + GH) are staged once in shared memory with the boundary
 // condition applied while loading. Each interface is worked by a group of 2P
 // lanes of one warp, one lane per stencil node j = -p+1..p:
-//   - the (p, component) pairs of the indicators psi^p (Eqs. 3.8-3.12, the
-//     minimum over components of Sec. 3.4) are spread over the group's lanes.
-//     Each pair is decided by a float test with a certified error margin
-//     (psi_filter); only when the margin cannot settle it is psi^p evaluated
-//     literally with explicitly rounded FP64 operations in the order of its
-//     definition. Either way the decision is the one a literal FP64
-//     evaluation of the same state takes. An OR-reduction over the group
-//     gives p_s = max A (Eqs. 3.2-3.3);
+//   - the indicators psi^p (Eqs. 3.8-3.12, the minimum over components of
+//     Sec. 3.4): lane c of the group decides every order p = 2..P of
+//     component c from the differences of the largest stencil (the smaller
+//     ones are nested in it). Each decision is a float test with a certified
+//     error margin (psi_filter_all); only when the margin cannot settle it
+//     is psi^p evaluated literally with explicitly rounded FP64 operations
+//     in the order of its definition. Either way the decision is the one a
+//     literal FP64 evaluation of the same state takes. An OR-reduction over
+//     the group gives p_s = max A (Eqs. 3.2-3.3);
 //   - for p_s >= 2 every lane runs the local Taylor recursion of Sec. 2.2 for
 //     its node in registers, in the dt-scaled form
 //         U^(k-1)_j = -lambda sum_r gamma^{1,j}_r F^(k-2)_r     (shuffles)

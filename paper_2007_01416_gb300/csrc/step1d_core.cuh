@@ -255,10 +255,14 @@ struct DPhys<ACAT_FLUX_EULER1D> {
 
 // CAT2p increment G of one interface by a group of 2p lanes (lane l <-> node
 // j = l - p + 1). hi/lo point at cell i of component 0 of the compensated
-// tile, components `cs` apart. Every lane returns G.
+// tile, components `cs` apart. xw: the warp's 64 exchange slots in shared
+// memory (two sets of 32 used alternately by k), through which the lanes of
+// the group read the F^(k-2) of all nodes of a system: one 16-byte store and
+// 2p 16-byte broadcast loads per lane and order instead of 2p s shuffles
+// (scalar laws shuffle). Every lane returns G.
 template <int p, int FLUX>
 __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int cs, int l, int base,
-                                          float lam, float adv, float gm1, float *Gout) {
+                                          float lam, float adv, float gm1, float4 *xw, float *Gout) {
   using TB = Tab<float>;
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
@@ -301,10 +305,23 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
     float U[S];
 #pragma unroll
     for (int c = 0; c < S; c++) U[c] = 0.0f;
+    if constexpr (S > 1) {
+      // the slot set of order k was last read at order k - 2, before every
+      // lane of the group passed the barrier of order k - 1
+      float4 *xb = xw + (k & 1) * 32;
+      xb[base + l] = make_float4(Fprev[0], Fprev[1], S > 2 ? Fprev[S > 2 ? 2 : 0] : 0.0f, 0.0f);
+      __syncwarp(mask);
 #pragma unroll
-    for (int r = 0; r < n; r++)
+      for (int r = 0; r < n; r++) {
+        const float4 f = xb[base + r];
+        const float fr[3] = {f.x, f.y, f.z};
 #pragma unroll
-      for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
+        for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], fr[c], U[c]);
+      }
+    } else {  // a scalar law: one shuffle per node
+#pragma unroll
+      for (int r = 0; r < n; r++) U[0] = fmaf(g1r[r], __shfl_sync(mask, Fprev[0], base + r), U[0]);
+    }
     float acc[S];
     float2 acc2[S];
 #pragma unroll
@@ -704,6 +721,8 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   const bool active = valid && m <= N;
   const int ic = il - 1 + TL::GH;
 
+  // the warps' shuffle-free exchange slots of the one-lane-per-node recursion
+  __shared__ float4 xs[(LPN == 1 && P >= 2 && S > 1) ? NW * 64 : 1];
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int icv = valid ? ic : 0;
   const int ps = select_order<P, S, true, LPN>(nullptr, &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW, l, grp,
@@ -716,14 +735,14 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     if (ps == 4) {
       if constexpr (P >= 4) {
         if constexpr (LPN == 2) cat_delta2<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-        else cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+        else cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
       }
     } else if (ps == 3) {
       if constexpr (P >= 3) {
         if constexpr (LPN == 2) {
           if (l < 12) cat_delta2<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
         } else if (l < 6) {
-          cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+          cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
         }
       }
     } else if (ps == 2) {
@@ -731,7 +750,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
         if constexpr (LPN == 2) {
           if (l < 8) cat_delta2<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
         } else if (l < 4) {
-          cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+          cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
         }
       }
     } else {

@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
   const int grp = lane >> 4, l = lane & 15, base = grp * 16;
   const unsigned gmask = 0xffffu << base;
   constexpr int CS = TW2 * TW2, RS = TW2;
-  constexpr int NPAIR = 2 * (P - 1) * S;
+  constexpr int NPAIR = 2 * S;  // (direction, component): every order p = 2..P at once
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
 
   for (int round = 0; round < NA * NA / 16; round++) {
@@ -676,18 +676,18 @@ __global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
     unsigned rej = 0;
     if (P >= 2) {
       for (int qq = l; qq < NPAIR; qq += 16) {
-        constexpr int PS = (P > 1 ? P - 1 : 1) * S;
-        const int dir = qq / PS, rem = qq - dir * PS;
-        const int p = 2 + rem / S, c = rem - (rem / S) * S;
+        const int dir = qq / S, c = qq - dir * S;
         if (dir == 0 ? !needF : !needG) continue;
-        bool ok;
-        if constexpr (F32)
-          ok = admit32_p(p, &thi[c][ty][tx], &tlo[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps,
-                         a.thr, a.fact_tau[p], a.psi2_mod);
-        else
-          ok = admit64_p(p, q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau[p],
-                         a.psi2_mod);
-        if (!ok) rej |= 1u << (dir * (P - 1) + (p - 2));
+        unsigned r = 0;
+        if constexpr (P >= 2) {
+          if constexpr (F32)
+            r = reject_set32<P>(&thi[c][ty][tx], &tlo[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr,
+                                a.fact_tau, a.psi2_mod);
+          else
+            r = reject_set64<P>(q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau,
+                                a.psi2_mod);
+        }
+        rej |= r << (dir * (P - 1));
       }
       rej = __reduce_or_sync(gmask, rej);
     }
@@ -1070,18 +1070,17 @@ __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
   __syncthreads();
   const double lx = sm.lx, ly = sm.ly;
   // --- order decisions of every (anchor, direction, p, component) ----------
-  constexpr int NPAIR = 2 * (P - 1) * S;
+  constexpr int NPAIR = 2 * S;  // (direction, component): every order p = 2..P at once
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   for (int q = tid; q < NAH * NAH * NPAIR; q += NT) {
     const int an = q / NPAIR, pr = q - an * NPAIR;
-    const int dir = pr / ((P - 1) * S), rem = pr - dir * (P - 1) * S;
-    const int p = 2 + rem / S, c = rem - (rem / S) * S;
+    const int dir = pr / S, c = pr - dir * S;
     const int ax = an % NAH - 1, ay = an / NAH - 1;
     const bool inside = x0 + ax < NXl && y0 + ay < NYl;
     if (!inside || (dir == 0 ? ay < 0 : ax < 0)) continue;
-    const bool ok = admit64_p(p, &sm.tile[c][ay + P][ax + P], dir == 0 ? 1 : TW, c == 0, FC, a.eps, a.thr,
-                              a.fact_tau[p], a.psi2_mod);
-    if (!ok) atomicOr(&sm.rej[an], 1u << (dir * (P - 1) + (p - 2)));
+    const unsigned r = reject_set64<P>(&sm.tile[c][ay + P][ax + P], dir == 0 ? 1 : TW, c == 0, FC, a.eps, a.thr,
+                                       a.fact_tau, a.psi2_mod);
+    if (r) atomicOr(&sm.rej[an], r << (dir * (P - 1)));
   }
   __syncthreads();
   // --- orders, block tasks, FL-CAT2 directions -----------------------------

@@ -92,6 +92,7 @@ struct Tab<float> {
 
 __device__ __forceinline__ long bc_index(long g, long N, int bc) {
   if (bc == ACAT_BC_PERIODIC) {
+    if (g >= 0 && g < N) return g;
     long r = g % N;
     return r < 0 ? r + N : r;
   }

@@ -47,7 +47,7 @@ class _Params(ctypes.Structure):
     _fields_ = [
         ("flux", ctypes.c_int), ("P", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("bc", ctypes.c_int), ("tau_factorial", ctypes.c_int), ("limiter_form", ctypes.c_int),
-        ("psi2_mod", ctypes.c_int), ("lo_flux", ctypes.c_int),
+        ("psi2_mod", ctypes.c_int), ("lo_flux", ctypes.c_int), ("rect_2d", ctypes.c_int),
         ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2), ("cfl", ctypes.c_double),
         ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
         ("y1", ctypes.c_double), ("psi_tol", ctypes.c_double), ("eps", ctypes.c_double),
@@ -75,6 +75,7 @@ class Problem:
     limiter_form: int = 0
     psi2_mod: int = 0   # 1: modified indicator psi~^2 (Sec. 3.2)
     lo_flux: int = 0    # F^lo: 0 Rusanov, 1 global Lax-Friedrichs, 2 HLL
+    rect_2d: int = 0    # 2D: 1 = one rectangular block S_{p1,p2} per anchor (Sec. 4, end)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -93,7 +94,7 @@ class Problem:
         p = _Params()
         p.flux, p.P, p.nx, p.ny, p.bc = self.flux, self.P, self.nx, self.ny, self.bc
         p.tau_factorial, p.limiter_form = self.tau_factorial, self.limiter_form
-        p.psi2_mod, p.lo_flux = self.psi2_mod, self.lo_flux
+        p.psi2_mod, p.lo_flux, p.rect_2d = self.psi2_mod, self.lo_flux, self.rect_2d
         p.gamma = self.gamma
         p.adv[0], p.adv[1] = self.adv
         p.cfl, p.x0, p.x1, p.y0, p.y1 = self.cfl, self.x0, self.x1, self.y0, self.y1
@@ -123,6 +124,8 @@ def lib():
         _lib.or_cat_flux_1d.argtypes = [pp, i, d, ctypes.c_double, ctypes.c_double, d]
         _lib.or_cat_flux_2d.argtypes = [pp, i, d, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, d, d]
+        _lib.or_cat_flux_2d_rect.argtypes = [pp, i, i, d, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, d, d]
         _lib.or_step_1d.argtypes = [pp, d, d, d, i8, d, d]
         _lib.or_fluxes_1d_at.argtypes = [pp, d, ctypes.c_double, i, i32, d, i8]
         _lib.or_step_1d_z.argtypes = [pp, d, d, ctypes.c_double, d, d]
@@ -207,6 +210,19 @@ def cat_flux_2d(prob: Problem, p: int, block, dt: float):
     G = np.zeros(prob.nvars)
     pr = prob._c()
     rc = lib().or_cat_flux_2d(ctypes.byref(pr), p, _dp(b), dt, prob.dx, prob.dy, _dp(F), _dp(G))
+    if rc:
+        raise ValueError(rc)
+    return F, G
+
+
+def cat_flux_2d_rect(prob: Problem, p1: int, p2: int, block, dt: float):
+    """2D CAT fluxes of the rectangular block S_{p1,p2} from block[s, 2p2(y), 2p1(x)]
+    anchored at i: F^{p1} along the row j2 = 0, G^{p2} along the column j1 = 0."""
+    b = _f64(block)
+    F = np.zeros(prob.nvars)
+    G = np.zeros(prob.nvars)
+    pr = prob._c()
+    rc = lib().or_cat_flux_2d_rect(ctypes.byref(pr), p1, p2, _dp(b), dt, prob.dx, prob.dy, _dp(F), _dp(G))
     if rc:
         raise ValueError(rc)
     return F, G

@@ -277,6 +277,16 @@ int or_cat_flux_2d(const or_params *P, int p, const double *ub, double dt, doubl
   return 0;
 }
 
+/* The fluxes of the rectangular block S_{p1,p2} (Sec. 4, end). */
+int or_cat_flux_2d_rect(const or_params *P, int p1, int p2, const double *ub, double dt, double dx,
+                        double dy, double *F, double *G) {
+  if (p1 < 1 || p1 > OR_MAXP || p2 < 1 || p2 > OR_MAXP) return -1;
+  or_tables T;
+  or_fill_tables(&T, p1 > p2 ? p1 : p2);
+  cat_flux_2d_rect_d(P, &T, p1, p2, ub, dt, dx, dy, F, G);
+  return 0;
+}
+
 /* One 1D step. *dt_io > 0 imposes dt; otherwise the CFL dt is computed and
  * returned there. orders: nx+1 codes; psi: (nx+1) x P values psi^1..psi^P
  * (psi^1 the limiter, psi^p the indicators); flux: (nx+1) x s. */

@@ -41,6 +41,9 @@ typedef struct {
                         difference) in place of psi^2                          */
   int lo_flux;       /* robust first-order flux F^lo of Eq. 3.4: 0 Rusanov
                         (local LF), 1 global LF (alpha = dx / dt), 2 HLL        */
+  int rect_2d;       /* 2D stencils: 0 square blocks S_{p1} for F and S_{p2}
+                        for G; 1 one rectangular block S_{p1,p2} per anchor
+                        (Sec. 4, end), with p = 1 for a direction on FL-CAT2  */
   double gamma;      /* ratio of specific heats (Euler)                         */
   double adv[2];     /* linear advection speeds a, b                            */
   double cfl;
@@ -63,6 +66,8 @@ int or_cat_flux_1d(const or_params *P, int p, const double *us, double dt,
                    double dx, double *F);
 int or_cat_flux_2d(const or_params *P, int p, const double *ub, double dt,
                    double dx, double dy, double *F, double *G);
+int or_cat_flux_2d_rect(const or_params *P, int p1, int p2, const double *ub, double dt,
+                        double dx, double dy, double *F, double *G);
 
 int or_step_1d(const or_params *P, const double *u, double *u_out,
                double *dt_io, int8_t *orders, double *psi, double *flux);

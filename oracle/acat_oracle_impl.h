@@ -163,63 +163,66 @@ static void FN(cat_flux_1d)(const or_params *P, const or_tables *T, int p,
 }
 
 /* ---------------------------------------------------------------------------
- * CAT2p numerical fluxes, 2D (Sec. 4: the recursion on the 2p x 2p block
- * S_p anchored at the corner x_{i+1/2}, Eqs. 4.5-4.6).
- *   ub[(c*2p + b)*2p + a] holds u^n_{i+j}, j = (a - p + 1, b - p + 1).
- * F is taken along the row j2 = 0, G along the column j1 = 0.
+ * CAT2p numerical fluxes, 2D (Sec. 4: the recursion on the block anchored at
+ * the corner x_{i+1/2}, Eqs. 4.5-4.6), on the rectangular block S_{p1,p2}:
+ * 2 p1 nodes in x (j1 = -p1+1..p1), 2 p2 nodes in y (j2 = -p2+1..p2).
+ *   ub[(c*2p2 + b)*2p1 + a] holds u^n_{i+j}, j = (a - p1 + 1, b - p2 + 1).
+ * x-derivatives take the 2 p1-point weights of the rows, y-derivatives the
+ * 2 p2-point weights of the columns. The time derivatives take the 2 pm time
+ * nodes r = -pm+1..pm, pm = max(p1, p2), and the recursion runs to k = 2 pm.
+ * F^{p1} is taken along the row j2 = 0 with the sum to k = 2 p1, G^{p2} along
+ * the column j1 = 0 with the sum to k = 2 p2. With p1 = p2 = p this is the
+ * square block S_p of the paper, operation for operation.
  * ------------------------------------------------------------------------- */
-static void FN(cat_flux_2d)(const or_params *P, const or_tables *T, int p,
-                            const R *ub, double dt, double dx, double dy,
-                            R *F, R *G) {
-  const int n = 2 * p, s = or_nvars(P), z = p - 1; /* z: local index of 0 */
+static void FN(cat_flux_2d_rect)(const or_params *P, const or_tables *T, int p1, int p2,
+                                 const R *ub, double dt, double dx, double dy,
+                                 R *F, R *G) {
+  const int n1 = 2 * p1, n2 = 2 * p2, s = or_nvars(P);
+  const int pm = p1 > p2 ? p1 : p2, n = 2 * pm;
+  const int z1 = p1 - 1, z2 = p2 - 1, zt = pm - 1; /* local indices of j1 = 0, j2 = 0, r = 0 */
   R ft[OR_MAXS][OR_MAXN][OR_MAXN], gt[OR_MAXS][OR_MAXN][OR_MAXN]; /* [c][b][a] */
   R nf[OR_MAXS][OR_MAXN][OR_MAXN], ng[OR_MAXS][OR_MAXN][OR_MAXN];
-  static const int L = OR_MAXN;
   R ut[OR_MAXN][OR_MAXS][OR_MAXN][OR_MAXN];
   R st[OR_MAXS], fr[OR_MAXS], gr[OR_MAXS];
-  (void)L;
+  (void)zt;
 
-  for (int b = 0; b < n; b++)
-    for (int a = 0; a < n; a++) {
-      for (int c = 0; c < s; c++) st[c] = ub[(c * n + b) * n + a];
+  for (int b = 0; b < n2; b++)
+    for (int a = 0; a < n1; a++) {
+      for (int c = 0; c < s; c++) st[c] = ub[(c * n2 + b) * n1 + a];
       FN(flux_x)(P, st, fr);
       FN(flux_y)(P, st, gr);
       for (int c = 0; c < s; c++) { ft[c][b][a] = fr[c]; gt[c][b][a] = gr[c]; }
     }
   for (int c = 0; c < s; c++) {
     R a1 = 0.0, a2 = 0.0;
-    for (int l = 0; l < n; l++) {
-      a1 = a1 + T->gh[p][l] * ft[c][z][l];
-      a2 = a2 + T->gh[p][l] * gt[c][l][z];
-    }
+    for (int l = 0; l < n1; l++) a1 = a1 + T->gh[p1][l] * ft[c][z2][l];
+    for (int l = 0; l < n2; l++) a2 = a2 + T->gh[p2][l] * gt[c][l][z1];
     F[c] = a1;
     G[c] = a2;
   }
   double dtk = 1.0, kfact = 1.0;
   for (int k = 2; k <= n; k++) {
-    /* (a) u~^{(k-1)} = -A^{1,j1}_{p,0}(f~^{(k-2)}_{(*,j2)}, dx)
-     *                  -A^{1,j2}_{p,0}(g~^{(k-2)}_{(j1,*)}, dy)           */
-    for (int b = 0; b < n; b++)
-      for (int a = 0; a < n; a++)
+    /* (a) u~^{(k-1)} = -A^{1,j1}_{p1,0}(f~^{(k-2)}_{(*,j2)}, dx)
+     *                  -A^{1,j2}_{p2,0}(g~^{(k-2)}_{(j1,*)}, dy)          */
+    for (int b = 0; b < n2; b++)
+      for (int a = 0; a < n1; a++)
         for (int c = 0; c < s; c++) {
           R sx = 0.0, sy = 0.0;
-          for (int l = 0; l < n; l++) {
-            sx = sx + T->g1[p][a][l] * ft[c][b][l];
-            sy = sy + T->g1[p][b][l] * gt[c][l][a];
-          }
+          for (int l = 0; l < n1; l++) sx = sx + T->g1[p1][a][l] * ft[c][b][l];
+          for (int l = 0; l < n2; l++) sy = sy + T->g1[p2][b][l] * gt[c][l][a];
           ut[k - 1][c][b][a] = -(sx / dx) - (sy / dy);
         }
     dtk = dtk * dt;
     kfact = kfact * k;
-    /* (b), (c) for f and g */
-    for (int b = 0; b < n; b++)
-      for (int a = 0; a < n; a++) {
+    /* (b), (c) for f and g, time nodes r = -pm+1..pm */
+    for (int b = 0; b < n2; b++)
+      for (int a = 0; a < n1; a++) {
         R af[OR_MAXS], ag[OR_MAXS];
         for (int c = 0; c < s; c++) { af[c] = 0.0; ag[c] = 0.0; }
         for (int rr = 0; rr < n; rr++) {
-          const double rdt = (double)(rr - p + 1) * dt;
+          const double rdt = (double)(rr - pm + 1) * dt;
           for (int c = 0; c < s; c++) {
-            R v = ub[(c * n + b) * n + a];
+            R v = ub[(c * n2 + b) * n1 + a];
             double pw = 1.0, lf = 1.0;
             for (int l = 1; l <= k - 1; l++) {
               pw = pw * rdt;
@@ -231,8 +234,8 @@ static void FN(cat_flux_2d)(const or_params *P, const or_tables *T, int p,
           FN(flux_x)(P, st, fr);
           FN(flux_y)(P, st, gr);
           for (int c = 0; c < s; c++) {
-            af[c] = af[c] + T->gk[p][k - 1][rr] * fr[c];
-            ag[c] = ag[c] + T->gk[p][k - 1][rr] * gr[c];
+            af[c] = af[c] + T->gk[pm][k - 1][rr] * fr[c];
+            ag[c] = ag[c] + T->gk[pm][k - 1][rr] * gr[c];
           }
         }
         for (int c = 0; c < s; c++) {
@@ -241,18 +244,28 @@ static void FN(cat_flux_2d)(const or_params *P, const or_tables *T, int p,
         }
       }
     for (int c = 0; c < s; c++)
-      for (int b = 0; b < n; b++)
-        for (int a = 0; a < n; a++) { ft[c][b][a] = nf[c][b][a]; gt[c][b][a] = ng[c][b][a]; }
+      for (int b = 0; b < n2; b++)
+        for (int a = 0; a < n1; a++) { ft[c][b][a] = nf[c][b][a]; gt[c][b][a] = ng[c][b][a]; }
     for (int c = 0; c < s; c++) {
-      R a1 = 0.0, a2 = 0.0;
-      for (int l = 0; l < n; l++) {
-        a1 = a1 + T->gh[p][l] * ft[c][z][l];
-        a2 = a2 + T->gh[p][l] * gt[c][l][z];
+      if (k <= n1) {
+        R a1 = 0.0;
+        for (int l = 0; l < n1; l++) a1 = a1 + T->gh[p1][l] * ft[c][z2][l];
+        F[c] = F[c] + (dtk / kfact) * a1;
       }
-      F[c] = F[c] + (dtk / kfact) * a1;
-      G[c] = G[c] + (dtk / kfact) * a2;
+      if (k <= n2) {
+        R a2 = 0.0;
+        for (int l = 0; l < n2; l++) a2 = a2 + T->gh[p2][l] * gt[c][l][z1];
+        G[c] = G[c] + (dtk / kfact) * a2;
+      }
     }
   }
+}
+
+/* The square block S_p of Eqs. 4.5-4.6. */
+static void FN(cat_flux_2d)(const or_params *P, const or_tables *T, int p,
+                            const R *ub, double dt, double dx, double dy,
+                            R *F, R *G) {
+  FN(cat_flux_2d_rect)(P, T, p, p, ub, dt, dx, dy, F, G);
 }
 
 /* ---------------------------------------------------------------------------
@@ -461,14 +474,18 @@ static void FN(gather_line_2d)(const or_params *P, const R *u, long x, long y, i
     }
 }
 
-static void FN(gather_block_2d)(const or_params *P, const R *u, long x, long y, int p, R *ub) {
-  const int s = or_nvars(P), n = 2 * p;
+static void FN(gather_block_2d_rect)(const or_params *P, const R *u, long x, long y, int p1, int p2, R *ub) {
+  const int s = or_nvars(P), n1 = 2 * p1, n2 = 2 * p2;
   const long NX = P->nx, NY = P->ny;
   for (int c = 0; c < s; c++)
-    for (int b = 0; b < n; b++)
-      for (int a = 0; a < n; a++)
-        ub[(c * n + b) * n + a] =
-            u[((long)c * NY + or_bc_map(P->bc, y - p + 1 + b, NY)) * NX + or_bc_map(P->bc, x - p + 1 + a, NX)];
+    for (int b = 0; b < n2; b++)
+      for (int a = 0; a < n1; a++)
+        ub[(c * n2 + b) * n1 + a] =
+            u[((long)c * NY + or_bc_map(P->bc, y - p2 + 1 + b, NY)) * NX + or_bc_map(P->bc, x - p1 + 1 + a, NX)];
+}
+
+static void FN(gather_block_2d)(const or_params *P, const R *u, long x, long y, int p, R *ub) {
+  FN(gather_block_2d_rect)(P, u, x, y, p, p, ub);
 }
 
 /* 2D interface flux anchored at cell (x, y): dir 0 gives F at (x+1/2, y),
@@ -485,8 +502,21 @@ static int FN(iface_2d)(const or_params *P, const or_tables *T, const R *u, long
   const int ps = or_select(P, T, line_re, LW, ic, 1, NULL);
   R ub[OR_MAXS * OR_MAXN * OR_MAXN], F[OR_MAXS], Gf[OR_MAXS];
   if (ps >= 2) {
-    FN(gather_block_2d)(P, u, x, y, ps, ub);
-    FN(cat_flux_2d)(P, T, ps, ub, dt, dx, dy, F, Gf);
+    if (P->rect_2d) {
+      /* the other direction's order at the same anchor (1 on FL-CAT2) gives
+       * the block's extent across this direction */
+      R oline[OR_MAXS * 2 * OR_MAXP];
+      double oline_re[OR_MAXS * 2 * OR_MAXP];
+      FN(gather_line_2d)(P, u, x, y, 1 - dir, G, oline);
+      for (int q = 0; q < s * LW; q++) oline_re[q] = RE(oline[q]);
+      const int po = or_select(P, T, oline_re, LW, ic, 1, NULL);
+      const int p1 = dir == 0 ? ps : po, p2 = dir == 0 ? po : ps;
+      FN(gather_block_2d_rect)(P, u, x, y, p1, p2, ub);
+      FN(cat_flux_2d_rect)(P, T, p1, p2, ub, dt, dx, dy, F, Gf);
+    } else {
+      FN(gather_block_2d)(P, u, x, y, ps, ub);
+      FN(cat_flux_2d)(P, T, ps, ub, dt, dx, dy, F, Gf);
+    }
     for (int c = 0; c < s; c++) out[c] = dir == 0 ? F[c] : Gf[c];
     return ps;
   }

@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--shape", default="",
                     help="launch shape 'nw,lpn,cps' for the f32_1d and batch_f32 profiling workloads")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "batch_f32", "adjoint", "adjoint_f32"],
+                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "2d_rect", "batch_f32", "adjoint",
+                             "adjoint_f32"],
                     help="profiling runs: one short measurement of a single workload")
     return ap.parse_args()
 
@@ -153,9 +154,23 @@ def cpu_baseline(budget_s: float = 12.0, max_steps: int = 4000) -> dict:
         u, _, _ = O.step_1d(pr, u)
         n += 1
     el = time.perf_counter() - t0
-    return {"value": NX * n / el, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+    cores = O.get_threads()
+    # the same oracle on one core, on a shorter sample
+    O.set_threads(1)
+    try:
+        u1 = c.u0.copy()
+        n1, t1 = 0, time.perf_counter()
+        while n1 < max_steps and time.perf_counter() - t1 < budget_s / 4:
+            u1, _, _ = O.step_1d(pr, u1)
+            n1 += 1
+        el1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(cores)
+    return {"value": NX * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} consecutive FP64 oracle steps of the workload from its initial state "
-                      f"({el:.1f} s, OpenMP over interfaces)"}
+                      f"({el:.1f} s, OpenMP over interfaces)",
+            "one_core": {"value": NX * n1 / el1, "unit": UNIT, "cores": 1,
+                         "sample": f"{n1} consecutive steps from the initial state ({el1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -368,6 +383,56 @@ def measure_2d_hi(torch, acat, W, flops, n, P, steps, K, flush, peak):
     return {"value": n * n * steps / (t * 1e-3), "unit": UNIT, "ms_per_run": t, "steps": steps, "n": n,
             "P": P, "roofline_frac": fl / (t / steps * 1e-3) / peak, "roofline_peak": "fp64",
             "blocks_per_anchor": {str(p): round(blocks[p] / (n * n), 4) for p in blocks},
+            "flcat2_directions": round(flc / (2 * n * n), 4)}
+
+
+def measure_2d_rect(torch, acat, W, flops, n, P, steps, K, flush, peak):
+    """2D Euler four-quadrant data at P = 4 (FP64) with the rectangular
+    stencils S_{p1,p2} (rect_2d = 1), n x n transmissive, CFL 0.4: the data the
+    square blocks cannot run at this order."""
+    import numpy as np
+    c = W.euler2d_quadrants(n=n, seed=SEED, P=P, steps=steps)
+    ctx = acat.Context(**dict(c.problem_kwargs(), rect_2d=1))
+    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    u.copy_(u0)
+    ctx.acat_run(u, 2)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        e0.record(stream)
+        ctx.acat_run(u, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    assert ctx.acat_status() == 0
+    orders = torch.zeros(n * (n + 1) * 2, dtype=torch.int8, device="cuda")
+    tmp = torch.empty_like(u)
+    ctx.acat_step(u, tmp, -1.0, None, None, orders)
+    torch.cuda.synchronize()
+    o = orders.cpu().numpy().astype(np.int64)
+    pF = o[:n * (n + 1)].reshape(n, n + 1)[:, 1:]
+    pG = o[n * (n + 1):].reshape(n + 1, n)[1:, :]
+    blk = (pF >= 2) | (pG >= 2)
+    fl_blocks = 0.0
+    for p1 in range(1, P + 1):
+        for p2 in range(1, P + 1):
+            cnt = int((blk & (pF == p1) & (pG == p2)).sum())
+            if cnt:
+                fl_blocks += cnt * flops.cat2d_rect_flops(p1, p2, W.EULER2D)
+    flc = int((pF == 1).sum() + (pG == 1).sum())
+    fl = fl_blocks + flops.step_flops_2d_tasks({}, flc, n * n, P, W.EULER2D, n * n)
+    rect = int((blk & (pF != pG)).sum())
+    t = min(ms)
+    ctx.close()
+    return {"value": n * n * steps / (t * 1e-3), "unit": UNIT, "ms_per_run": t, "steps": steps, "n": n,
+            "P": P, "roofline_frac": fl / (t / steps * 1e-3) / peak, "roofline_peak": "fp64",
+            "rect_blocks_per_anchor": round(rect / (n * n), 4),
+            "square_blocks_per_anchor": round(int((blk & (pF == pG)).sum()) / (n * n), 4),
             "flcat2_directions": round(flc / (2 * n * n), 4)}
 
 
@@ -676,6 +741,9 @@ def run_ours(args):
         # the high-order 2D step (square blocks, P = 3)
         variants["2d_euler_P3_smooth_1024_f64"] = measure_2d_hi(torch, acat, W, flops, 1024, 3, 10, 2, flush,
                                                                 peak64)
+        # rectangular stencils S_{p1,p2} on four-quadrant data at P = 4
+        variants["2d_euler_P4_quadrants_rect_512_f64"] = measure_2d_rect(torch, acat, W, flops, 512, 4, 4, 2,
+                                                                         flush, peak64)
         # batched: 4096 ragged instances (P = 3), 1000 steps in FP32, and 10 steps of
         # the plain FP64 step for the ratio
         b32 = measure_batch(torch, acat, W, flops, acat.PREC_F32, 1000, 1, flush, peak32)
@@ -746,6 +814,8 @@ def run_single(args):
         out = {"ms": m["ms"]}
     elif args.workload == "2d_p3":
         out = measure_2d_hi(torch, acat, W, flops, 1024, 3, n, 1, flush, 1.0)
+    elif args.workload == "2d_rect":
+        out = measure_2d_rect(torch, acat, W, flops, 512, 4, n, 1, flush, 1.0)
     elif args.workload in ("2d_f32", "2d_f64"):
         f32 = args.workload == "2d_f32"
         out = measure_2d(torch, acat, W, flops, 4096 if f32 else 1024,

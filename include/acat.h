@@ -92,7 +92,15 @@ enum {
  *                 the larger spectral radius), ACAT_LO_GLOBAL_LF (alpha =
  *                 dx / dt), ACAT_LO_HLL (wave-speed bounds: the smaller of the
  *                 two states' smallest eigenvalues, the larger of their
- *                 largest). The adjoint supports ACAT_LO_RUSANOV only. */
+ *                 largest). The adjoint supports ACAT_LO_RUSANOV only.
+ *   rect_2d       2D stencils (Sec. 4, end). 0 (default): the x-flux of order
+ *                 2 p1 from the square block S_{p1}, the y-flux of order 2 p2
+ *                 from S_{p2}. 1: both from one rectangular block S_{p1,p2} of
+ *                 2 p1 x 2 p2 nodes per anchor (a direction on FL-CAT2 counts
+ *                 as p = 1), x-derivatives over its rows, y-derivatives over
+ *                 its columns, time derivatives on 2 max(p1, p2) time levels.
+ *                 FP64 only (UNSUPPORTED for FP32 2D with P >= 2); no effect
+ *                 in 1D. */
 typedef struct {
   int flux;
   int P;
@@ -103,6 +111,7 @@ typedef struct {
   int limiter_form;
   int psi2_mod;
   int lo_flux;
+  int rect_2d;
   double gamma;
   double adv[2];
   double cfl;

@@ -32,6 +32,7 @@ class acat_params(ctypes.Structure):
         ("flux", ctypes.c_int), ("P", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("tau_factorial", ctypes.c_int),
         ("limiter_form", ctypes.c_int), ("psi2_mod", ctypes.c_int), ("lo_flux", ctypes.c_int),
+        ("rect_2d", ctypes.c_int),
         ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2),
         ("cfl", ctypes.c_double), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
         ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("psi_tol", ctypes.c_double),

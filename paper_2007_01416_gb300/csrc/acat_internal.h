@@ -101,6 +101,7 @@ struct Step2DArgs {
   int limiter_form;
   int psi2_mod;
   int lo_flux;
+  int rect_2d;                // 1: rectangular blocks S_{p1,p2} (FP64, high-order kernel)
   int slot;                   // step index mod 3
   double dx, dy, cfl;
   double dt_fixed, t_end;

@@ -88,6 +88,7 @@ int check_params(const acat_params *p) {
   if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return ACAT_ERR_INVALID_ARG;
   if (p->psi2_mod != 0 && p->psi2_mod != 1) return ACAT_ERR_INVALID_ARG;
   if (p->lo_flux < ACAT_LO_RUSANOV || p->lo_flux > ACAT_LO_HLL) return ACAT_ERR_INVALID_ARG;
+  if (p->rect_2d != 0 && p->rect_2d != 1) return ACAT_ERR_INVALID_ARG;
   if ((p->flux == ACAT_FLUX_EULER1D || p->flux == ACAT_FLUX_EULER2D) && !(p->gamma > 1.0))
     return ACAT_ERR_INVALID_ARG;
   const bool is2d = p->ny > 1 || p->flux == ACAT_FLUX_EULER2D;
@@ -95,6 +96,7 @@ int check_params(const acat_params *p) {
     if (p->ny < 2 * (p->P > 2 ? p->P : 2)) return ACAT_ERR_INVALID_ARG;
     if (p->flux != ACAT_FLUX_EULER2D && p->flux != ACAT_FLUX_LINEAR) return ACAT_ERR_UNSUPPORTED;
     if (p->P > 2 && p->precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;  // FP32 2D: P <= 2
+    if (p->rect_2d && p->P >= 2 && p->precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;
     if ((long)p->nx * (long)p->ny > (1l << 31)) return ACAT_ERR_TOO_LARGE;
     return ACAT_OK;
   }
@@ -146,6 +148,7 @@ Step2DArgs base_args2(acat_ctx *c) {
   a.limiter_form = p.limiter_form;
   a.psi2_mod = p.psi2_mod;
   a.lo_flux = p.lo_flux;
+  a.rect_2d = p.rect_2d;
   a.dx = (p.x1 - p.x0) / (double)p.nx;
   a.dy = (p.y1 - p.y0) / (double)p.ny;
   a.cfl = p.cfl;

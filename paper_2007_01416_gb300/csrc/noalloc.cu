@@ -51,6 +51,7 @@ int validate(const acat_params *p) {
   if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return ACAT_ERR_INVALID_ARG;
   if (p->psi2_mod != 0 && p->psi2_mod != 1) return ACAT_ERR_INVALID_ARG;
   if (p->lo_flux < ACAT_LO_RUSANOV || p->lo_flux > ACAT_LO_HLL) return ACAT_ERR_INVALID_ARG;
+  if (p->rect_2d != 0 && p->rect_2d != 1) return ACAT_ERR_INVALID_ARG;
   if (p->flux == ACAT_FLUX_EULER1D && !(p->gamma > 1.0)) return ACAT_ERR_INVALID_ARG;
   if (p->ny != 1 || p->flux == ACAT_FLUX_EULER2D || p->precision != ACAT_PREC_F64)
     return ACAT_ERR_UNSUPPORTED;

@@ -917,6 +917,8 @@ struct Smem2H {
   unsigned rej[NAH * NAH];    // rejected orders: bit dir * (P - 1) + (p - 2)
   unsigned short task[P + 1][2 * NAH * NAH];
   int ntask[P + 1];
+  unsigned rtask[2 * NAH * NAH];  // rectangular blocks: anchor | wants | p1 << 10 | p2 << 13
+  int nrtask;
   double lx, ly;
 };
 
@@ -1044,6 +1046,137 @@ __device__ __forceinline__ void block_tasks(Smem2H<P, FLUX> &sm, const Step2DArg
   }
 }
 
+// The rectangular block tasks (rect_2d): one block S_{p1,p2} of 2 p1 x 2 p2
+// nodes per task, p1 != p2 (a direction on FL-CAT2 counts as p = 1). The
+// recursion of block_tasks with runtime extents: x-derivatives over the
+// 2 p1 nodes of a row, y-derivatives over the 2 p2 nodes of a column, the
+// 2 pm time levels of pm = max(p1, p2), the recursion to k = 2 pm; F sums to
+// k = 2 p1 along the row j2 = 0, G to k = 2 p2 along the column j1 = 0.
+// (2P)^2 threads per task, node (ia, ib) on thread ti (2P)^2 + ib 2P + ia.
+template <int P, int FLUX>
+__device__ __forceinline__ void rect_tasks(Smem2H<P, FLUX> &sm, const Step2DArgs &a, double lx, double ly) {
+  using TB = Tab<double>;
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  constexpr int NM = 2 * P, NN = NM * NM, per = NT / NN;
+  const double gm1 = a.gamma - 1.0, axv = a.adv[0], ayv = a.adv[1];
+  const int nt = sm.nrtask;
+  const int tid = threadIdx.x, ti = tid / NN, node = tid - ti * NN;
+  const int ia = node % NM, ib = node / NM;
+  for (int base = 0; base < nt; base += per) {
+    const bool slot_ok = ti < per && base + ti < nt;
+    const unsigned tk = slot_ok ? sm.rtask[base + ti] : 0u;
+    const int an = (int)(tk & 0xffu);
+    const int p1 = slot_ok ? (int)((tk >> 10) & 7u) : 1, p2 = slot_ok ? (int)((tk >> 13) & 7u) : 1;
+    const int n1 = 2 * p1, n2 = 2 * p2, pm = p1 > p2 ? p1 : p2, n = 2 * pm, zt = pm - 1;
+    const bool act = slot_ok && ia < n1 && ib < n2;
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    double u[S], f0[S], g0[S], Fs[S], Gs[S], arg[NM][S];
+    if (act) {
+      const int tx = ax + P - p1 + 1 + ia, ty = ay + P - p2 + 1 + ib;
+#pragma unroll
+      for (int c = 0; c < S; c++) u[c] = sm.tile[c][ty][tx];
+      PH::flux2(u, f0, g0, axv, ayv, gm1);
+    } else {
+#pragma unroll
+      for (int c = 0; c < S; c++) u[c] = f0[c] = g0[c] = 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      Fs[c] = f0[c];
+      Gs[c] = g0[c];
+      sm.X[tid][c] = f0[c];
+      sm.Y[tid][c] = g0[c];
+    }
+#pragma unroll
+    for (int rr = 0; rr < NM; rr++)
+#pragma unroll
+      for (int c = 0; c < S; c++) arg[rr][c] = u[c];
+#pragma unroll 1
+    for (int k = 2; k <= NM; k++) {
+      __syncthreads();
+      const bool go = act && k <= n;
+      double U[S];
+      if (go) {
+        double Ux[S], Uy[S];
+#pragma unroll
+        for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0;
+#pragma unroll
+        for (int r = 0; r < NM; r++) {
+          if (r < n1) {
+            const double w = TB::g1(p1, ia, r);
+#pragma unroll
+            for (int c = 0; c < S; c++) Ux[c] = fma(w, sm.X[ti * NN + ib * NM + r][c], Ux[c]);
+          }
+          if (r < n2) {
+            const double w = TB::g1(p2, ib, r);
+#pragma unroll
+            for (int c = 0; c < S; c++) Uy[c] = fma(w, sm.Y[ti * NN + r * NM + ia][c], Uy[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < S; c++) U[c] = -(lx * Ux[c]) - ly * Uy[c];
+      }
+      __syncthreads();
+      if (go) {
+        double af[S], ag[S];
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          af[c] = TB::gk(pm, k - 1, zt) * f0[c];
+          ag[c] = TB::gk(pm, k - 1, zt) * g0[c];
+        }
+#pragma unroll
+        for (int rr = 0; rr < NM; rr++) {
+          if (rr >= n || rr == zt) continue;
+          const double cr = TB::taylor(pm, rr, k - 1), wk = TB::gk(pm, k - 1, rr);
+          double fr[S], gr[S];
+#pragma unroll
+          for (int c = 0; c < S; c++) arg[rr][c] = fma(cr, U[c], arg[rr][c]);
+          PH::flux2(arg[rr], fr, gr, axv, ayv, gm1);
+#pragma unroll
+          for (int c = 0; c < S; c++) {
+            af[c] = fma(wk, fr[c], af[c]);
+            ag[c] = fma(wk, gr[c], ag[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          sm.X[tid][c] = af[c];
+          sm.Y[tid][c] = ag[c];
+          if (k <= n1) Fs[c] = fma(TB::invfact(k), af[c], Fs[c]);
+          if (k <= n2) Gs[c] = fma(TB::invfact(k), ag[c], Gs[c]);
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if (ib == p2 - 1) sm.X[tid][c] = TB::gh(p1, ia) * Fs[c];
+        if (ia == p1 - 1) sm.Y[tid][c] = TB::gh(p2, ib) * Gs[c];
+      }
+    }
+    __syncthreads();
+    if (slot_ok && node == 0) {
+      if (tk & WANT_F)
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          double t = 0.0;
+          for (int r = 0; r < n1; r++) t += sm.X[ti * NN + (p2 - 1) * NM + r][c];
+          sm.Fx[ay][ax + 1][c] = t;
+        }
+      if (tk & WANT_G)
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          double t = 0.0;
+          for (int r = 0; r < n2; r++) t += sm.Y[ti * NN + r * NM + (p1 - 1)][c];
+          sm.Gy[ay + 1][ax][c] = t;
+        }
+    }
+    __syncthreads();
+  }
+}
+
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
   using PH = Phys2<FLUX>;
@@ -1060,6 +1193,7 @@ __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
     sm.ly = dt / a.dy;
   }
   if (tid <= P) sm.ntask[tid] = 0;
+  if (tid == 0) sm.nrtask = 0;
   for (int q = tid; q < NAH * NAH; q += NT) sm.rej[q] = 0u;
   const double *uin = static_cast<const double *>(a.u_in);
   for (int q = tid; q < S * CELLS; q += NT) {
@@ -1077,7 +1211,9 @@ __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
     const int dir = pr / S, c = pr - dir * S;
     const int ax = an % NAH - 1, ay = an / NAH - 1;
     const bool inside = x0 + ax < NXl && y0 + ay < NYl;
-    if (!inside || (dir == 0 ? ay < 0 : ax < 0)) continue;
+    // rectangular blocks take both orders of every anchor that has a flux
+    const bool skip = a.rect_2d ? (ax < 0 && ay < 0) : (dir == 0 ? ay < 0 : ax < 0);
+    if (!inside || skip) continue;
     const unsigned r = reject_set64<P>(&sm.tile[c][ay + P][ax + P], dir == 0 ? 1 : TW, c == 0, FC, a.eps, a.thr,
                                        a.fact_tau, a.psi2_mod);
     if (r) atomicOr(&sm.rej[an], r << (dir * (P - 1)));
@@ -1095,7 +1231,12 @@ __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
     if (needF && a.ord_x && (ax >= 0 || gxa == -1)) a.ord_x[gya * (NXl + 1) + (gxa + 1)] = (int8_t)px;
     if (needG && a.ord_y && (ay >= 0 || gya == -1)) a.ord_y[(gya + 1) * NXl + gxa] = (int8_t)py;
     const bool bF = needF && px >= 2, bG = needG && py >= 2;
-    if (bF && bG && px == py) {
+    if (a.rect_2d) {
+      // one block S_{px,py} serves both directions of the anchor
+      const unsigned want = (bF ? WANT_F : 0u) | (bG ? WANT_G : 0u);
+      if (want && px == py) sm.task[px][atomicAdd(&sm.ntask[px], 1)] = (unsigned short)(an | want);
+      else if (want) sm.rtask[atomicAdd(&sm.nrtask, 1)] = (unsigned)an | want | ((unsigned)px << 10) | ((unsigned)py << 13);
+    } else if (bF && bG && px == py) {
       sm.task[px][atomicAdd(&sm.ntask[px], 1)] = (unsigned short)(an | WANT_F | WANT_G);
     } else {
       if (bF) sm.task[px][atomicAdd(&sm.ntask[px], 1)] = (unsigned short)(an | WANT_F);
@@ -1118,6 +1259,7 @@ __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
   block_tasks<2, P, FLUX>(sm, a, lx, ly);
   if constexpr (P >= 3) block_tasks<3, P, FLUX>(sm, a, lx, ly);
   if constexpr (P >= 4) block_tasks<4, P, FLUX>(sm, a, lx, ly);
+  if (a.rect_2d) rect_tasks<P, FLUX>(sm, a, lx, ly);
   // --- update and wave-speed epilogue (Eq. 4.9) ---------------------------
   double mx = 0.0, my = 0.0;
   bool bad = false;
@@ -1171,6 +1313,9 @@ int launch2_hi(const Step2DArgs &a, cudaStream_t st) {
 template <int FLUX, bool F32>
 int launch2_p(int P, const Step2DArgs &a, cudaStream_t st) {
   if (P == 1) return launch2<1, FLUX, F32>(a, st);
+  if constexpr (!F32) {
+    if (P == 2 && a.rect_2d) return launch2_hi<2, FLUX>(a, st);  // blocks S_{2,1}, S_{1,2}
+  }
   if (P == 2) return launch2<2, FLUX, F32>(a, st);
   if constexpr (!F32) {
     if (P == 3) return launch2_hi<3, FLUX>(a, st);

@@ -67,6 +67,20 @@ def cat2d_flops(p: int, flux: int) -> int:
     return nodes * phi + (n - 1) * per_k + 2 * 2 * n * S
 
 
+def cat2d_rect_flops(p1: int, p2: int, flux: int) -> int:
+    """2D block recursion on the rectangular block S_{p1,p2} (2 p1 x 2 p2
+    nodes, 2 max(p1, p2) time levels): per node the x-derivative sum over a
+    row (2 p1 terms), the y-derivative sum over a column (2 p2 terms), the
+    Taylor update, the f/g pair at the levels r != 0 and both time sums."""
+    n1, n2, S = 2 * p1, 2 * p2, NVARS[flux]
+    n = 2 * max(p1, p2)
+    phi = PHI[3] if flux == 3 else 2 * PHI[0]
+    nodes = n1 * n2
+    per_k = nodes * (2 * n1 * S + 2 * n2 * S + 2 * S) + nodes * 2 * S \
+        + nodes * (n - 1) * (2 * S + phi + 4 * S) + nodes * 4 * S
+    return nodes * phi + (n - 1) * per_k + 2 * (n1 + n2) * S
+
+
 def flcat2_2d_flops(flux: int) -> int:
     S, phi = NVARS[flux], PHI[3] if flux == 3 else 2 * PHI[0]
     return 6 * phi + 40 * S + 30

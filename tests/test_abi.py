@@ -51,13 +51,15 @@ def test_params_struct_matches_header(lib):
     p = acat.default_params()
     assert p.P == 2 and p.ny == 1 and p.tau_factorial == 1
     assert abs(p.gamma - 1.4) < 1e-15 and p.eps == 1e-12 and p.psi_tol == 0.1
-    # 10 ints then 10 doubles
-    assert ctypes.sizeof(acat.acat_params) == 10 * 4 + 10 * 8
+    # 11 ints, 4 bytes of padding to the 8-byte alignment of the doubles, 10 doubles
+    assert ctypes.sizeof(acat.acat_params) == 11 * 4 + 4 + 10 * 8
+    assert acat.acat_params.gamma.offset == 48 and p.rect_2d == 0
 
 
 @pytest.mark.parametrize("bad", [dict(P=0), dict(P=5), dict(nx=3, P=2), dict(flux=9), dict(cfl=0.0),
                                  dict(bc=7), dict(psi_tol=1.0), dict(eps=-1.0),
-                                 dict(flux=2, gamma=1.0), dict(x1=-1.0), dict(psi2_mod=2), dict(lo_flux=3)])
+                                 dict(flux=2, gamma=1.0), dict(x1=-1.0), dict(psi2_mod=2), dict(lo_flux=3),
+                                 dict(rect_2d=2)])
 def test_create_rejects_bad_params_without_device(lib, bad):
     # validation runs before any CUDA call
     from paper_2007_01416_gb300 import acat

@@ -120,3 +120,25 @@ def test_rect_step_conserves_and_differs_from_square(oracle):
     assert np.abs(ur - us).max() > 1e-8  # the x-fluxes beside the jump changed
     for c in range(4):
         assert abs(ur[c].sum() - u[c].sum()) < 1e-12 * np.abs(u[c]).sum()
+
+
+@pytest.mark.parametrize("seed", [0, 2])
+def test_rect_keeps_four_quadrant_data_physical_at_P4(oracle, seed):
+    """With square blocks the row and column indicators do not see a jump
+    that crosses the 2p x 2p block transversally, and four-quadrant Euler
+    data at P = 4 goes non-physical in the first step; the rectangular block
+    follows the transverse order and the run stays physical."""
+    c = W.euler2d_quadrants(n=32, seed=seed, P=4)
+
+    def physical(u):
+        rho = u[0]
+        p = 0.4 * (u[3] - 0.5 * (u[1] ** 2 + u[2] ** 2) / rho)
+        return bool(np.all(rho > 0) and np.all(p > 0) and np.all(np.isfinite(u)))
+
+    sq, _, _, _ = oracle.step_2d(oracle.Problem(**c.problem_kwargs()), c.u0)
+    assert not physical(sq)
+    pr = oracle.Problem(**dict(c.problem_kwargs(), rect_2d=1))
+    u = c.u0
+    for _ in range(10):
+        u, _, _, _ = oracle.step_2d(pr, u)
+        assert physical(u)

@@ -193,3 +193,64 @@ def test_full_size_2d_sampled(env, prec):
     gpu = got[:, cy, cx].T
     err = np.abs(gpu - ref).max() / np.abs(un).max()
     assert err < (1e-7 if f32 else 1e-12), err
+
+
+# ---------------------------------------------------------------------------
+# Rectangular stencils S_{p1,p2} (rect_2d = 1): one block of 2 p1 x 2 p2
+# nodes per anchor, in the shared-memory block kernel (FP64, P = 2..4)
+# ---------------------------------------------------------------------------
+RECT_CASES = [("quadrants", 2, 40, 37, 1), ("quadrants", 3, 45, 40, 1), ("quadrants", 4, 40, 44, 0),
+              ("quadrants", 4, 27, 13, 1), ("smooth2d", 3, 50, 61, 0), ("smooth2d", 4, 37, 33, 1),
+              ("transport", 4, 26, 25, 1), ("transport", 3, 30, 28, 0), ("lax_liu_6", 3, 40, 16, 1)]
+
+
+@pytest.mark.parametrize("kind,P,nx,ny,bc", RECT_CASES)
+def test_single_step_2d_rect(env, kind, P, nx, ny, bc):
+    torch, O, acat = env
+    c = _case(kind, P, nx, ny, bc, seed=1)
+    kw = dict(c.problem_kwargs(), rect_2d=1)
+    with acat.Context(**kw) as ctx:
+        out, dt, ox, oy = _step2(env, ctx, c.u0, nx, ny)
+        assert ctx.acat_status() == 0
+    pr = O.Problem(**kw)
+    assert dt == O.dt_cfl(pr, c.u0)
+    ref, _, rox, roy = O.step_2d(pr, c.u0, dt)
+    assert np.array_equal(ox, rox), np.argwhere(ox != rox)[:5]
+    assert np.array_equal(oy, roy), np.argwhere(oy != roy)[:5]
+    err = np.abs(out - ref).max() / max(1.0, np.abs(ref).max())
+    assert err < 1e-12, err
+    if kind == "quadrants":
+        # anchors with p1 != p2 and a block exist (at P = 2 the pairs (2, 1) and
+        # (1, 2)), and there the rectangular block changes the flux
+        px, py = ox[:, :-1], oy[:-1, :]
+        assert np.any(((px >= 2) | (py >= 2)) & (px != py))
+        with acat.Context(**c.problem_kwargs()) as sq:
+            out_sq, _, _, _ = _step2(env, sq, c.u0, nx, ny, dt)
+        assert np.abs(out_sq - out).max() > 1e-10
+
+
+def test_teacher_forced_2d_rect_quadrants(env):
+    """Four-quadrant Euler data at P = 4 with rectangular stencils: 8 steps
+    against the oracle from the GPU state, every state physical (with square
+    blocks the first step already produces negative pressures here)."""
+    torch, O, acat = env
+    c = _case("quadrants", 4, 36, 36, 1, seed=2)
+    kw = dict(c.problem_kwargs(), rect_2d=1)
+    pr = O.Problem(**kw)
+    u = c.u0
+    with acat.Context(**kw) as ctx:
+        for n in range(8):
+            out, dt, ox, oy = _step2(env, ctx, u, c.nx, c.ny)
+            assert ctx.acat_status() == 0, n
+            ref, _, rox, roy = O.step_2d(pr, u, dt)
+            assert np.array_equal(ox, rox) and np.array_equal(oy, roy), n
+            assert np.abs(out - ref).max() / np.abs(ref).max() < 1e-12, n
+            u = out
+
+
+def test_rect_2d_fp32_is_refused(env):
+    torch, O, acat = env
+    c = _case("quadrants", 2, 20, 20, 1)
+    with pytest.raises(acat.AcatError) as ei:
+        acat.Context(**dict(c.problem_kwargs(), rect_2d=1), precision=acat.PREC_F32)
+    assert ei.value.code == -5

@@ -274,11 +274,15 @@ __device__ __forceinline__ void cat2d_f64(const double *q, int cs, int rs, int l
 }
 
 // FP32 block recursion in the delta formulation about the anchor state u_a:
-// returns G_F = F - f(u_a) and G_G = G - g(u_a).
+// returns G_F = F - f(u_a) and G_G = G - g(u_a). xw: the warp's 128 exchange
+// slots in shared memory (two sets of 2 x 32 used alternately by k), through
+// which a system's nodes read the F^(k-2) of their row and the G^(k-2) of
+// their column: two 16-byte stores and 2 x 2p 16-byte loads per lane and
+// order instead of 2 x 2p s shuffles (scalar laws shuffle).
 template <int p, int FLUX>
 __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int cs, int rs, int l,
                                           int base, float lx, float ly, float ax, float ay, float gm1,
-                                          float *GFo, float *GGo) {
+                                          float4 *xw, float *GFo, float *GGo) {
   using TB = Tab<float>;
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
@@ -321,13 +325,31 @@ __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int 
     float Ux[S], Uy[S];
 #pragma unroll
     for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0f;
+    if constexpr (S > 1) {
+      // the slot set of order k was last read at order k - 2, before every
+      // lane of the block passed the barrier of order k - 1
+      float4 *xb = xw + (k & 1) * 64;
+      xb[base + l] = make_float4(Pf[0], Pf[1], S > 2 ? Pf[S > 2 ? 2 : 0] : 0.0f, S > 3 ? Pf[S > 3 ? 3 : 0] : 0.0f);
+      xb[32 + base + l] =
+          make_float4(Pg[0], Pg[1], S > 2 ? Pg[S > 2 ? 2 : 0] : 0.0f, S > 3 ? Pg[S > 3 ? 3 : 0] : 0.0f);
+      __syncwarp(mask);
 #pragma unroll
-    for (int r = 0; r < n; r++)
+      for (int r = 0; r < n; r++) {
+        const float4 f = xb[base + b1 * n + r], g = xb[32 + base + r * n + a1];
+        const float fr[4] = {f.x, f.y, f.z, f.w}, gr[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-      for (int c = 0; c < S; c++) {
-        Ux[c] = fmaf(gx[r], __shfl_sync(mask, Pf[c], base + b1 * n + r), Ux[c]);
-        Uy[c] = fmaf(gy[r], __shfl_sync(mask, Pg[c], base + r * n + a1), Uy[c]);
+        for (int c = 0; c < S; c++) {
+          Ux[c] = fmaf(gx[r], fr[c], Ux[c]);
+          Uy[c] = fmaf(gy[r], gr[c], Uy[c]);
+        }
       }
+    } else {
+#pragma unroll
+      for (int r = 0; r < n; r++) {
+        Ux[0] = fmaf(gx[r], __shfl_sync(mask, Pf[0], base + b1 * n + r), Ux[0]);
+        Uy[0] = fmaf(gy[r], __shfl_sync(mask, Pg[0], base + r * n + a1), Uy[0]);
+      }
+    }
     float U[S], af[S], ag[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
@@ -658,6 +680,8 @@ __global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
   const double lxd = s_lx, lyd = s_ly;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane >> 4, l = lane & 15, base = grp * 16;
+  // the warps' exchange slots of the FP32 block recursion of systems
+  __shared__ float4 xs2[(F32 && S > 1 && P >= 2) ? (NT / 32) * 128 : 1];
   const unsigned gmask = 0xffffu << base;
   constexpr int CS = TW2 * TW2, RS = TW2;
   constexpr int NPAIR = 2 * S;  // (direction, component): every order p = 2..P at once
@@ -704,7 +728,7 @@ __global__ void __launch_bounds__(NT, F32 ? 2 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
       if constexpr (P >= 2) {
         if constexpr (F32) {
           cat2d_f32<2, FLUX>(&thi[0][ty][tx], &tlo[0][ty][tx], CS, RS, l, base, s_lxf, s_lyf, a.advf[0],
-                             a.advf[1], a.gm1f, F, G);
+                             a.advf[1], a.gm1f, &xs2[warp * 128], F, G);
         } else {
           cat2d_f64<2, FLUX>(q64, CS, RS, l, base, lxd, lyd, a.adv[0], a.adv[1], a.gamma - 1.0, F, G);
         }

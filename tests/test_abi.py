@@ -74,3 +74,11 @@ def test_strerror(lib):
     assert acat.strerror(0) == "ok"
     assert "invalid" in acat.strerror(-1)
     assert acat.strerror(-999) == "unknown error"
+
+
+@pytest.mark.parametrize("kw", [dict(nx=(1 << 30) + 1), dict(flux=3, P=2, nx=1 << 16, ny=(1 << 15) + 1)])
+def test_create_rejects_too_large_without_device(lib, kw):
+    from paper_2007_01416_gb300 import acat
+    p = acat.make_params(**kw)
+    h = ctypes.c_void_p()
+    assert lib.acat_create(ctypes.byref(p), ctypes.byref(h)) == -6 and not h.value

@@ -167,7 +167,9 @@ __device__ __forceinline__ double superbee(double r) {
 // I (1 - thr) >= thr tau, i.e. I >= r tau with r = thr / (1 - thr). The test is
 // first evaluated in float from the first differences d_k = u_{k+1} - u_k,
 // k = -p+1..p-1, each with an absolute error bound e_k:
-//   I_L, I_R, I from the d_k (relative error below 4e-6),
+//   I_L, I_R, I from the d_k (relative error below 4e-6 while the errors
+//   the d_k carry into I_L and I_R stay below 8e-7 of them; undecided
+//   otherwise),
 //   Delta^{2p-1} u = Delta^{2p-2} d by repeated differencing, its bound
 //   propagated as e' = e_{k+1} + e_k + 2^-24 |t'|,
 // and the decision is taken only when the bounds leave no doubt (with a
@@ -255,14 +257,25 @@ __device__ __forceinline__ void psi_filter_all(const float *d, const float *e, f
     }
   }
   unsigned a = 0, u = 0;
-  float il = 0.0f, ir = 0.0f;
+  float il = 0.0f, ir = 0.0f, el = 0.0f, er = 0.0f;
 #pragma unroll
   for (int p = 2; p <= PM; p++) {
     const unsigned bit = 1u << (p - 2);
-    il = fmaf(d[PM - p], d[PM - p], il);
-    ir = fmaf(d[PM + p - 2], d[PM + p - 2], ir);
+    const float dl = d[PM - p], dr = d[PM + p - 2], bl = e[PM - p], br = e[PM + p - 2];
+    il = fmaf(dl, dl, il);
+    ir = fmaf(dr, dr, ir);
+    // bounds of the error that the differences' errors carry into the sums
+    el = fmaf(bl, 2.0f * fabsf(dl) + bl, el);
+    er = fmaf(br, 2.0f * fabsf(dr) + br, er);
     const float IL = il + eps, IR = ir + eps;
     if (!(IL > 1e-30f && IR > 1e-30f) || !(IL < 1e30f && IR < 1e30f)) {
+      u |= bit;
+      continue;
+    }
+    // the relative error of I stays below 4e-6 only while these carried
+    // errors are below 8e-7 of I_L and I_R (differences much smaller than
+    // the rounding of the state, with a small eps): otherwise undecided
+    if (!(el <= 8e-7f * IL && er <= 8e-7f * IR)) {
       u |= bit;
       continue;
     }

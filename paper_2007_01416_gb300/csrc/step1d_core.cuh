@@ -210,7 +210,7 @@ struct DPhys<ACAT_FLUX_EULER1D> {
     Base b;
     b.rho = u[0];
     b.m = u[1];
-    b.v = u[1] * __frcp_rn(u[0]);
+    b.v = u[1] * recip(u[0]);
     const float p = gm1 * fmaf(-0.5f * u[1], b.v, u[2]);
     b.H = u[2] + p;
     b.gm1 = gm1;
@@ -222,7 +222,7 @@ struct DPhys<ACAT_FLUX_EULER1D> {
   //   dp = (gamma - 1)(c - d(mv)/2)
   //   df = (b, d(mv) + dp, dv H + (v + dv)(c + dp))
   __device__ static __forceinline__ void dflux(const Base &B, const float *d, float *df) {
-    const float dv = fmaf(-B.v, d[0], d[1]) * __frcp_rn(B.rho + d[0]);
+    const float dv = fmaf(-B.v, d[0], d[1]) * recip(B.rho + d[0]);
     const float vn = B.v + dv;
     const float dmv = fmaf(B.m, dv, d[1] * vn);
     const float dp = B.gm1 * fmaf(-0.5f, dmv, d[2]);
@@ -234,7 +234,7 @@ struct DPhys<ACAT_FLUX_EULER1D> {
   __device__ static __forceinline__ void dflux_x2(const Base &B, const float2 *d, float2 *df) {
     const float2 t = f2fma(f2dup(-B.v), d[0], d[1]);
     const float2 den = f2add(f2dup(B.rho), d[0]);
-    const float2 dv = f2mul(t, make_float2(__frcp_rn(den.x), __frcp_rn(den.y)));
+    const float2 dv = f2mul(t, make_float2(recip(den.x), recip(den.y)));
     const float2 vn = f2add(f2dup(B.v), dv);
     const float2 dmv = f2fma(f2dup(B.m), dv, f2mul(d[1], vn));
     const float2 dp = f2mul(f2dup(B.gm1), f2fma(f2dup(-0.5f), dmv, d[2]));

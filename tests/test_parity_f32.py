@@ -182,3 +182,26 @@ def test_single_instance_shape_and_autotune(env):
         with pytest.raises(acat.AcatError) as ei:
             ctx.acat_autotune(torch.from_numpy(c.u0).cuda())
         assert ei.value.code == -5
+
+
+@pytest.mark.parametrize("amp", [1e-9, 1e-12])
+def test_orders_with_eps_zero_on_nearly_constant_data(env, amp):
+    """eps = 0 and differences far below the float rounding of the state: the
+    differences carry relative errors too large for the float filter, which
+    must leave the decisions to the literal FP64 evaluation; the order codes
+    equal the oracle's."""
+    torch, O, acat = env
+    nx = 1000
+    x = W.centres(nx, 0.0, 1.0)
+    rho = 1.0 + amp * np.sin(2 * np.pi * x) + 1e-3 * (x > 0.5)
+    u0 = W.prim_to_cons_1d(rho, np.full(nx, 0.25), np.full(nx, 0.7) + amp * np.cos(6 * np.pi * x))
+    kw = dict(flux=W.EULER1D, P=4, nx=nx, ny=1, bc=1, cfl=0.4, x0=0.0, x1=1.0, eps=0.0)
+    pair = acat.to_pair(u0)
+    xval = acat.from_pair(pair)
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        out, dt, orders = _step32(env, ctx, pair, nx)
+    pr = O.Problem(**kw)
+    ref, _, oref = O.step_1d(pr, xval, dt)
+    assert np.array_equal(orders, oref), np.nonzero(orders != oref)
+    err = np.abs(acat.from_pair(out) - ref).max() / np.abs(ref).max()
+    assert err < STEP_TOL, err

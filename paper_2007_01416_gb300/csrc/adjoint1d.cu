@@ -56,7 +56,7 @@ struct Jac<ACAT_FLUX_EULER1D> {
   // df2 = (v (gm1 v^2 / 2 - H), H - gm1 v^2, gamma v), H = (E + p) / rho.
   template <typename R>
   __device__ static void jt(const R *u, const R *y, R *out, R, R gm1) {
-    const R ri = R(1) / u[0];
+    const R ri = recip(u[0]);  // FP64: within an ulp of 1/rho; float: the hardware approximation
     const R v = u[1] * ri;
     const R p = gm1 * (u[2] - R(0.5) * u[1] * v);
     const R H = (u[2] + p) * ri;

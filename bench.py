@@ -342,13 +342,13 @@ def measure_2d(torch, acat, W, flops, n, prec, steps, K, flush, peak):
             "flcat2_directions": round(flc / (2 * n * (n + 1)), 4)}
 
 
-def measure_2d_hi(torch, acat, W, flops, n, P, steps, K, flush, peak):
-    """2D Euler P = 3, 4 (FP64) on smooth data with a contact (the high-order
-    2D step), n x n periodic, CFL 0.4."""
+def measure_2d_hi(torch, acat, W, flops, n, P, steps, K, flush, peak, prec=0):
+    """2D Euler P = 3, 4 on smooth data with a contact (the high-order 2D
+    step), n x n periodic, CFL 0.4; FP64, or FP32 on the compensated state."""
     import numpy as np
     c = W.euler2d_smooth(n=n, seed=SEED, P=P, steps=steps)
-    ctx = acat.Context(**c.problem_kwargs())
-    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    ctx = acat.Context(**c.problem_kwargs(), precision=prec)
+    u0 = torch.from_numpy(acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()).cuda()
     u = torch.empty_like(u0)
     stream = torch.cuda.current_stream()
     u.copy_(u0)
@@ -386,14 +386,14 @@ def measure_2d_hi(torch, acat, W, flops, n, P, steps, K, flush, peak):
             "flcat2_directions": round(flc / (2 * n * n), 4)}
 
 
-def measure_2d_rect(torch, acat, W, flops, n, P, steps, K, flush, peak):
-    """2D Euler four-quadrant data at P = 4 (FP64) with the rectangular
-    stencils S_{p1,p2} (rect_2d = 1), n x n transmissive, CFL 0.4: the data the
-    square blocks cannot run at this order."""
+def measure_2d_rect(torch, acat, W, flops, n, P, steps, K, flush, peak, prec=0):
+    """2D Euler four-quadrant data at P = 4 with the rectangular stencils
+    S_{p1,p2} (rect_2d = 1), n x n transmissive, CFL 0.4: the data the square
+    blocks cannot run at this order; FP64, or FP32 on the compensated state."""
     import numpy as np
     c = W.euler2d_quadrants(n=n, seed=SEED, P=P, steps=steps)
-    ctx = acat.Context(**dict(c.problem_kwargs(), rect_2d=1))
-    u0 = torch.from_numpy(c.u0.copy()).cuda()
+    ctx = acat.Context(**dict(c.problem_kwargs(), rect_2d=1), precision=prec)
+    u0 = torch.from_numpy(acat.to_pair(c.u0) if prec == acat.PREC_F32 else c.u0.copy()).cuda()
     u = torch.empty_like(u0)
     stream = torch.cuda.current_stream()
     u.copy_(u0)
@@ -744,6 +744,14 @@ def run_ours(args):
         # rectangular stencils S_{p1,p2} on four-quadrant data at P = 4
         variants["2d_euler_P4_quadrants_rect_512_f64"] = measure_2d_rect(torch, acat, W, flops, 512, 4, 4, 2,
                                                                          flush, peak64)
+        # the same two high-order 2D workloads in FP32 (compensated state)
+        h32 = measure_2d_hi(torch, acat, W, flops, 1024, 3, 10, 2, flush, peak32, prec=acat.PREC_F32)
+        r32 = measure_2d_rect(torch, acat, W, flops, 512, 4, 4, 2, flush, peak32, prec=acat.PREC_F32)
+        h32["roofline_peak"] = r32["roofline_peak"] = "fp32"
+        h32["speedup_vs_f64"] = h32["value"] / variants["2d_euler_P3_smooth_1024_f64"]["value"]
+        r32["speedup_vs_f64"] = r32["value"] / variants["2d_euler_P4_quadrants_rect_512_f64"]["value"]
+        variants["2d_euler_P3_smooth_1024_f32"] = h32
+        variants["2d_euler_P4_quadrants_rect_512_f32"] = r32
         # batched: 4096 ragged instances (P = 3), 1000 steps in FP32, and 10 steps of
         # the plain FP64 step for the ratio
         b32 = measure_batch(torch, acat, W, flops, acat.PREC_F32, 1000, 1, flush, peak32)

@@ -99,8 +99,7 @@ enum {
  *                 2 p1 x 2 p2 nodes per anchor (a direction on FL-CAT2 counts
  *                 as p = 1), x-derivatives over its rows, y-derivatives over
  *                 its columns, time derivatives on 2 max(p1, p2) time levels.
- *                 FP64 only (UNSUPPORTED for FP32 2D with P >= 2); no effect
- *                 in 1D. */
+ *                 No effect in 1D. */
 typedef struct {
   int flux;
   int P;
@@ -127,8 +126,9 @@ void acat_default_params(acat_params *p);
 /* Validates *p, uploads the differentiation-weight tables (Eq. 2.10; the flux
  * weights of Eq. 2.14 are those that satisfy Eq. 2.11 at k = 1) to the
  * current device and allocates the context's device workspace (dt/time
- * slots, status word). Errors: INVALID_ARG (bad field, nx < 2P, P outside
- * 1..4, 2D with P > 2 or non-Euler/linear flux), UNSUPPORTED, NOMEM, CUDA. */
+ * slots, status word). Errors: INVALID_ARG (bad field, nx or ny < 2 max(P, 2),
+ * P outside 1..4), UNSUPPORTED (2D with a flux other than Euler or linear
+ * transport), TOO_LARGE, NOMEM, CUDA. */
 int acat_create(const acat_params *p, acat_ctx **out);
 
 /* A batch of n_inst independent 1D problems of ragged sizes n_per_inst[b]

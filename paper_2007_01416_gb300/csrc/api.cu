@@ -95,8 +95,7 @@ int check_params(const acat_params *p) {
   if (is2d) {
     if (p->ny < 2 * (p->P > 2 ? p->P : 2)) return ACAT_ERR_INVALID_ARG;
     if (p->flux != ACAT_FLUX_EULER2D && p->flux != ACAT_FLUX_LINEAR) return ACAT_ERR_UNSUPPORTED;
-    if (p->P > 2 && p->precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;  // FP32 2D: P <= 2
-    if (p->rect_2d && p->P >= 2 && p->precision != ACAT_PREC_F64) return ACAT_ERR_UNSUPPORTED;
+
     if ((long)p->nx * (long)p->ny > (1l << 31)) return ACAT_ERR_TOO_LARGE;
     return ACAT_OK;
   }

@@ -1327,6 +1327,321 @@ int launch2(const Step2DArgs &a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// 2D step for P = 3, 4 in FP32, and the rectangular stencils in FP32 at
+// P = 2..4: the structure of k_step2d_hi on the compensated state. Every
+// block task (square or rectangular) runs one thread per node on a
+// (2P)^2-thread slot with runtime extents 2 p1 x 2 p2, in the delta
+// formulation of the P <= 2 FP32 kernel: node j carries increments about the
+// anchor state u_a, f(u_j) - f(u_a) from a cancellation-free difference, and
+// every time level's flux increment f(u_j + del) - f(u_j) likewise; the
+// fluxes leave as F - f(u_a), G - g(u_a), and the update adds
+// f(u_{i-1}) - f(u_i) itself (TwoSum / Fast2Sum into the pair).
+// ---------------------------------------------------------------------------
+template <int P, int FLUX>
+struct Smem2HF {
+  static constexpr int S = Phys2<FLUX>::S;
+  static constexpr int TW = TXH + 2 * P;
+  float thi[S][TW][TW], tlo[S][TW][TW];
+  float Fx[TXH][TXH + 1][S];
+  float Gy[TXH + 1][TXH][S];
+  float X[NT][S], Y[NT][S];   // F^(k), G^(k) increments of the nodes of a round
+  unsigned rej[NAH * NAH];    // rejected orders: bit dir * (P - 1) + (p - 2)
+  unsigned task[2 * NAH * NAH];  // anchor | wants | p1 << 10 | p2 << 13
+  int ntask;
+  float lx, ly;
+};
+
+template <int P, int FLUX>
+__device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step2DArgs &a, float lx, float ly) {
+  using TB = Tab<float>;
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  constexpr int NM = 2 * P, NN = NM * NM, per = NT / NN;
+  const float gm1 = a.gm1f, axv = a.advf[0], ayv = a.advf[1];
+  const int nt = sm.ntask;
+  const int tid = threadIdx.x, ti = tid / NN, node = tid - ti * NN;
+  const int ia = node % NM, ib = node / NM;
+  for (int base = 0; base < nt; base += per) {
+    const bool slot_ok = ti < per && base + ti < nt;
+    const unsigned tk = slot_ok ? sm.task[base + ti] : 0u;
+    const int an = (int)(tk & 0xffu);
+    const int p1 = slot_ok ? (int)((tk >> 10) & 7u) : 1, p2 = slot_ok ? (int)((tk >> 13) & 7u) : 1;
+    const int n1 = 2 * p1, n2 = 2 * p2, pm = p1 > p2 ? p1 : p2, n = 2 * pm, zt = pm - 1;
+    const bool act = slot_ok && ia < n1 && ib < n2;
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    float Ff[S], Fg[S], dels[NM][S];
+    typename PH::Base bj;
+    if (act) {
+      const int tx = ax + P - p1 + 1 + ia, ty = ay + P - p2 + 1 + ib;
+      float ua[S], uj[S], d0[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        ua[c] = sm.thi[c][ay + P][ax + P];
+        uj[c] = sm.thi[c][ty][tx];
+        d0[c] = (sm.thi[c][ty][tx] - sm.thi[c][ay + P][ax + P]) + (sm.tlo[c][ty][tx] - sm.tlo[c][ay + P][ax + P]);
+      }
+      PH::dflux2(PH::base(ua, axv, ayv, gm1), d0, Ff, Fg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
+      bj = PH::base(uj, axv, ayv, gm1);
+    } else {
+      float z[S];
+#pragma unroll
+      for (int c = 0; c < S; c++) z[c] = Ff[c] = Fg[c] = 0.0f;
+      bj = PH::base(z, axv, ayv, gm1);
+    }
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      sm.X[tid][c] = Ff[c];
+      sm.Y[tid][c] = Fg[c];
+    }
+#pragma unroll
+    for (int rr = 0; rr < NM; rr++)
+#pragma unroll
+      for (int c = 0; c < S; c++) dels[rr][c] = 0.0f;
+#pragma unroll 1
+    for (int k = 2; k <= NM; k++) {
+      __syncthreads();
+      const bool go = act && k <= n;
+      float U[S];
+      if (go) {
+        float Ux[S], Uy[S];
+#pragma unroll
+        for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0f;
+#pragma unroll
+        for (int r = 0; r < NM; r++) {
+          if (r < n1) {
+            const float w = TB::g1(p1, ia, r);
+#pragma unroll
+            for (int c = 0; c < S; c++) Ux[c] = fmaf(w, sm.X[ti * NN + ib * NM + r][c], Ux[c]);
+          }
+          if (r < n2) {
+            const float w = TB::g1(p2, ib, r);
+#pragma unroll
+            for (int c = 0; c < S; c++) Uy[c] = fmaf(w, sm.Y[ti * NN + r * NM + ia][c], Uy[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < S; c++) U[c] = -(lx * Ux[c]) - ly * Uy[c];
+      }
+      __syncthreads();
+      if (go) {
+        float af[S], ag[S];
+#pragma unroll
+        for (int c = 0; c < S; c++) af[c] = ag[c] = 0.0f;
+#pragma unroll
+        for (int rr = 0; rr < NM; rr++) {
+          if (rr >= n || rr == zt) continue;
+          const float cr = TB::taylor(pm, rr, k - 1), wk = TB::gk(pm, k - 1, rr);
+          float ef[S], eg[S];
+#pragma unroll
+          for (int c = 0; c < S; c++) dels[rr][c] = fmaf(cr, U[c], dels[rr][c]);
+          PH::dflux2(bj, dels[rr], ef, eg);  // f(u_j + del) - f(u_j): the level's weights sum to 0
+#pragma unroll
+          for (int c = 0; c < S; c++) {
+            af[c] = fmaf(wk, ef[c], af[c]);
+            ag[c] = fmaf(wk, eg[c], ag[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          sm.X[tid][c] = af[c];
+          sm.Y[tid][c] = ag[c];
+          if (k <= n1) Ff[c] = fmaf(TB::invfact(k), af[c], Ff[c]);
+          if (k <= n2) Fg[c] = fmaf(TB::invfact(k), ag[c], Fg[c]);
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if (ib == p2 - 1) sm.X[tid][c] = TB::gh(p1, ia) * Ff[c];
+        if (ia == p1 - 1) sm.Y[tid][c] = TB::gh(p2, ib) * Fg[c];
+      }
+    }
+    __syncthreads();
+    if (slot_ok && node == 0) {
+      if (tk & WANT_F)
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          float t = 0.0f;
+          for (int r = 0; r < n1; r++) t += sm.X[ti * NN + (p2 - 1) * NM + r][c];
+          sm.Fx[ay][ax + 1][c] = t;
+        }
+      if (tk & WANT_G)
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+          float t = 0.0f;
+          for (int r = 0; r < n2; r++) t += sm.Y[ti * NN + r * NM + (p1 - 1)][c];
+          sm.Gy[ay + 1][ax][c] = t;
+        }
+    }
+    __syncthreads();
+  }
+}
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
+  using PH = Phys2<FLUX>;
+  constexpr int S = PH::S;
+  constexpr int TW = Smem2HF<P, FLUX>::TW;
+  constexpr int CELLS = TW * TW;
+  __shared__ Smem2HF<P, FLUX> sm;
+  __shared__ double s_red[2][NT / 32];
+  const int tid = threadIdx.x;
+  const long NXl = a.NX, NYl = a.NY;
+  const long x0 = (long)blockIdx.x * TXH, y0 = (long)blockIdx.y * TXH;
+  if (tid == 0) {
+    const double dt = step_dt2(a);
+    sm.lx = (float)(dt / a.dx);
+    sm.ly = (float)(dt / a.dy);
+    sm.ntask = 0;
+  }
+  for (int q = tid; q < NAH * NAH; q += NT) sm.rej[q] = 0u;
+  const float *uin = static_cast<const float *>(a.u_in);
+  for (int q = tid; q < S * CELLS; q += NT) {
+    const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW, xx = rem - yy * TW;
+    const long gx = bc2(x0 - P + xx, NXl, a.bc), gy = bc2(y0 - P + yy, NYl, a.bc);
+    const long gi = ((long)c * NYl + gy) * NXl + gx;
+    sm.thi[c][yy][xx] = uin[gi];
+    sm.tlo[c][yy][xx] = uin[(long)S * NYl * NXl + gi];
+  }
+  __syncthreads();
+  const float lx = sm.lx, ly = sm.ly;
+  // --- order decisions: every (anchor, direction, component), all orders at once
+  constexpr int NPAIR = 2 * S;
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  for (int q = tid; q < NAH * NAH * NPAIR; q += NT) {
+    const int an = q / NPAIR, pr = q - an * NPAIR;
+    const int dir = pr / S, c = pr - dir * S;
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    const bool inside = x0 + ax < NXl && y0 + ay < NYl;
+    const bool skip = a.rect_2d ? (ax < 0 && ay < 0) : (dir == 0 ? ay < 0 : ax < 0);
+    if (!inside || skip) continue;
+    const unsigned r = reject_set32<P>(&sm.thi[c][ay + P][ax + P], &sm.tlo[c][ay + P][ax + P], dir == 0 ? 1 : TW,
+                                       c == 0, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
+    if (r) atomicOr(&sm.rej[an], r << (dir * (P - 1)));
+  }
+  __syncthreads();
+  // --- orders, block tasks, FL-CAT2 directions
+  for (int an = tid; an < NAH * NAH; an += NT) {
+    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    const long gxa = x0 + ax, gya = y0 + ay;
+    const bool inside = gxa < NXl && gya < NYl;
+    const bool needF = inside && ay >= 0, needG = inside && ax >= 0;
+    const unsigned rej = sm.rej[an], all = (1u << (P - 1)) - 1u;
+    const unsigned accx = ~rej & all, accy = ~(rej >> (P - 1)) & all;
+    const int px = accx ? (32 - __clz(accx)) + 1 : 1, py = accy ? (32 - __clz(accy)) + 1 : 1;
+    if (needF && a.ord_x && (ax >= 0 || gxa == -1)) a.ord_x[gya * (NXl + 1) + (gxa + 1)] = (int8_t)px;
+    if (needG && a.ord_y && (ay >= 0 || gya == -1)) a.ord_y[(gya + 1) * NXl + gxa] = (int8_t)py;
+    const bool bF = needF && px >= 2, bG = needG && py >= 2;
+    const unsigned ua = (unsigned)an;
+    if (a.rect_2d) {
+      const unsigned want = (bF ? WANT_F : 0u) | (bG ? WANT_G : 0u);
+      if (want) sm.task[atomicAdd(&sm.ntask, 1)] = ua | want | ((unsigned)px << 10) | ((unsigned)py << 13);
+    } else if (bF && bG && px == py) {
+      sm.task[atomicAdd(&sm.ntask, 1)] = ua | WANT_F | WANT_G | ((unsigned)px << 10) | ((unsigned)px << 13);
+    } else {
+      if (bF) sm.task[atomicAdd(&sm.ntask, 1)] = ua | WANT_F | ((unsigned)px << 10) | ((unsigned)px << 13);
+      if (bG) sm.task[atomicAdd(&sm.ntask, 1)] = ua | WANT_G | ((unsigned)py << 10) | ((unsigned)py << 13);
+    }
+    const bool flF = needF && px < 2, flG = needG && py < 2;
+    if (flF || flG) {
+      float F1[S], G1[S];
+      flcat2_2d_f32<FLUX>(&sm.thi[0][ay + P][ax + P], &sm.tlo[0][ay + P][ax + P], CELLS, TW, flF, flG, lx, ly,
+                          a.advf[0], a.advf[1], a.gammaf, a.gm1f, a.limiter_form, a.lo_flux, F1, G1);
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        if (flF) sm.Fx[ay][ax + 1][c] = F1[c];
+        if (flG) sm.Gy[ay + 1][ax][c] = G1[c];
+      }
+    }
+  }
+  __syncthreads();
+  block_tasks_f32<P, FLUX>(sm, a, lx, ly);
+  // --- update on the compensated pair and the wave-speed epilogue (Eq. 4.9)
+  float mx = 0.0f, my = 0.0f;
+  bool bad = false;
+  float *uo = static_cast<float *>(a.u_out);
+  for (int t = tid; t < TXH * TXH; t += NT) {
+    const int cy = t / TXH, cx = t - cy * TXH;
+    const long gx = x0 + cx, gy = y0 + cy;
+    if (gx >= NXl || gy >= NYl) continue;
+    const int tx = cx + P, ty = cy + P;
+    float uc[S], dlx[S], dly[S], Bx[S], By[S], junk[S], hf[S], lf[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      uc[c] = sm.thi[c][ty][tx];
+      dlx[c] = (sm.thi[c][ty][tx - 1] - sm.thi[c][ty][tx]) + (sm.tlo[c][ty][tx - 1] - sm.tlo[c][ty][tx]);
+      dly[c] = (sm.thi[c][ty - 1][tx] - sm.thi[c][ty][tx]) + (sm.tlo[c][ty - 1][tx] - sm.tlo[c][ty][tx]);
+    }
+    const typename PH::Base B = PH::base(uc, a.advf[0], a.advf[1], a.gm1f);
+    PH::dflux2(B, dlx, Bx, junk);  // f(u_{x-1,y}) - f(u)
+    PH::dflux2(B, dly, junk, By);  // g(u_{x,y-1}) - g(u)
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      const float dx_ = __fmul_rn(lx, __fadd_rn(Bx[c], __fsub_rn(sm.Fx[cy][cx][c], sm.Fx[cy][cx + 1][c])));
+      const float dy_ = __fmul_rn(ly, __fadd_rn(By[c], __fsub_rn(sm.Gy[cy][cx][c], sm.Gy[cy + 1][cx][c])));
+      const float d = __fadd_rn(dx_, dy_);
+      const float h = sm.thi[c][ty][tx], w = sm.tlo[c][ty][tx];
+      // TwoSum(h, d), then Fast2Sum with the low part
+      const float s = __fadd_rn(h, d);
+      const float bp = __fsub_rn(s, h);
+      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+      const float w2 = __fadd_rn(w, e);
+      const float hn = __fadd_rn(s, w2);
+      const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
+      const long gi = ((long)c * NYl + gy) * NXl + gx;
+      uo[gi] = hn;
+      uo[(long)S * NYl * NXl + gi] = ln;
+      hf[c] = hn;
+      lf[c] = ln;
+    }
+    const float g = a.gammaf;
+    const float sxf = PH::fspeed(hf, a.advf[0], a.advf[1], g, 0);
+    const float syf = PH::fspeed(hf, a.advf[0], a.advf[1], g, 1);
+    if (!PH::fphysical(hf, g)) {
+      double un[S], sx, sy;
+#pragma unroll
+      for (int c = 0; c < S; c++) un[c] = (double)hf[c] + (double)lf[c];
+      bool ok;
+      PH::speed2(un, a.adv[0], a.adv[1], a.gamma, sx, sy, ok);
+      bad |= !ok;
+    }
+    mx = fmaxf(mx, sxf);
+    my = fmaxf(my, syf);
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  if (lane == 0) {
+    s_red[0][warp] = (double)mx;
+    s_red[1][warp] = (double)my;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double vx = s_red[0][0], vy = s_red[1][0];
+    for (int w = 1; w < NT / 32; w++) {
+      vx = fmax(vx, s_red[0][w]);
+      vy = fmax(vy, s_red[1][w]);
+    }
+    const int zs = (a.slot + 1) % 3;
+    atomic_max_pos(&a.smax[zs * 2 + 0], vx);
+    atomic_max_pos(&a.smax[zs * 2 + 1], vy);
+  }
+}
+
+template <int P, int FLUX>
+int launch2_hi_f32(const Step2DArgs &a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.NX + TXH - 1) / TXH), (unsigned)((a.NY + TXH - 1) / TXH));
+  k_step2d_hi_f32<P, FLUX><<<grid, NT, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
 template <int P, int FLUX>
 int launch2_hi(const Step2DArgs &a, cudaStream_t st) {
   dim3 grid((unsigned)((a.NX + TXH - 1) / TXH), (unsigned)((a.NY + TXH - 1) / TXH));
@@ -1337,11 +1652,14 @@ int launch2_hi(const Step2DArgs &a, cudaStream_t st) {
 template <int FLUX, bool F32>
 int launch2_p(int P, const Step2DArgs &a, cudaStream_t st) {
   if (P == 1) return launch2<1, FLUX, F32>(a, st);
-  if constexpr (!F32) {
+  if constexpr (F32) {
+    if (P == 2 && a.rect_2d) return launch2_hi_f32<2, FLUX>(a, st);  // blocks S_{2,1}, S_{1,2}
+    if (P == 2) return launch2<2, FLUX, F32>(a, st);
+    if (P == 3) return launch2_hi_f32<3, FLUX>(a, st);
+    if (P == 4) return launch2_hi_f32<4, FLUX>(a, st);
+  } else {
     if (P == 2 && a.rect_2d) return launch2_hi<2, FLUX>(a, st);  // blocks S_{2,1}, S_{1,2}
-  }
-  if (P == 2) return launch2<2, FLUX, F32>(a, st);
-  if constexpr (!F32) {
+    if (P == 2) return launch2<2, FLUX, F32>(a, st);
     if (P == 3) return launch2_hi<3, FLUX>(a, st);
     if (P == 4) return launch2_hi<4, FLUX>(a, st);
   }

@@ -248,9 +248,46 @@ def test_teacher_forced_2d_rect_quadrants(env):
             u = out
 
 
-def test_rect_2d_fp32_is_refused(env):
+# FP32 with P >= 3 and the FP32 rectangular stencils: the block kernel in the
+# delta formulation on the compensated state (orders bit-exact, 1e-7 per step)
+F32_HI_CASES = [("smooth2d", 3, 50, 61, 0, 0), ("smooth2d", 4, 37, 33, 1, 0), ("transport", 3, 30, 28, 0, 0),
+                ("transport", 4, 26, 25, 1, 0), ("quadrants", 3, 45, 40, 1, 1), ("quadrants", 4, 40, 44, 0, 1),
+                ("quadrants", 2, 40, 37, 1, 1), ("smooth2d", 3, 25, 27, 1, 1)]
+
+
+@pytest.mark.parametrize("kind,P,nx,ny,bc,rect", F32_HI_CASES)
+def test_single_step_2d_f32_high_order(env, kind, P, nx, ny, bc, rect):
     torch, O, acat = env
-    c = _case("quadrants", 2, 20, 20, 1)
-    with pytest.raises(acat.AcatError) as ei:
-        acat.Context(**dict(c.problem_kwargs(), rect_2d=1), precision=acat.PREC_F32)
-    assert ei.value.code == -5
+    c = _case(kind, P, nx, ny, bc, seed=1)
+    kw = dict(c.problem_kwargs(), rect_2d=rect)
+    pair = acat.to_pair(c.u0)
+    x = acat.from_pair(pair)
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        out, dt, ox, oy = _step2(env, ctx, pair, nx, ny)
+        assert ctx.acat_status() == 0
+    pr = O.Problem(**kw)
+    assert dt == O.dt_cfl(pr, x)
+    ref, _, rox, roy = O.step_2d(pr, x, dt)
+    assert np.array_equal(ox, rox), np.argwhere(ox != rox)[:5]
+    assert np.array_equal(oy, roy), np.argwhere(oy != roy)[:5]
+    err = np.abs(acat.from_pair(out) - ref).max() / max(1.0, np.abs(ref).max())
+    assert err < 1e-7, err
+
+
+def test_teacher_forced_2d_f32_rect_quadrants(env):
+    """FP32 with rectangular stencils on four-quadrant data at P = 4: 6 steps
+    against the oracle from the GPU state (value hi + lo)."""
+    torch, O, acat = env
+    c = _case("quadrants", 4, 32, 30, 1, seed=3)
+    kw = dict(c.problem_kwargs(), rect_2d=1)
+    pr = O.Problem(**kw)
+    pair = acat.to_pair(c.u0)
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        for n in range(6):
+            x = acat.from_pair(pair)
+            out, dt, ox, oy = _step2(env, ctx, pair, c.nx, c.ny)
+            assert ctx.acat_status() == 0, n
+            ref, _, rox, roy = O.step_2d(pr, x, dt)
+            assert np.array_equal(ox, rox) and np.array_equal(oy, roy), n
+            assert np.abs(acat.from_pair(out) - ref).max() / np.abs(ref).max() < 1e-7, n
+            pair = out

@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--shape", default="",
                     help="launch shape 'nw,lpn,cps' for the f32_1d and batch_f32 profiling workloads")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "2d_rect", "batch_f32", "adjoint",
-                             "adjoint_f32"],
+                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "2d_p3_f32", "2d_rect", "batch_f32",
+                             "adjoint", "adjoint_f32"],
                     help="profiling runs: one short measurement of a single workload")
     return ap.parse_args()
 
@@ -824,6 +824,8 @@ def run_single(args):
         out = measure_2d_hi(torch, acat, W, flops, 1024, 3, n, 1, flush, 1.0)
     elif args.workload == "2d_rect":
         out = measure_2d_rect(torch, acat, W, flops, 512, 4, n, 1, flush, 1.0)
+    elif args.workload == "2d_p3_f32":
+        out = measure_2d_hi(torch, acat, W, flops, 1024, 3, n, 1, flush, 1.0, prec=acat.PREC_F32)
     elif args.workload in ("2d_f32", "2d_f64"):
         f32 = args.workload == "2d_f32"
         out = measure_2d(torch, acat, W, flops, 4096 if f32 else 1024,

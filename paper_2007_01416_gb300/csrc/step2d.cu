@@ -1338,6 +1338,17 @@ int launch2(const Step2DArgs &a, cudaStream_t st) {
 // fluxes leave as F - f(u_a), G - g(u_a), and the update adds
 // f(u_{i-1}) - f(u_i) itself (TwoSum / Fast2Sum into the pair).
 // ---------------------------------------------------------------------------
+// The float weight tables in shared memory: the FP32 block tasks index them
+// with per-task orders and a per-thread node, which constant memory serves
+// one address at a time.
+struct TabSF {
+  float g1[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];
+  float gk[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];
+  float taylor[ACAT_MAXP + 1][ACAT_MAXN][ACAT_MAXN];
+  float gh[ACAT_MAXP + 1][ACAT_MAXN];
+  float invfact[ACAT_MAXN + 1];
+};
+
 template <int P, int FLUX>
 struct Smem2HF {
   static constexpr int S = Phys2<FLUX>::S;
@@ -1350,11 +1361,12 @@ struct Smem2HF {
   unsigned task[2 * NAH * NAH];  // anchor | wants | p1 << 10 | p2 << 13
   int ntask;
   float lx, ly;
+  TabSF tab;
 };
 
 template <int P, int FLUX>
 __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step2DArgs &a, float lx, float ly) {
-  using TB = Tab<float>;
+  const TabSF &TB = sm.tab;
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   constexpr int NM = 2 * P, NN = NM * NM, per = NT / NN;
@@ -1410,12 +1422,12 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
 #pragma unroll
         for (int r = 0; r < NM; r++) {
           if (r < n1) {
-            const float w = TB::g1(p1, ia, r);
+            const float w = TB.g1[p1][ia][r];
 #pragma unroll
             for (int c = 0; c < S; c++) Ux[c] = fmaf(w, sm.X[ti * NN + ib * NM + r][c], Ux[c]);
           }
           if (r < n2) {
-            const float w = TB::g1(p2, ib, r);
+            const float w = TB.g1[p2][ib][r];
 #pragma unroll
             for (int c = 0; c < S; c++) Uy[c] = fmaf(w, sm.Y[ti * NN + r * NM + ia][c], Uy[c]);
           }
@@ -1431,7 +1443,7 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
 #pragma unroll
         for (int rr = 0; rr < NM; rr++) {
           if (rr >= n || rr == zt) continue;
-          const float cr = TB::taylor(pm, rr, k - 1), wk = TB::gk(pm, k - 1, rr);
+          const float cr = TB.taylor[pm][rr][k - 1], wk = TB.gk[pm][k - 1][rr];
           float ef[S], eg[S];
 #pragma unroll
           for (int c = 0; c < S; c++) dels[rr][c] = fmaf(cr, U[c], dels[rr][c]);
@@ -1446,8 +1458,8 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
         for (int c = 0; c < S; c++) {
           sm.X[tid][c] = af[c];
           sm.Y[tid][c] = ag[c];
-          if (k <= n1) Ff[c] = fmaf(TB::invfact(k), af[c], Ff[c]);
-          if (k <= n2) Fg[c] = fmaf(TB::invfact(k), ag[c], Fg[c]);
+          if (k <= n1) Ff[c] = fmaf(TB.invfact[k], af[c], Ff[c]);
+          if (k <= n2) Fg[c] = fmaf(TB.invfact[k], ag[c], Fg[c]);
         }
       }
     }
@@ -1455,8 +1467,8 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
     if (act) {
 #pragma unroll
       for (int c = 0; c < S; c++) {
-        if (ib == p2 - 1) sm.X[tid][c] = TB::gh(p1, ia) * Ff[c];
-        if (ia == p1 - 1) sm.Y[tid][c] = TB::gh(p2, ib) * Fg[c];
+        if (ib == p2 - 1) sm.X[tid][c] = TB.gh[p1][ia] * Ff[c];
+        if (ia == p1 - 1) sm.Y[tid][c] = TB.gh[p2][ib] * Fg[c];
       }
     }
     __syncthreads();
@@ -1498,6 +1510,16 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
     sm.ntask = 0;
   }
   for (int q = tid; q < NAH * NAH; q += NT) sm.rej[q] = 0u;
+  {
+    constexpr int NW3 = (ACAT_MAXP + 1) * ACAT_MAXN * ACAT_MAXN;
+    for (int q = tid; q < NW3; q += NT) {
+      (&sm.tab.g1[0][0][0])[q] = (&c_tab.g1f[0][0][0])[q];
+      (&sm.tab.gk[0][0][0])[q] = (&c_tab.gkf[0][0][0])[q];
+      (&sm.tab.taylor[0][0][0])[q] = (&c_tab.taylorf[0][0][0])[q];
+    }
+    for (int q = tid; q < (ACAT_MAXP + 1) * ACAT_MAXN; q += NT) (&sm.tab.gh[0][0])[q] = (&c_tab.ghf[0][0])[q];
+    for (int q = tid; q <= ACAT_MAXN; q += NT) sm.tab.invfact[q] = c_tab.invfactf[q];
+  }
   const float *uin = static_cast<const float *>(a.u_in);
   for (int q = tid; q < S * CELLS; q += NT) {
     const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW, xx = rem - yy * TW;

@@ -2,7 +2,7 @@
 order decisions and limiter as FP64 takes them on hi + lo; the first step's
 dt from an FP64 wave-speed reduction (later steps of a run reduce in float).
 
-Bars (derived in the design doc from the arithmetic): the order codes of one step
+Bars (from the arithmetic of the float path): the order codes of one step
 match the FP64 oracle bit for bit from the same state value hi + lo (the
 decisions are taken in FP64 on that exact value); one step agrees with the
 oracle within 1e-7 of max|u| (float rounding of flux increments, at most

@@ -223,7 +223,9 @@ int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int ns
  * constant: the dt the forward step used) and every discrete choice frozen as
  * the forward step takes it at u_n: the selected orders (Eqs. 3.2-3.3) and,
  * for FL-CAT2 interfaces (Eq. 3.4), the superbee piece, the upwind side or the
- * (component, side) of the limiter minimum, and the Rusanov maximum. All else
+ * (component, side) of the limiter minimum, the Rusanov maximum, and for the
+ * HLL F^lo its branch and the states that give its wave-speed bounds (the
+ * global LF F^lo has alpha = dx / dt, a constant with dt). All else
  * -- the CAT2p recursion of Sec. 2.2, the limiter value inside its piece, the
  * Rusanov speed -- is differentiated. u_n, ubar_np1, ubar_n: device states
  * in the context's layout: FP64 [s][nx]; FP32 compensated pairs
@@ -231,8 +233,7 @@ int acat_run_host(acat_ctx *ctx, const void *u_host_in, void *u_host_out, int ns
  * FP32 reverse sweep runs in float, FL-CAT2 interfaces in FP64 on hi + lo).
  * ubar_n must not alias ubar_np1. Uses a context-owned scratch array
  * ((nx+1) x max(2P,4) x s doubles, allocated on first use).
- * Errors: INVALID_ARG, UNSUPPORTED (2D or batched contexts, lo_flux other than
- * ACAT_LO_RUSANOV), NOMEM, CUDA. */
+ * Errors: INVALID_ARG, UNSUPPORTED (2D or batched contexts), NOMEM, CUDA. */
 int acat_adjoint_step(acat_ctx *ctx, const void *u_n_dev, double dt, const void *ubar_np1_dev,
                       void *ubar_n_dev, void *stream);
 

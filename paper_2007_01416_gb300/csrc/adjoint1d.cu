@@ -38,6 +38,8 @@ struct Jac<ACAT_FLUX_LINEAR> {
     out[0] += a * y[0];
   }
   __device__ static void grad_speed(const double *, double, double *g) { g[0] = 0.0; }
+  // gradients of the smallest and largest eigenvalue (HLL wave-speed bounds)
+  __device__ static void grad_eig(const double *, double, double *gmin, double *gmax) { gmin[0] = gmax[0] = 0.0; }
 };
 
 template <>
@@ -47,6 +49,7 @@ struct Jac<ACAT_FLUX_BURGERS> {
     out[0] += u[0] * y[0];
   }
   __device__ static void grad_speed(const double *u, double, double *g) { g[0] = u[0] < 0.0 ? -1.0 : 1.0; }
+  __device__ static void grad_eig(const double *, double, double *gmin, double *gmax) { gmin[0] = gmax[0] = 1.0; }
 };
 
 template <>
@@ -76,6 +79,22 @@ struct Jac<ACAT_FLUX_EULER1D> {
     g[0] = sg * (-v * ri) + k * (0.5 * gm1 * v * v - p * ri);
     g[1] = sg * ri + k * (-gm1 * v);
     g[2] = k * gm1;
+  }
+  // v -/+ c: grad v = (-v/rho, 1/rho, 0), grad c = k (gm1 v^2/2 - p/rho, -gm1 v, gm1)
+  __device__ static void grad_eig(const double *u, double gamma, double *gmin, double *gmax) {
+    const double gm1 = gamma - 1.0;
+    const double ri = 1.0 / u[0];
+    const double v = u[1] * ri;
+    const double p = gm1 * (u[2] - 0.5 * u[1] * v);
+    const double c = sqrt(gamma * p * ri);
+    const double k = gamma / (2.0 * c) * ri;
+    const double gv[3] = {-v * ri, ri, 0.0};
+    const double gc[3] = {k * (0.5 * gm1 * v * v - p * ri), k * (-gm1 * v), k * gm1};
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      gmin[q] = gv[q] - gc[q];
+      gmax[q] = gv[q] + gc[q];
+    }
   }
 };
 
@@ -297,7 +316,7 @@ __device__ void psi1_grad(const double *q, int cs, int limiter_form, double adv,
 // the cells i-1..i+2 (node 0 <-> i-1).
 template <int FLUX>
 __device__ void flcat2_adj(const double *q, int cs, double lam, double adv, double gamma,
-                           int limiter_form, const double *Fbar, double *ub) {
+                           int limiter_form, int lo_flux, const double *Fbar, double *ub) {
   constexpr int S = Phys<FLUX>::S;
   const double gm1 = gamma - 1.0;
   double u0[S], u1[S], f0[S], f1[S], a0[S], a1[S], t0[S], t1[S];
@@ -320,29 +339,60 @@ __device__ void flcat2_adj(const double *q, int cs, double lam, double adv, doub
   bool ok;
   const double s0 = Phys<FLUX>::speed(u0, adv, gamma, ok), s1 = Phys<FLUX>::speed(u1, adv, gamma, ok);
   const bool right = s1 > s0;
-  const double alpha = right ? s1 : s0;
+  // F^lo: Rusanov (alpha the larger spectral radius), global LF (alpha =
+  // 1/lambda, a constant with dt frozen) or HLL (frozen branch and frozen
+  // argmin / argmax of the eigenvalue bounds)
+  const bool hll = lo_flux == ACAT_LO_HLL, glf = lo_flux == ACAT_LO_GLOBAL_LF;
+  const double alpha = glf ? 1.0 / lam : (right ? s1 : s0);
+  double n0 = 0.0, x0 = 0.0, n1 = 0.0, x1 = 0.0;
+  if (hll) {
+    Phys<FLUX>::eig(u0, adv, gamma, n0, x0);
+    Phys<FLUX>::eig(u1, adv, gamma, n1, x1);
+  }
+  const bool lmin1 = n1 < n0, lmax1 = x1 > x0;
+  const double sl = lmin1 ? n1 : n0, sr = lmax1 ? x1 : x0;
+  const int hcase = !hll ? -1 : (sl >= 0.0 ? 0 : (sr <= 0.0 ? 1 : 2));
   const double w = psi1<FLUX>(q, cs, limiter_form, adv);
   double F1[S], Flo[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     F1[c] = 0.5 * (f0[c] + f1[c]) + 0.25 * ((t0[c] - f0[c]) + (t1[c] - f1[c]));
-    Flo[c] = 0.5 * (f0[c] + f1[c]) - 0.5 * alpha * (u1[c] - u0[c]);
+    if (hcase == 0) Flo[c] = f0[c];
+    else if (hcase == 1) Flo[c] = f1[c];
+    else if (hcase == 2) Flo[c] = (sr * f0[c] - sl * f1[c] + sl * sr * (u1[c] - u0[c])) / (sr - sl);
+    else Flo[c] = 0.5 * (f0[c] + f1[c]) - 0.5 * alpha * (u1[c] - u0[c]);
   }
 #pragma unroll
   for (int k = 0; k < 4 * S; k++) ub[k] = 0.0;
-  double wb = 0.0, alb = 0.0;
+  double wb = 0.0, alb = 0.0, slb = 0.0, srb = 0.0;
   double f0b[S], f1b[S], t0b[S], t1b[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     wb += Fbar[c] * (F1[c] - Flo[c]);
     const double F1b = w * Fbar[c], Flob = (1.0 - w) * Fbar[c];
-    f0b[c] = 0.25 * F1b + 0.5 * Flob;
-    f1b[c] = 0.25 * F1b + 0.5 * Flob;
+    f0b[c] = 0.25 * F1b;
+    f1b[c] = 0.25 * F1b;
     t0b[c] = 0.25 * F1b;
     t1b[c] = 0.25 * F1b;
-    ub[1 * S + c] += 0.5 * alpha * Flob;
-    ub[2 * S + c] -= 0.5 * alpha * Flob;
-    alb -= 0.5 * Flob * (u1[c] - u0[c]);
+    if (hcase == 0) {
+      f0b[c] += Flob;
+    } else if (hcase == 1) {
+      f1b[c] += Flob;
+    } else if (hcase == 2) {
+      const double D = sr - sl, du = u1[c] - u0[c];
+      f0b[c] += sr / D * Flob;
+      f1b[c] -= sl / D * Flob;
+      ub[2 * S + c] += sl * sr / D * Flob;
+      ub[1 * S + c] -= sl * sr / D * Flob;
+      slb += Flob * (-f1[c] + sr * du + Flo[c]) / D;
+      srb += Flob * (f0[c] + sl * du - Flo[c]) / D;
+    } else {
+      f0b[c] += 0.5 * Flob;
+      f1b[c] += 0.5 * Flob;
+      ub[1 * S + c] += 0.5 * alpha * Flob;
+      ub[2 * S + c] -= 0.5 * alpha * Flob;
+      alb -= 0.5 * Flob * (u1[c] - u0[c]);
+    }
   }
   double a0b[S], a1b[S];
 #pragma unroll
@@ -359,10 +409,22 @@ __device__ void flcat2_adj(const double *q, int cs, double lam, double adv, doub
   }
   Jac<FLUX>::jt(u0, f0b, ub + 1 * S, adv, gm1);
   Jac<FLUX>::jt(u1, f1b, ub + 2 * S, adv, gm1);
-  double gs[S];
-  Jac<FLUX>::grad_speed(right ? u1 : u0, gamma, gs);
+  if (lo_flux == ACAT_LO_RUSANOV) {
+    double gs[S];
+    Jac<FLUX>::grad_speed(right ? u1 : u0, gamma, gs);
 #pragma unroll
-  for (int c = 0; c < S; c++) ub[(right ? 2 : 1) * S + c] += alb * gs[c];
+    for (int c = 0; c < S; c++) ub[(right ? 2 : 1) * S + c] += alb * gs[c];
+  }
+  if (hcase == 2) {
+    double gmin[S], gmax[S], gjunk[S];
+    Jac<FLUX>::grad_eig(lmin1 ? u1 : u0, gamma, gmin, gjunk);
+    Jac<FLUX>::grad_eig(lmax1 ? u1 : u0, gamma, gjunk, gmax);
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      ub[(lmin1 ? 2 : 1) * S + c] += slb * gmin[c];
+      ub[(lmax1 ? 2 : 1) * S + c] += srb * gmax[c];
+    }
+  }
   double gw[4 * S];
   psi1_grad<FLUX>(q, cs, limiter_form, adv, gw);
 #pragma unroll
@@ -450,7 +512,7 @@ __global__ void __launch_bounds__(NWF * 32) k_adj1d(const Step1DArgs a, const do
     }
   } else if (l == 0) {
     double ub[4 * S];
-    flcat2_adj<FLUX>(q0, TL::TW, lam, a.adv, a.gamma, a.limiter_form, Fb, ub);
+    flcat2_adj<FLUX>(q0, TL::TW, lam, a.adv, a.gamma, a.limiter_form, a.lo_flux, Fb, ub);
     for (int s = 0; s < NS; s++) {
       const int node = s - NS / 2 + 1;  // -1..2 carry values
 #pragma unroll
@@ -597,7 +659,7 @@ __global__ void __launch_bounds__(NWF * 32) k_adj1d_f32(const Step1DArgs a, cons
     for (int c = 0; c < S; c++)
 #pragma unroll
       for (int k = 0; k < 4; k++) qd[c][k] = (double)thi[c][ic - 1 + k] + (double)tlo[c][ic - 1 + k];
-    flcat2_adj<FLUX>(&qd[0][1], 4, lamd, a.adv, a.gamma, a.limiter_form, Fbd, ub);
+    flcat2_adj<FLUX>(&qd[0][1], 4, lamd, a.adv, a.gamma, a.limiter_form, a.lo_flux, Fbd, ub);
     for (int s = 0; s < NS; s++) {
       const int node = s - NS / 2 + 1;
 #pragma unroll

@@ -762,7 +762,7 @@ int adjoint_launch(acat_ctx *c, const void *u_n, double dt, const double *dt_dev
   return e ? ACAT_ERR_CUDA : ACAT_OK;
 }
 
-bool adjoint_ctx(const acat_ctx *c) { return c->dim == 1 && !c->batched && c->p.lo_flux == ACAT_LO_RUSANOV; }
+bool adjoint_ctx(const acat_ctx *c) { return c->dim == 1 && !c->batched; }
 
 }  // namespace
 

@@ -163,13 +163,23 @@ def test_batched_variants_equal_single_runs(env):
             assert np.array_equal(got[:, offs[b]:offs[b + 1]], v.cpu().numpy()), b
 
 
-def test_adjoint_with_psi2_mod_and_refusal_of_other_lo_flux(env):
+@pytest.mark.parametrize("mod,lo,kind", [(1, 0, "euler"), (0, 1, "euler"), (0, 2, "euler"), (1, 2, "euler"),
+                                         (0, 2, "burgers"), (0, 1, "burgers")])
+def test_adjoint_with_variants(env, mod, lo, kind):
+    """J^T of one step with psi~^2 and the F^lo variants (global LF, HLL)
+    against the complex-step Jacobian of the oracle (its discrete choices,
+    the HLL branch and bounds among them, taken on real parts)."""
     torch, O, acat = env
-    c = W.euler1d_riemann_entropy(nx=24, seed=0, P=2)
-    kw = dict(c.problem_kwargs(), psi2_mod=1)
+    if kind == "euler":
+        c = W.euler1d_riemann_entropy(nx=24, seed=0, P=2)
+    else:
+        c = _case1("burgers", 2, 24, 1)
+    kw = dict(c.problem_kwargs(), psi2_mod=mod, lo_flux=lo)
     pr = O.Problem(**kw)
     u = c.u0
     dt = O.dt_cfl(pr, u)
+    _, _, orders = O.step_1d(pr, u, dt)
+    assert np.any(orders == 1)  # FL-CAT2 interfaces, where F^lo enters
     h = 1e-30
     J = np.zeros((u.size, u.size))
     for k in range(u.size):
@@ -185,8 +195,3 @@ def test_adjoint_with_psi2_mod_and_refusal_of_other_lo_flux(env):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-10
-    with acat.Context(**dict(kw, lo_flux=2)) as ctx:
-        out = torch.empty(u.shape, dtype=torch.float64, device="cuda")
-        with pytest.raises(acat.AcatError) as ei:
-            ctx.acat_adjoint_step(torch.from_numpy(u.copy()).cuda(), dt, torch.from_numpy(w).cuda(), out)
-        assert ei.value.code == -5

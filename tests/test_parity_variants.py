@@ -2,8 +2,8 @@
 indicator psi~^2 (Sec. 3.2; order codes bit-exact, decided by the same
 filtered/literal scheme as psi^p) and the F^lo fluxes of FL-CAT2 (global
 Lax-Friedrichs, HLL), in 1D FP64/FP32, 2D FP64/FP32, the batched step and the
-adjoint (psi~^2 only: the adjoint refuses F^lo other than Rusanov). Bars as
-for the default variants: 1e-12 (FP64) and 1e-7 (FP32) of max|u| per step.
+adjoint (J^T against the oracle's complex-step Jacobian, 1e-10). Bars as for
+the default variants: 1e-12 (FP64) and 1e-7 (FP32) of max|u| per step.
 """
 import numpy as np
 import pytest

@@ -436,6 +436,29 @@ def measure_2d_rect(torch, acat, W, flops, n, P, steps, K, flush, peak, prec=0):
             "flcat2_directions": round(flc / (2 * n * n), 4)}
 
 
+def f32_error(torch, acat, kw, u0, steps, sizes=None):
+    """L1 and Linf of an FP32 run (compensated state) against the FP64 run of
+    the same workload, `steps` steps from the same initial state, relative to
+    the FP64 state's mean |u| and max |u|. The FP64 path matches the oracle
+    within 1e-12 per step."""
+    import numpy as np
+    extra = {} if sizes is None else {"sizes": sizes}
+    c64 = acat.Context(**kw, **extra)
+    c32 = acat.Context(**kw, precision=acat.PREC_F32, **extra)
+    u64 = torch.from_numpy(np.ascontiguousarray(u0, dtype=np.float64)).cuda()
+    u32 = torch.from_numpy(acat.to_pair(u0)).cuda()
+    c64.acat_run(u64, steps)
+    c32.acat_run(u32, steps)
+    torch.cuda.synchronize()
+    assert c64.acat_status() == 0 and c32.acat_status() == 0
+    d = (acat.from_pair(u32) - u64).abs()
+    out = {"steps": steps, "l1_rel_vs_f64": float(d.mean() / u64.abs().mean()),
+           "linf_rel_vs_f64": float(d.max() / u64.abs().max())}
+    c64.close()
+    c32.close()
+    return out
+
+
 def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak, shape=None):
     """4096 independent 1D Euler instances, N uniform in [256, 16384], P = 3,
     one persistent launch per step."""
@@ -484,7 +507,7 @@ def measure_batch(torch, acat, W, flops, prec, steps, K, flush, peak, shape=None
             "order_mix": {str(k): round(h[k] / (M + len(sizes)), 4) for k in range(1, 5)}}
 
 
-def measure_adjoint(torch, acat, W, K, flush, steps=2000, prec=0):
+def measure_adjoint(torch, acat, W, K, flush, steps=2000, prec=0, grad_out=None):
     """Gradient of the L2 misfit L = dx/2 sum |u^n - u_target|^2 for the 1D
     Euler acoustic pulse (P = 2, N = 8192, periodic, 2000 steps, target from a
     second seed): the recorded forward run plus the reverse run (recompute per
@@ -550,6 +573,11 @@ def measure_adjoint(torch, acat, W, K, flush, steps=2000, prec=0):
         torch.cuda.synchronize()
         ta.append(e0.elapsed_time(e1))
     launches = ctx.launch_count() - l0
+    if grad_out is not None:  # dL/du^0 of the last gradient run, as FP64 values
+        ctx.acat_run_record(u0, uN, n, every, ckpt, dts)
+        seed(g)
+        ctx.acat_adjoint_run(ckpt, dts, n, every, g, g)
+        grad_out.append(acat.from_pair(g) if f32 else g.clone())
     ctx.close()
     t_f, t_g, t_a = min(tf), min(tr), min(ta)
     recompute = (n - len(ckpt)) * t_f / n
@@ -736,6 +764,9 @@ def run_ours(args):
         v32["roofline_peak"] = "fp32"
         v64["roofline_peak"] = "fp64"
         v32["speedup_vs_f64_per_cell_update"] = v32["value"] / v64["value"]
+        c2 = W.euler2d_quadrants(n=4096, seed=SEED, P=2, steps=500, cfl=CFL)
+        v32["accuracy"] = f32_error(torch, acat, c2.problem_kwargs(), c2.u0, 10)
+        del c2
         variants["2d_euler_P2_4096_f32"] = v32
         variants["2d_euler_P2_1024_f64"] = v64
         # the high-order 2D step (square blocks, P = 3)
@@ -748,6 +779,10 @@ def run_ours(args):
         h32 = measure_2d_hi(torch, acat, W, flops, 1024, 3, 10, 2, flush, peak32, prec=acat.PREC_F32)
         r32 = measure_2d_rect(torch, acat, W, flops, 512, 4, 4, 2, flush, peak32, prec=acat.PREC_F32)
         h32["roofline_peak"] = r32["roofline_peak"] = "fp32"
+        ch = W.euler2d_smooth(n=1024, seed=SEED, P=3, steps=10)
+        h32["accuracy"] = f32_error(torch, acat, ch.problem_kwargs(), ch.u0, 10)
+        cr = W.euler2d_quadrants(n=512, seed=SEED, P=4, steps=4)
+        r32["accuracy"] = f32_error(torch, acat, dict(cr.problem_kwargs(), rect_2d=1), cr.u0, 4)
         h32["speedup_vs_f64"] = h32["value"] / variants["2d_euler_P3_smooth_1024_f64"]["value"]
         r32["speedup_vs_f64"] = r32["value"] / variants["2d_euler_P4_quadrants_rect_512_f64"]["value"]
         variants["2d_euler_P3_smooth_1024_f32"] = h32
@@ -758,6 +793,12 @@ def run_ours(args):
         b64 = measure_batch(torch, acat, W, flops, acat.PREC_F64, 10, 1, flush, peak64)
         b32["roofline_peak"], b64["roofline_peak"] = "fp32", "fp64"
         b32["speedup_vs_f64_per_cell_update"] = b32["value"] / b64["value"]
+        import numpy as np
+        sizes, states = W.euler1d_batched(n_inst=4096, seed=SEED)
+        b32["accuracy"] = f32_error(torch, acat,
+                                    W.euler1d_riemann_entropy(nx=256, seed=0, P=3, cfl=CFL).problem_kwargs(),
+                                    np.concatenate(states, axis=1), 20, sizes=sizes)
+        del states
         variants["batched_euler_P3_4096inst_f32"] = b32
         variants["batched_euler_P3_4096inst_f64"] = b64
         # gradient through 2000 steps (hand-written adjoint, sqrt(n) checkpoints)
@@ -766,11 +807,20 @@ def run_ours(args):
         lin64 = measure_linear(torch, acat, W, flops, acat.PREC_F64, 4, NX, 1000, 2, flush, peak64)
         lin32 = measure_linear(torch, acat, W, flops, acat.PREC_F32, 4, NX, 1000, 2, flush, peak32)
         lin64["roofline_peak"], lin32["roofline_peak"] = "fp64", "fp32"
+        cl = W.burgers_sine(nx=NX, seed=SEED, P=4, steps=1000)
+        lin32["accuracy"] = f32_error(torch, acat, dict(cl.problem_kwargs(), flux=W.LINEAR, adv=(1.0, 0.0)),
+                                      cl.u0, 1000)
         variants["linear_P4_16384_f64"] = lin64
         variants["linear_P4_16384_f32"] = lin32
-        a64 = measure_adjoint(torch, acat, W, 2, flush)
-        a32 = measure_adjoint(torch, acat, W, 2, flush, prec=acat.PREC_F32)
+        grads = []
+        a64 = measure_adjoint(torch, acat, W, 2, flush, grad_out=grads)
+        a32 = measure_adjoint(torch, acat, W, 2, flush, prec=acat.PREC_F32, grad_out=grads)
         a32["gradient_speedup_vs_f64"] = a64["ms_gradient"] / a32["ms_gradient"]
+        dg = (grads[1] - grads[0]).abs()
+        a32["accuracy"] = {"what": "dL/du0 against the FP64 gradient (each on its own trajectory)",
+                           "l1_rel_vs_f64": float(dg.mean() / grads[0].abs().mean()),
+                           "linf_rel_vs_f64": float(dg.max() / grads[0].abs().max())}
+        del grads, dg
         variants["adjoint_euler_P2_8192_f64"] = a64
         variants["adjoint_euler_P2_8192_f32"] = a32
 

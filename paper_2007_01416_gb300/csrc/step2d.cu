@@ -1425,6 +1425,18 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
     for (int rr = 0; rr < NM; rr++)
 #pragma unroll
       for (int c = 0; c < S; c++) dels[rr][c] = 0.0f;
+    // the derivative weights of the node's row and column, read once per task
+    // at P <= 3 (at P = 4 they would cost the registers of the second CTA per
+    // SM, and the loop reads them from the shared table)
+    constexpr bool HW = P <= 3;
+    float wx[HW ? NM : 1], wy[HW ? NM : 1];
+    if constexpr (HW) {
+#pragma unroll
+      for (int r = 0; r < NM; r++) {
+        wx[r] = act && r < n1 ? TB.g1[p1][ia][r] : 0.0f;
+        wy[r] = act && r < n2 ? TB.g1[p2][ib][r] : 0.0f;
+      }
+    }
 #pragma unroll 1
     for (int k = 2; k <= NM; k++) {
       __syncthreads();
@@ -1437,12 +1449,16 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
 #pragma unroll
         for (int r = 0; r < NM; r++) {
           if (r < n1) {
-            const float w = TB.g1[p1][ia][r];
+            float w;
+            if constexpr (HW) w = wx[r];
+            else w = TB.g1[p1][ia][r];
 #pragma unroll
             for (int c = 0; c < S; c++) Ux[c] = fmaf(w, sm.X[xrow + r][c], Ux[c]);
           }
           if (r < n2) {
-            const float w = TB.g1[p2][ib][r];
+            float w;
+            if constexpr (HW) w = wy[r];
+            else w = TB.g1[p2][ib][r];
 #pragma unroll
             for (int c = 0; c < S; c++) Uy[c] = fmaf(w, sm.Y[ycol + r * SM::YS][c], Uy[c]);
           }

@@ -76,7 +76,8 @@ enum {
  *   bc            ACAT_BC_PERIODIC or ACAT_BC_TRANSMISSIVE (zero-gradient
  *                 ghost cells, the "outflow"/"free" conditions of Sec. 5).
  *   precision     ACAT_PREC_F64, or ACAT_PREC_F32 (float arithmetic on a
- *                 compensated float-pair state; indicators in FP64).
+ *                 compensated float-pair state; the order decisions are
+ *                 those of FP64 on the state value hi + lo).
  *   cfl           CFL number of the dt rule above.
  *   psi_tol       p is admissible when psi^p >= 1 - psi_tol (the paper's
  *                 "psi^p ~ 1", Eq. 3.2, has no threshold; default 0.1).
@@ -92,7 +93,7 @@ enum {
  *                 the larger spectral radius), ACAT_LO_GLOBAL_LF (alpha =
  *                 dx / dt), ACAT_LO_HLL (wave-speed bounds: the smaller of the
  *                 two states' smallest eigenvalues, the larger of their
- *                 largest). The adjoint supports ACAT_LO_RUSANOV only.
+ *                 largest).
  *   rect_2d       2D stencils (Sec. 4, end). 0 (default): the x-flux of order
  *                 2 p1 from the square block S_{p1}, the y-flux of order 2 p2
  *                 from S_{p2}. 1: both from one rectangular block S_{p1,p2} of

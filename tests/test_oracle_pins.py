@@ -517,3 +517,81 @@ def test_2d_local_error_order_transport(oracle, P):
         errs.append(np.abs(un[0] - f(x - dt + 0 * y, y - dt + 0 * x))[ok].max())
     rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(2)]
     assert rates[-1] > 2 * P + 1 - 0.6, (errs, rates)
+
+
+# ---------------------------------------------------------------------------
+# The limiter psi^1 (Eqs. 3.5-3.7): superbee values at chosen ratios
+# ---------------------------------------------------------------------------
+# superbee at ratios where its value is known by hand (max(0, min(2r, 1),
+# min(r, 2)) read off its graph): the rising part, the plateau at 1, the
+# second rise and the cap at 2, and negative ratios
+SUPERBEE_AT = [(0.25, 0.5), (0.75, 1.0), (1.5, 1.5), (3.0, 2.0), (-1.0, 0.0), (0.5, 1.0),
+               (2.0, 2.0), (5.0, 2.0), (1.0, 1.0), (-0.25, 0.0), (1.25, 1.25)]
+
+
+def _jumps_for_ratios(ratios, upwind_left):
+    """Cell jumps J_m = u_m - u_{m-1}, m = 1..K+8, such that the upwind ratio
+    at interface m0 + k (between cells m0 + k - 1 and m0 + k) is ratios[k]:
+    J_{m-1} / J_m for a positive speed, J_{m+1} / J_m for a negative one."""
+    K, m0 = len(ratios), 4
+    J = np.full(K + 9, 0.01)
+    if upwind_left:
+        for k, r in enumerate(ratios):
+            J[m0 + k] = J[m0 + k - 1] / r
+    else:
+        # fill from the right: J_m = J_{m+1} / r_m
+        for k in reversed(range(K)):
+            J[m0 + k] = J[m0 + k + 1] / ratios[k]
+    return J, m0
+
+
+@pytest.mark.parametrize("positive", [True, False])
+def test_limiter_superbee_values_roe_side(oracle, positive):
+    """Burgers with P = 1 (FL-CAT2 everywhere): psi^1 at each interface is
+    superbee of the upwind ratio, the side picked by the sign of the Roe
+    speed (Eq. 3.6). Positive states take the left jump, negative states the
+    right one."""
+    ratios = [r for r, _ in SUPERBEE_AT]
+    J, m0 = _jumps_for_ratios(ratios, upwind_left=positive)
+    # u_m - u_{m-1} = J_m (positive states), or -J_m (negative states: the
+    # jumps change sign together, which keeps every ratio)
+    prof = np.concatenate([[0.0], np.cumsum(J[1:])])
+    u = 1.0 + prof if positive else -1.0 - prof
+    assert (u > 0).all() if positive else (u < 0).all()
+    N = u.size
+    pr = prob(oracle, flux=oracle.BURGERS, P=1, nx=N, bc=1, x0=0.0, x1=1.0, cfl=0.4)
+    _, _, orders, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
+    assert (orders[1:N] == 1).all()
+    for k, (_, want) in enumerate(SUPERBEE_AT):
+        assert psi[m0 + k, 0] == pytest.approx(want, rel=1e-12, abs=1e-15), (k, psi[m0 + k, 0])
+
+
+def test_limiter_zero_local_jump(oracle):
+    """Reading of a zero local jump (Eq. 3.5 divides by it): a zero upwind jump
+    gives r = 1 (psi^1 = 1), a positive upwind jump r = +inf (psi^1 = 2), a
+    negative one r = -inf (psi^1 = 0)."""
+    # positive states: the upwind jump is the left one
+    u = np.array([1.0, 1.0, 1.0, 1.0, 1.1, 1.1, 1.1, 1.0, 1.0, 1.0, 1.0, 1.0])
+    N = u.size
+    pr = prob(oracle, flux=oracle.BURGERS, P=1, nx=N, bc=1, x0=0.0, x1=1.0, cfl=0.4)
+    _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
+    assert psi[2, 0] == 1.0   # cells 1, 2 equal, upwind jump u_1 - u_0 = 0
+    assert psi[5, 0] == 2.0   # cells 4, 5 equal, upwind jump u_4 - u_3 = +0.1
+    assert psi[8, 0] == 0.0   # cells 7, 8 equal, upwind jump u_7 - u_6 = -0.1
+
+
+def test_limiter_min_form(oracle):
+    """limiter_form = 1 (Eq. 3.7 for a scalar law): psi^1 = min(superbee(r-),
+    superbee(r+)) with both one-sided ratios, whatever the speed's sign.
+    Jumps 0.01, 0.04, 0.02, 0.06 give at the interface of the 0.04 jump the
+    ratios 0.25 and 0.5, superbee 0.5 and 1, so 0.5; at the 0.02 jump the
+    ratios 2 and 3, superbee 2 and 2, so 2."""
+    J = np.array([0.01, 0.01, 0.01, 0.04, 0.02, 0.06, 0.06, 0.06])
+    u = 1.0 + np.concatenate([[0.0], np.cumsum(J)])
+    N = u.size
+    pr = prob(oracle, flux=oracle.BURGERS, P=1, nx=N, bc=1, x0=0.0, x1=1.0, cfl=0.4,
+              limiter_form=1)
+    _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
+    # interface m lies across the jump u_m - u_{m-1} = J[m - 1]
+    assert psi[4, 0] == pytest.approx(0.5, rel=1e-12)
+    assert psi[5, 0] == pytest.approx(2.0, rel=1e-12)

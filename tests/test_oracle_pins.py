@@ -595,3 +595,74 @@ def test_limiter_min_form(oracle):
     # interface m lies across the jump u_m - u_{m-1} = J[m - 1]
     assert psi[4, 0] == pytest.approx(0.5, rel=1e-12)
     assert psi[5, 0] == pytest.approx(2.0, rel=1e-12)
+
+
+def test_limiter_systems_min_over_components_and_sides(oracle):
+    """Euler with P = 1: psi^1 = min over components of min(superbee(r-),
+    superbee(r+)) (Eq. 3.7, Sec. 3.4). Three interfaces, each with the
+    minimum in a different component, the other components at ratio 1:
+    rho with jumps 0.01, 0.04, 0.02 around the interface's own (ratios 0.25
+    and 0.5: superbee 0.5 and 1, so 0.5); m with 0.01, 0.1, 0.01 (ratios
+    0.1, 0.1: 0.2); E with 0.05, 0.1, 0.01 (ratios 0.5 and 0.1: 1 and 0.2,
+    so 0.2)."""
+    N = 30
+    Jr = np.full(N - 1, 0.01)
+    Jm = np.full(N - 1, 0.01)
+    Je = np.full(N - 1, 0.02)
+    # interface 8 crosses jump index 7 (u_8 - u_7): rho carries the minimum 0.5
+    Jr[6], Jr[7], Jr[8] = 0.01, 0.04, 0.02
+    # interface 16: m carries 0.2 (rho, E at ratio 1)
+    Jm[14], Jm[15], Jm[16] = 0.01, 0.1, 0.01
+    # interface 24: E carries min(superbee(0.05 / 0.1), superbee(0.01 / 0.1)) = 0.2
+    Je[22], Je[23], Je[24] = 0.05, 0.1, 0.01
+    rho = 1.0 + np.concatenate([[0.0], np.cumsum(Jr)])
+    m = 0.2 + np.concatenate([[0.0], np.cumsum(Jm)])
+    E = 3.0 + np.concatenate([[0.0], np.cumsum(Je)])
+    u = np.stack([rho, m, E])
+    assert ((E - 0.5 * m * m / rho) > 0).all()
+    pr = prob(oracle, flux=oracle.EULER1D, P=1, nx=N, bc=1, x0=0.0, x1=1.0, cfl=0.4)
+    _, _, _, psi = oracle.step_1d(pr, u, 1e-4, want_psi=True)
+    assert psi[8, 0] == pytest.approx(0.5, rel=1e-12)
+    assert psi[16, 0] == pytest.approx(0.2, rel=1e-12)
+    assert psi[24, 0] == pytest.approx(0.2, rel=1e-12)
+    # an interface away from the patterns: every ratio is 1
+    assert psi[4, 0] == pytest.approx(1.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# CFL time step (Sec. 5: dt = CFL dx / s^max; 2D: Sec. 5.5)
+# ---------------------------------------------------------------------------
+def test_dt_closed_forms(oracle):
+    """Hand-computed time steps: Burgers s^max = max |u|; Euler s^max =
+    max(|v| + c), c = sqrt(gamma p / rho); 2D Euler CFL/2 min(dx / s_x,
+    dy / s_y) with s_x from |v_x| + c and s_y from |v_y| + c."""
+    N = 10
+    u = np.linspace(-2.0, 1.5, N)[None, :]  # max |u| = 2
+    pr = prob(oracle, flux=oracle.BURGERS, P=2, nx=N, x0=-1.0, x1=1.0, cfl=0.5)
+    assert oracle.dt_cfl(pr, u) == pytest.approx(0.5 * 0.2 / 2.0, rel=1e-15)
+    # Euler: rho = 1, v = 0.5, p = 1 in every cell but one with rho = 0.5,
+    # v = -1, p = 2 (c = sqrt(5.6), the larger speed 1 + sqrt(5.6))
+    rho = np.ones(N)
+    v = np.full(N, 0.5)
+    p = np.ones(N)
+    rho[3], v[3], p[3] = 0.5, -1.0, 2.0
+    U = np.stack([rho, rho * v, p / 0.4 + 0.5 * rho * v * v])
+    pr = prob(oracle, flux=oracle.EULER1D, P=2, nx=N, x0=0.0, x1=2.0, cfl=0.4)
+    assert oracle.dt_cfl(pr, U) == pytest.approx(0.4 * 0.2 / (1.0 + math.sqrt(5.6)), rel=1e-14)
+    # 2D Euler on 8 x 6 cells of [0,1] x [0,0.3] (dx = 1/8, dy = 1/20): one
+    # cell with (rho, vx, vy, p) = (1, 2, 0, 1.4) (c = 1.4), the rest
+    # (1, 0, 0.1, 1.4); the y term is the smaller (0.05 / 1.5 < 0.125 / 3.4)
+    nx, ny = 8, 6
+    rho = np.ones((ny, nx))
+    vx = np.zeros((ny, nx))
+    vy = np.full((ny, nx), 0.1)
+    p = np.full((ny, nx), 1.4)
+    vx[2, 5], vy[2, 5] = 2.0, 0.0
+    E = p / 0.4 + 0.5 * rho * (vx * vx + vy * vy)
+    U2 = np.stack([rho, rho * vx, rho * vy, E])
+    pr = prob(oracle, flux=oracle.EULER2D, P=2, nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=0.3, cfl=0.4)
+    c = math.sqrt(1.4 * 1.4 / 1.0)
+    sx, sy = 2.0 + c, 0.1 + c
+    assert 0.05 / sy < 0.125 / sx
+    want = 0.2 * min(0.125 / sx, 0.05 / sy)
+    assert oracle.dt_cfl(pr, U2) == pytest.approx(want, rel=1e-14)

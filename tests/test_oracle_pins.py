@@ -666,3 +666,28 @@ def test_dt_closed_forms(oracle):
     assert 0.05 / sy < 0.125 / sx
     want = 0.2 * min(0.125 / sx, 0.05 / sy)
     assert oracle.dt_cfl(pr, U2) == pytest.approx(want, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Indicator values worked by hand from Eqs. 3.8-3.12 (eps = 0)
+# ---------------------------------------------------------------------------
+# p = 2 on (f_{i-1}, f_i, f_{i+1}, f_{i+2}) = (0, 1, 3, 4): lateral differences
+# 1 (left) and 1 (right), the central one 2 left out, so I_L = I_R = 1 and
+# I_2 = 1/2; the third undivided difference 4 - 3*3 + 3*1 - 0 = -2, so
+# tau_2 = (3! * -2)^2 = 144 as printed, 4 without the factorial.
+# p = 3 on (0, 1, 1, 2, 4, 4): left differences 1, 0 (I_L = 1), right 2, 0
+# (I_R = 4), I_3 = 4/5; the fifth difference 4 - 5*4 + 10*2 - 10*1 + 5*1 - 0
+# = -1, so tau_3 = (5! * -1)^2 = 14400, or 1.
+PSI_BY_HAND = [(2, [0.0, 1.0, 3.0, 4.0], 1, 0.5 / 144.5), (2, [0.0, 1.0, 3.0, 4.0], 0, 0.5 / 4.5),
+               (3, [0.0, 1.0, 1.0, 2.0, 4.0, 4.0], 1, 0.8 / 14400.8),
+               (3, [0.0, 1.0, 1.0, 2.0, 4.0, 4.0], 0, 0.8 / 1.8)]
+
+
+@pytest.mark.parametrize("p,f,fact,want", PSI_BY_HAND)
+def test_indicator_values_by_hand(oracle, p, f, fact, want):
+    N, m = 14, 7  # interface m between cells i = m - 1 and m
+    u = np.full(N, 0.5)
+    u[m - p:m + p] = f
+    pr = prob(oracle, flux=oracle.LINEAR, P=p, nx=N, adv=(1.0, 0.0), eps=0.0, tau_factorial=fact, bc=1)
+    _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
+    assert psi[m, p - 1] == pytest.approx(want, rel=1e-14)

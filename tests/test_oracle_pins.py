@@ -691,3 +691,18 @@ def test_indicator_values_by_hand(oracle, p, f, fact, want):
     pr = prob(oracle, flux=oracle.LINEAR, P=p, nx=N, adv=(1.0, 0.0), eps=0.0, tau_factorial=fact, bc=1)
     _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
     assert psi[m, p - 1] == pytest.approx(want, rel=1e-14)
+
+
+# psi~^2 (Sec. 3.2) on (0, 1, 3, 7): differences 1, 2, 4; I^1 = 1 * 20 / 21,
+# I^2 = 5 * 16 / 21; the third difference 7 - 9 + 3 - 0 = 1, tau_2 = 36 (or
+# 1 without the factorial); psi~^2 = max(20 / 776, 80 / 836) = 80 / 836 (or
+# max(20 / 41, 80 / 101) = 80 / 101), where psi^2 (I_2 = 16 / 17) is 16 / 628.
+@pytest.mark.parametrize("mod,fact,want", [(1, 1, 80.0 / 836.0), (1, 0, 80.0 / 101.0), (0, 1, 16.0 / 628.0)])
+def test_modified_indicator_value_by_hand(oracle, mod, fact, want):
+    N, m = 12, 6
+    u = np.full(N, 0.5)
+    u[m - 2:m + 2] = [0.0, 1.0, 3.0, 7.0]
+    pr = prob(oracle, flux=oracle.LINEAR, P=2, nx=N, adv=(1.0, 0.0), eps=0.0, tau_factorial=fact, bc=1,
+              psi2_mod=mod)
+    _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
+    assert psi[m, 1] == pytest.approx(want, rel=1e-14)

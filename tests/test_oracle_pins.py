@@ -706,3 +706,33 @@ def test_modified_indicator_value_by_hand(oracle, mod, fact, want):
               psi2_mod=mod)
     _, _, _, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
     assert psi[m, 1] == pytest.approx(want, rel=1e-14)
+
+
+@pytest.mark.parametrize("P", [2])
+def test_2d_local_error_order_anisotropic(oracle, P):
+    """u_t + a u_x + b u_y = 0 with a != b on cells with dy = dx / 2: one step
+    from exact values has local error O(dx^{2P+1}) only if every x-quantity
+    takes dx and a and every y-quantity dy and b (Eqs. 4.5-4.6, 4.9); a swap
+    leaves an O(dt) error."""
+    errs = []
+    Ns = (16, 32, 64)
+    a, b = 1.0, 0.35
+    for N in Ns:
+        pr = prob(oracle, flux=oracle.LINEAR, P=P, nx=N, ny=N, adv=(a, b), bc=1, cfl=0.5,
+                  x0=0.0, x1=1.0, y0=0.0, y1=0.5)
+        x = W.centres(N, 0.0, 1.0)[None, :]
+        y = W.centres(N, 0.0, 0.5)[:, None]
+        f = lambda x, y: np.exp(2.5 * x + 1.5 * y) + 0.3 * x * y  # noqa: E731
+        u = f(x + 0 * y, y + 0 * x)[None]
+        un, dt, ox, oy = oracle.step_2d(pr, u)
+        # dt = CFL/2 min(dx / a, dy / b) with dx = 1/N, dy = 0.5/N
+        assert dt == pytest.approx(0.25 * min((1.0 / N) / a, (0.5 / N) / b), rel=1e-14)
+        ok = (ox[:, :-1] == P) & (ox[:, 1:] == P) & (oy[:-1, :] == P) & (oy[1:, :] == P)
+        ok[:P + 1, :] = False
+        ok[:, :P + 1] = False
+        ok[-P - 1:, :] = False
+        ok[:, -P - 1:] = False
+        assert ok.sum() >= 0.9 * (N - 2 * P - 2) ** 2
+        errs.append(np.abs(un[0] - f(x - a * dt + 0 * y, y - b * dt + 0 * x))[ok].max())
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(2)]
+    assert rates[-1] > 2 * P + 1 - 0.6, (errs, rates)

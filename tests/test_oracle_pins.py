@@ -469,6 +469,30 @@ def test_2d_reduces_to_1d_for_x_only_data(oracle):
     assert np.all(oy == 2)
 
 
+def test_2d_reduces_to_1d_for_y_only_data(oracle):
+    """The same Sod data laid along y (v_y the 1D velocity, v_x = 0): every
+    column equals the 1D step, with the y-momentum in the place of the 1D
+    momentum; the y-orders equal the 1D orders."""
+    N, NX = 32, 6
+    c1 = W.riemann_1d("sod", N, P=2)
+    pr1 = prob(oracle, **c1.problem_kwargs())
+    rho, vel, pre = W.cons_to_prim_1d(c1.u0)
+    col = lambda a: np.repeat(a[:, None], NX, axis=1)  # noqa: E731
+    u2 = W.prim_to_cons_2d(col(rho), col(0 * vel), col(vel), col(pre))
+    pr2 = prob(oracle, flux=oracle.EULER2D, P=2, nx=NX, ny=N, bc=1, cfl=0.8, x0=0.0, x1=1.0,
+               y0=c1.x0, y1=c1.x1)
+    dt = 0.4 * pr1.dx / 2.5
+    un1, _, o1 = oracle.step_1d(pr1, c1.u0, dt)
+    un2, _, ox, oy = oracle.step_2d(pr2, u2, dt)
+    for cx in range(NX):
+        assert np.allclose(un2[0, :, cx], un1[0], rtol=1e-13, atol=1e-13)
+        assert np.allclose(un2[2, :, cx], un1[1], rtol=1e-13, atol=1e-13)
+        assert np.allclose(un2[3, :, cx], un1[2], rtol=1e-13, atol=1e-13)
+        assert np.array_equal(oy[:, cx], o1)
+    assert np.abs(un2[1]).max() < 1e-13
+    assert np.all(ox == 2)
+
+
 def test_2d_diagonal_symmetry_lax_liu(oracle):
     # configuration 8 (Table 5) is symmetric under x <-> y with u <-> v
     c = W.lax_liu(8, 24, P=2)

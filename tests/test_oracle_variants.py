@@ -138,6 +138,19 @@ def test_hll_transonic_burgers_value(oracle):
     assert F[0, 0] == -1.0
 
 
+def test_hll_bounds_from_the_other_state(oracle):
+    """Burgers with u_l = 2, u_r = -1 (a shock): the smallest eigenvalue comes
+    from the right state and the largest from the left, s_l = -1, s_r = 2,
+    and the HLL flux is (2 * 2 - (-1) * 0.5 + (-1)(2)(-1 - 2)) / 3 = 3.5
+    (worked by hand). psi^1 = 0 there: the Roe speed 1/2 > 0 picks
+    r- = (u_i - u_{i-1}) / (u_{i+1} - u_i) = 0 / -3, superbee 0."""
+    u = np.array([[2.0, 2.0, 2.0, -1.0, -1.0, -1.0]])
+    pr = oracle.Problem(flux=oracle.BURGERS, P=1, nx=6, bc=1, lo_flux=2)
+    F, orders = oracle.fluxes_1d_at(pr, u, 1e-3, [3])
+    assert orders[0] == 1
+    assert F[0, 0] == pytest.approx(3.5, rel=1e-15)
+
+
 def test_rusanov_default_unchanged(oracle):
     """lo_flux = 0 is the Rusanov flux: on transport with a > 0 it is also the
     upwind flux a u_l."""

@@ -760,3 +760,20 @@ def test_2d_local_error_order_anisotropic(oracle, P):
         errs.append(np.abs(un[0] - f(x - a * dt + 0 * y, y - b * dt + 0 * x))[ok].max())
     rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(2)]
     assert rates[-1] > 2 * P + 1 - 0.6, (errs, rates)
+
+
+def test_admissibility_threshold_is_inclusive(oracle):
+    """p is admissible when psi^p >= 1 - delta (Eq. 3.2 read with a threshold):
+    a stencil with psi^3 = 1/2 exactly and delta = 1/2 selects p = 3. On
+    (0, 1, 0, -3/2, -5/2, -3/2) the differences are 1, -1 (left), -3/2
+    (central) and -1, 1 (right): I_L = I_R = 2, I_3 = 1; the fifth difference
+    is 1 (tau_3 = 1 without the factorial), so psi^3 = 1/2 in exact binary
+    arithmetic. psi^2 on (1, 0, -3/2, -5/2) is 1/2 / (1/2 + 1) = 1/3."""
+    N, m = 14, 7
+    u = np.full(N, 0.25)
+    u[m - 3:m + 3] = [0.0, 1.0, 0.0, -1.5, -2.5, -1.5]
+    pr = prob(oracle, flux=oracle.LINEAR, P=3, nx=N, adv=(1.0, 0.0), eps=0.0, tau_factorial=0, bc=1,
+              psi_tol=0.5)
+    _, _, orders, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
+    assert psi[m, 2] == 0.5 and psi[m, 1] == pytest.approx(1.0 / 3.0, rel=1e-15)
+    assert orders[m] == 3

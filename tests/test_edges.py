@@ -112,3 +112,30 @@ def test_constant_state_is_a_fixed_point(env, P):
             ctx.acat_run(u, 100)
             torch.cuda.synchronize()
             assert np.array_equal(u.cpu().numpy(), conv(u0))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_order_decision_exactly_at_the_threshold(env, prec):
+    """psi^3 = 1/2 exactly with delta = 1/2 (the oracle pin of the inclusive
+    threshold): the filtered decision cannot certify either side, the literal
+    FP64 fallback finds psi^3 >= 1 - delta, and the GPU selects p = 3 there as
+    the oracle does."""
+    torch, O, acat = env
+    N, m = 14, 7
+    i = np.arange(N, dtype=np.float64)
+    u = 3.0 + 0.125 * i + 0.015625 * i * i  # no two equal neighbours, wrap included (eps = 0)
+    u[m - 3:m + 3] = [0.0, 1.0, 0.0, -1.5, -2.5, -1.5]
+    assert (np.diff(np.r_[u, u[0]]) != 0).all()
+    u = u[None, :]
+    kw = dict(flux=W.LINEAR, P=3, nx=N, ny=1, bc=0, adv=(1.0, 0.0), cfl=0.5, x0=0.0, x1=1.0,
+              eps=0.0, tau_factorial=0, psi_tol=0.5)
+    f32 = prec == "f32"
+    with acat.Context(**kw, precision=acat.PREC_F32 if f32 else acat.PREC_F64) as ctx:
+        out, dt, orders = _step(torch, ctx, acat.to_pair(u) if f32 else u, N + 1)
+        assert ctx.acat_status() == 0
+    pr = O.Problem(**kw)
+    ref, _, oref = O.step_1d(pr, u, dt)
+    assert oref[m] == 3
+    assert np.array_equal(orders, oref), (orders, oref)
+    got = acat.from_pair(out) if f32 else out
+    assert np.abs(got - ref).max() / np.abs(ref).max() < (1e-7 if f32 else 1e-12)

@@ -777,3 +777,22 @@ def test_admissibility_threshold_is_inclusive(oracle):
     _, _, orders, psi = oracle.step_1d(pr, u[None, :], 1e-4, want_psi=True)
     assert psi[m, 2] == 0.5 and psi[m, 1] == pytest.approx(1.0 / 3.0, rel=1e-15)
     assert orders[m] == 3
+
+
+def test_transmissive_ghosts_are_copies(oracle):
+    """Transmissive boundaries copy the edge cell into every ghost (reading of
+    the paper's outflow / free conditions). Linear transport, P = 2, data
+    starting (1, 2, ...): the stencil of interface 0 is (u_0, u_0, u_0, u_1) =
+    (1, 1, 1, 2), so I_{2,L} = eps, psi^2 ~ 0 and the interface is FL-CAT2;
+    there r = 0/0 reads as 1, psi^1 = 1, and the flux is the CAT2 one of the
+    constant pair (u_-1, u_0) = (1, 1): F_0 = a exactly. Mirrored ghosts
+    (u_-2 = u_1) would give psi^2 = 1 there instead."""
+    N = 12
+    u = (1.0 + np.arange(N, dtype=np.float64) ** 1.5)[None, :]
+    a = 0.8
+    pr = prob(oracle, flux=oracle.LINEAR, P=2, nx=N, adv=(a, 0.0), bc=1, x0=0.0, x1=1.0, cfl=0.5)
+    _, _, orders, psi, F = oracle.step_1d(pr, u, 1e-3, want_psi=True, want_flux=True)
+    assert orders[0] == 1 and psi[0, 1] < 1e-9 and psi[0, 0] == 1.0
+    assert F[0, 0] == a * u[0, 0]
+    # the right boundary likewise: interface N sees (u_{N-2}, u_{N-1}, u_{N-1}, u_{N-1})
+    assert orders[N] == 1 and F[N, 0] == pytest.approx(a * u[0, N - 1], rel=1e-15)

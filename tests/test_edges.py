@@ -1,7 +1,8 @@
 """Edge cases of the CUDA path against the oracle: the smallest grids the
 stencils allow (nx = ny = 2 max(P, 2), every cell a ghost of another),
 zero-step runs, a batch of one instance, constant states (every order
-admissible, the state a fixed point) and P = 1 (FL-CAT2 only)."""
+admissible, the state a fixed point), P = 1 (FL-CAT2 only) and an order
+decision exactly at the admissibility threshold."""
 import numpy as np
 import pytest
 

@@ -30,6 +30,10 @@
  *   - Order codes (int8): p_s in 2..P, or 1 when the FL-CAT2 flux was used.
  *   - `stream` is a cudaStream_t (NULL: the legacy default stream). All calls
  *     except acat_create, acat_destroy and acat_status are asynchronous on it.
+ *   - The weight tables are uploaded to each device's constant memory once,
+ *     by the first acat_create (or acat_run_noalloc) on that device. Do not use
+ *     the library across a reset of the device (cudaDeviceReset): the tables
+ *     would not be uploaded again.
  *   - Return values: ACAT_OK (0) or a negative ACAT_ERR_* code; no call
  *     throws. Errors the device detects (non-physical states, a bad dt) are
  *     recorded as sticky ACAT_STATUS_* bits, read by acat_status.
@@ -281,8 +285,10 @@ int acat_adjoint_run(acat_ctx *ctx, const void *ckpt_dev, const double *dts_dev,
  * Scratch (dt and time slots, status word, the ping-pong work buffer) lives
  * in one static device array of 256 B + ACAT_NOALLOC_MAX_STATE inside the
  * library, held by every GPU that loads the library until the process exits.
- * The first call on a device uploads the weight tables and resolves the
- * array's device address; make that call before any stream capture. All calls
+ * The first call on a device uploads the weight tables (once per device,
+ * shared with acat_create); make that call before any stream capture. Every
+ * call asks the runtime for the array's device address, which allocates
+ * nothing. All calls
  * share the array, and it keeps the last call's contents (its slots are
  * cleared at the start of each call). Calls that overlap on the GPU race on
  * it, so issue them on one stream. Steps are launched one by one (no graph).

@@ -128,6 +128,7 @@ def lib():
                                              ctypes.c_double, d, d]
         _lib.or_step_1d.argtypes = [pp, d, d, d, i8, d, d]
         _lib.or_fluxes_1d_at.argtypes = [pp, d, ctypes.c_double, i, i32, d, i8]
+        _lib.or_step_1d_cells.argtypes = [pp, d, ctypes.c_double, i, i32, d]
         _lib.or_step_1d_z.argtypes = [pp, d, d, ctypes.c_double, d, d]
         _lib.or_step_2d.argtypes = [pp, d, d, d, i8, i8]
         _lib.or_step_2d_cells.argtypes = [pp, d, ctypes.c_double, i, i32, i32, d]
@@ -265,6 +266,19 @@ def fluxes_1d_at(prob: Problem, u, dt: float, ifaces):
     if rc:
         raise RuntimeError(rc)
     return F, orders
+
+
+def step_1d_cells(prob: Problem, u, dt: float, cells) -> np.ndarray:
+    """u^{n+1} at selected cells only (Eq. 2.12); returns [len(cells), s]."""
+    u = _f64(u)
+    idx = np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.zeros((len(idx), prob.nvars))
+    pr = prob._c()
+    rc = lib().or_step_1d_cells(ctypes.byref(pr), _dp(u), float(dt), len(idx),
+                                idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(out))
+    if rc:
+        raise RuntimeError(rc)
+    return out
 
 
 def step_1d_complex(prob: Problem, u_re, u_im, dt: float):

@@ -320,6 +320,30 @@ int or_fluxes_1d_at(const or_params *P, const double *u, double dt, int n, const
   return 0;
 }
 
+/* u^{n+1} at selected cells only (Eq. 2.12 with the fluxes of its two
+ * interfaces); out[q*s + c]. */
+int or_step_1d_cells(const or_params *P, const double *u, double dt, int n, const int32_t *cells,
+                     double *out) {
+  if (or_check(P)) return -1;
+  const int s = or_nvars(P), G = P->P > 2 ? P->P : 2;
+  const long N = P->nx;
+  const double dx = (P->x1 - P->x0) / (double)N;
+  or_tables T;
+  or_fill_tables(&T, P->P);
+  const double lam = dt / dx;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int q = 0; q < n; q++) {
+    const long i = cells[q];
+    double line[OR_MAXS * 2 * OR_MAXP], fl[OR_MAXS], fr[OR_MAXS];
+    gather_line_1d_d(P, u, i - 1, G, line);
+    iface_1d_d(P, &T, line, line, G, dt, dx, fl, NULL);
+    gather_line_1d_d(P, u, i, G, line);
+    iface_1d_d(P, &T, line, line, G, dt, dx, fr, NULL);
+    for (int c = 0; c < s; c++) out[(long)q * s + c] = u[c * N + i] + lam * (fl[c] - fr[c]);
+  }
+  return 0;
+}
+
 /* Complex-step evaluation of one 1D step at fixed dt (all branches are taken
  * on the real parts). */
 int or_step_1d_z(const or_params *P, const double *u_re, const double *u_im, double dt,

@@ -73,6 +73,8 @@ int or_step_1d(const or_params *P, const double *u, double *u_out,
                double *dt_io, int8_t *orders, double *psi, double *flux);
 int or_fluxes_1d_at(const or_params *P, const double *u, double dt, int n,
                     const int32_t *ifaces, double *F, int8_t *orders);
+int or_step_1d_cells(const or_params *P, const double *u, double dt, int n,
+                     const int32_t *cells, double *out);
 int or_step_1d_z(const or_params *P, const double *u_re, const double *u_im,
                  double dt, double *out_re, double *out_im);
 

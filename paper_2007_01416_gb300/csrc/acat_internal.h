@@ -135,6 +135,9 @@ int acat_launch_smax1d(int flux, int prec, const Step1DArgs &a, void *stream);
 // One 1D step; returns 0 or a cudaError_t value.
 int acat_launch_step1d(int P, int flux, int prec, const Step1DArgs &a, void *stream);
 int acat_upload_tables_current_device();
+// acat_upload_tables_current_device once per device (dev must be current);
+// returns an acat error code.
+int acat_ensure_tables(int dev);
 int acat_cells_per_cta_1d(int P, int prec);
 // CTAs of the small-CTA FP64 step (boundary counters it needs: that many).
 int acat_fine_ctas_1d(int P, long N);

@@ -305,6 +305,18 @@ int ensure_chain(acat_ctx *c, void *u, double t_end) {
 
 }  // namespace
 
+// The weight tables of every kernel file, uploaded once per device with that
+// device current (shared by acat_create and acat_run_noalloc).
+int acat_ensure_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  if (dev < 0 || dev >= 64) return ACAT_ERR_UNSUPPORTED;
+  if (!g_tab_done[dev]) {
+    if (acat_upload_tables_current_device() != 0) return ACAT_ERR_CUDA;
+    g_tab_done[dev] = true;
+  }
+  return ACAT_OK;
+}
+
 extern "C" {
 
 void acat_default_params(acat_params *p) {
@@ -351,17 +363,10 @@ int acat_create(const acat_params *p, acat_ctx **out) {
     return ACAT_ERR_CUDA;
   }
   {
-    std::lock_guard<std::mutex> lk(g_tab_mu);
-    if (c->device < 0 || c->device >= 64) {
+    const int rt = acat_ensure_tables(c->device);
+    if (rt != ACAT_OK) {
       delete c;
-      return ACAT_ERR_UNSUPPORTED;
-    }
-    if (!g_tab_done[c->device]) {
-      if (acat_upload_tables_current_device() != 0) {
-        delete c;
-        return ACAT_ERR_CUDA;
-      }
-      g_tab_done[c->device] = true;
+      return rt;
     }
   }
   const size_t sb = (size_t)acat_state_bytes(c);

@@ -21,7 +21,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/acat.h"
 #include "acat_internal.h"
@@ -32,10 +31,6 @@ constexpr size_t kSlotBytes = 256;
 constexpr size_t kMaxState = (size_t)ACAT_NOALLOC_MAX_STATE;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kSlotBytes + kMaxState];
-
-std::mutex g_mu;
-bool g_ready[64] = {false};
-unsigned char *g_ptr[64] = {nullptr};
 
 int nvars1d(int flux) { return flux == ACAT_FLUX_EULER1D ? 3 : 1; }
 
@@ -58,19 +53,16 @@ int validate(const acat_params *p) {
   return ACAT_OK;
 }
 
-// Once per device, with that device current: weight tables into constant
-// memory and the device address of the scratch array.
+// With the device current: the weight tables in constant memory (uploaded
+// once per device, shared with acat_create), then the device address of the
+// scratch array, asked on every call so that no address outlives the context
+// it was taken in.
 int setup(int dev, unsigned char **ptr) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (dev < 0 || dev >= 64) return ACAT_ERR_UNSUPPORTED;
-  if (!g_ready[dev]) {
-    if (acat_upload_tables_current_device() != 0) return ACAT_ERR_CUDA;
-    void *addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return ACAT_ERR_CUDA;
-    g_ptr[dev] = static_cast<unsigned char *>(addr);
-    g_ready[dev] = true;
-  }
-  *ptr = g_ptr[dev];
+  const int rc = acat_ensure_tables(dev);
+  if (rc != ACAT_OK) return rc;
+  void *addr = nullptr;
+  if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return ACAT_ERR_CUDA;
+  *ptr = static_cast<unsigned char *>(addr);
   return ACAT_OK;
 }
 

@@ -66,11 +66,12 @@ __global__ void __launch_bounds__(NT, MinCtas<P, true>::value) k_step1d_f32(cons
 // FP64 step in small CTAs (NWF warps): CTA b computes the NI interfaces
 // [b NI, b NI + NI) and updates the cells between them; the cell between
 // two CTAs is updated by whichever of the two finishes second. Each CTA
-// publishes its edge fluxes, fences, and counts itself in at the boundary
-// counters of its left and right neighbours (atomicAdd; no CTA ever waits):
-// the one that reads 1 owns the boundary cell, reads the other edge flux from
-// L2 and resets the counter for the next step. Small CTAs spread a step's
-// interfaces evenly over the SMs, and no interface is computed twice.
+// publishes its edge fluxes, fences (release), and counts itself in at the
+// boundary counters of its left and right neighbours (atomicAdd; no CTA ever
+// waits): the one that reads 1 fences again (acquire), owns the boundary
+// cell, reads the other edge flux from L2 and resets the counter for the next
+// step. Small CTAs spread a step's interfaces evenly over the SMs, and no
+// interface is computed twice.
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1DArgs a) {
   using TL = Tiling<P, NWF>;
@@ -141,6 +142,10 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
       own1 = 1;
       a.cnt[blockIdx.x] = 0;
     }
+    // acquire: the neighbour's edge flux, published before its fence and
+    // atomic, is read (by any thread, after the barrier below) only after
+    // this fence, which follows the atomic that observed it
+    if (own0 | own1) __threadfence();
     s_own[0] = own0;
     s_own[1] = own1;
   }

@@ -796,3 +796,31 @@ def test_transmissive_ghosts_are_copies(oracle):
     assert F[0, 0] == a * u[0, 0]
     # the right boundary likewise: interface N sees (u_{N-2}, u_{N-1}, u_{N-1}, u_{N-1})
     assert orders[N] == 1 and F[N, 0] == pytest.approx(a * u[0, N - 1], rel=1e-15)
+
+
+@pytest.mark.parametrize("P", [3, 4])
+def test_order_is_max_of_admissible_set(oracle, P):
+    """p_s = max A (Eq. 3.3): smaller stencils need not be admissible. Data
+    (x - x*)^2 + (x - x*)^3 with the critical point x* at the midpoint of cells
+    m-2 and m-1, h = 0.05: the left lateral weight of S_2 is only
+    (h^3/4)^2 + eps while tau_2 = (3! 6 h^3)^2, so psi^2 ~ 5e-5 rejects
+    (value checked against its closed form);
+    the fifth and seventh differences of a cubic vanish, so tau_3 = tau_4 = 0
+    to rounding and psi^3 = psi^4 = 1 accept. The selected order is P. A rule
+    taking the largest p whose smaller stencils are all admissible would give
+    FL-CAT2 (code 1) here."""
+    h, n, m = 0.05, 16, 8
+    x = (np.arange(n) + 0.5) * h
+    xs = 0.5 * (x[m - 2] + x[m - 1])
+    u = ((x - xs) ** 2 + (x - xs) ** 3)[None, :]
+    pr = prob(oracle, flux=oracle.LINEAR, P=P, nx=n, adv=(1.0, 0.0), bc=1)
+    _, _, orders, psi = oracle.step_1d(pr, u, 1e-4, want_psi=True)
+    # closed forms: d_L = h^3/4, d_R = u(x* + 5h/2) - u(x* + 3h/2) = 4h^2 + 49h^3/4,
+    # third difference 6 h^3
+    IL, IR = (h ** 3 / 4.0) ** 2 + 1e-12, (4.0 * h ** 2 + 12.25 * h ** 3) ** 2 + 1e-12
+    I2 = IL * IR / (IL + IR)
+    assert psi[m, 1] == pytest.approx(I2 / (I2 + (36.0 * h ** 3) ** 2), rel=1e-9)
+    assert psi[m, 1] < 0.9
+    for p in range(3, P + 1):
+        assert psi[m, p - 1] > 1.0 - 1e-12
+    assert orders[m] == P

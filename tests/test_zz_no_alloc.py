@@ -68,6 +68,26 @@ def test_noalloc_matches_acat_run_twice(env):
         assert status == 0
 
 
+def test_noalloc_clears_slots_between_calls(env):
+    """The slots of the shared array (wave speed, time, status) are cleared at
+    the start of every call: a first call with a much larger wave speed, or one
+    that sets a status bit, leaves nothing behind for the next."""
+    strong = W.euler1d_riemann_entropy(nx=2048, seed=21, P=3)
+    strong.u0[2] *= 40.0  # energy x 40: wave speed about 6x that of the data below
+    calm = W.acoustic_pulse(nx=1024, seed=22, P=2)
+    got, t_got, status = _noalloc(env, strong, 5)
+    assert status == 0
+    got, t_got, status = _noalloc(env, calm, 31)
+    ref, t_ref = _with_context(env, calm, 31)
+    assert np.array_equal(got, ref) and t_got == t_ref and status == 0
+    bad = W.euler1d_riemann_entropy(nx=512, seed=23, P=2)
+    bad.u0[0, 100] = -1.0  # negative density: the step flags it
+    _, _, status = _noalloc(env, bad, 1)
+    assert status != 0
+    got, t_got, status = _noalloc(env, calm, 31)
+    assert np.array_equal(got, ref) and t_got == t_ref and status == 0
+
+
 def test_noalloc_rejects_oversized_state(env):
     torch, acat, L = env
     case = W.euler1d_riemann_entropy(nx=350000, seed=0, P=2)  # 8.4 MB > 8 MiB

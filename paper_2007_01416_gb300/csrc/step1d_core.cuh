@@ -171,8 +171,12 @@ struct DPhys<ACAT_FLUX_LINEAR> {
     float a;
   };
   __device__ static __forceinline__ Base base(const float *, float a, float) { return Base{a}; }
+  __device__ static __forceinline__ Base base2(const float *, const float *, float a, float) { return Base{a}; }
   __device__ static __forceinline__ void dflux(const Base &b, const float *d, float *df) {
     df[0] = b.a * d[0];
+  }
+  __device__ static __forceinline__ void dflux_pair(const Base &b, const float *dh, const float *dl, float *df) {
+    df[0] = b.a * (dh[0] + dl[0]);
   }
   // two increments at once, packed in the lanes of float2 values
   __device__ static __forceinline__ void dflux_x2(const Base &b, const float2 *d, float2 *df) {
@@ -189,9 +193,14 @@ struct DPhys<ACAT_FLUX_BURGERS> {
     float u;
   };
   __device__ static __forceinline__ Base base(const float *u, float, float) { return Base{u[0]}; }
+  __device__ static __forceinline__ Base base2(const float *h, const float *, float, float) { return Base{h[0]}; }
   // (u + d)^2/2 - u^2/2 = d (u + d/2)
   __device__ static __forceinline__ void dflux(const Base &b, const float *d, float *df) {
     df[0] = d[0] * fmaf(0.5f, d[0], b.u);
+  }
+  __device__ static __forceinline__ void dflux_pair(const Base &b, const float *dh, const float *dl, float *df) {
+    const float d[1] = {dh[0] + dl[0]};
+    dflux(b, d, df);
   }
   __device__ static __forceinline__ void dflux_x2(const Base &b, const float2 *d, float2 *df) {
     df[0] = f2mul(d[0], f2fma(f2dup(0.5f), d[0], f2dup(b.u)));
@@ -204,15 +213,35 @@ template <>
 struct DPhys<ACAT_FLUX_EULER1D> {
   static constexpr int S = 3;
   struct Base {
-    float rho, m, v, H, gm1;
+    float rho, m, v, vl, H, gm1;  // v + vl: the velocity as a float-float pair
   };
   __device__ static __forceinline__ Base base(const float *u, float, float gm1) {
     Base b;
     b.rho = u[0];
     b.m = u[1];
     b.v = u[1] * recip(u[0]);
+    b.vl = 0.0f;
     const float p = gm1 * fmaf(-0.5f * u[1], b.v, u[2]);
     b.H = u[2] + p;
+    b.gm1 = gm1;
+    return b;
+  }
+  // The base of a compensated state hi + lo, with the velocity m / rho carried
+  // to float-float accuracy: v = fl(m_hi / rho_hi), and vl from the residual
+  // m - v rho (its leading part m_hi - v rho_hi exact in one FMA). Increments
+  // at constant velocity (an entropy wave) have b = v a exactly, and the
+  // numerator b - v a of dv cancels: with v rounded to float it would leave
+  // eps32 |v a| of noise in every energy and momentum increment, which the
+  // (2p-1)-th difference of tau_p amplifies over a run.
+  __device__ static __forceinline__ Base base2(const float *h, const float *l, float, float gm1) {
+    Base b;
+    b.rho = h[0];
+    b.m = h[1];
+    const float r = recip(h[0]);
+    b.v = h[1] * r;
+    b.vl = (fmaf(-b.v, h[0], h[1]) + fmaf(-b.v, l[0], l[1])) * r;
+    const float p = gm1 * fmaf(-0.5f * h[1], b.v, h[2]);
+    b.H = h[2] + p;
     b.gm1 = gm1;
     return b;
   }
@@ -222,7 +251,21 @@ struct DPhys<ACAT_FLUX_EULER1D> {
   //   dp = (gamma - 1)(c - d(mv)/2)
   //   df = (b, d(mv) + dp, dv H + (v + dv)(c + dp))
   __device__ static __forceinline__ void dflux(const Base &B, const float *d, float *df) {
-    const float dv = fmaf(-B.v, d[0], d[1]) * recip(B.rho + d[0]);
+    const float dv = fmaf(-B.vl, d[0], fmaf(-B.v, d[0], d[1])) * recip(B.rho + d[0]);
+    const float vn = B.v + dv;
+    const float dmv = fmaf(B.m, dv, d[1] * vn);
+    const float dp = B.gm1 * fmaf(-0.5f, dmv, d[2]);
+    df[0] = d[1];
+    df[1] = dmv + dp;
+    df[2] = fmaf(dv, B.H, vn * (d[2] + dp));
+  }
+  // the increment d = dh + dl given as an unevaluated pair (dh: difference of
+  // the hi parts, exact for nearby values; dl: of the lo parts): the
+  // cancelling numerator of dv is formed from both parts
+  __device__ static __forceinline__ void dflux_pair(const Base &B, const float *dh, const float *dl, float *df) {
+    const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
+    const float num = fmaf(-B.vl, dh[0], fmaf(-B.v, dh[0], dh[1]) + fmaf(-B.v, dl[0], dl[1]));
+    const float dv = num * recip(B.rho + d[0]);
     const float vn = B.v + dv;
     const float dmv = fmaf(B.m, dv, d[1] * vn);
     const float dp = B.gm1 * fmaf(-0.5f, dmv, d[2]);
@@ -232,7 +275,7 @@ struct DPhys<ACAT_FLUX_EULER1D> {
   }
   // the same for two increments packed in float2 lanes
   __device__ static __forceinline__ void dflux_x2(const Base &B, const float2 *d, float2 *df) {
-    const float2 t = f2fma(f2dup(-B.v), d[0], d[1]);
+    const float2 t = f2fma(f2dup(-B.vl), d[0], f2fma(f2dup(-B.v), d[0], d[1]));
     const float2 den = f2add(f2dup(B.rho), d[0]);
     const float2 dv = f2mul(t, make_float2(recip(den.x), recip(den.y)));
     const float2 vn = f2add(f2dup(B.v), dv);
@@ -272,12 +315,15 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
   float g1r[n];
 #pragma unroll
   for (int r = 0; r < n; r++) g1r[r] = TB::g1(p, l, r);
-  float ui[S], uj[S], d0[S];
+  float ui[S], uil[S], uj[S], ujl[S], dh[S], dl[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     ui[c] = hi[c * cs];
+    uil[c] = lo[c * cs];
     uj[c] = hi[c * cs + j];
-    d0[c] = (hi[c * cs + j] - hi[c * cs]) + (lo[c * cs + j] - lo[c * cs]);
+    ujl[c] = lo[c * cs + j];
+    dh[c] = uj[c] - ui[c];
+    dl[c] = ujl[c] - uil[c];
   }
   // the 2p - 1 time levels r != 0 (level q <-> table row q < p - 1 ? q : q + 1)
   // are worked in pairs packed in float2 lanes (p <= 3; at p = 4 the pairs
@@ -285,8 +331,8 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
   constexpr int NL = n - 1, NP = p <= 3 ? NL / 2 : 0;
   float D[S], Fsum[S], Fprev[S], dels[NL - 2 * NP][S];
   float2 del2[NP > 0 ? NP : 1][S];
-  DP::dflux(DP::base(ui, adv, gm1), d0, D);  // f(u_j) - f(u_i)
-  const typename DP::Base bj = DP::base(uj, adv, gm1);
+  DP::dflux_pair(DP::base2(ui, uil, adv, gm1), dh, dl, D);  // f(u_j) - f(u_i)
+  const typename DP::Base bj = DP::base2(uj, ujl, adv, gm1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     Fsum[c] = D[c];
@@ -397,17 +443,20 @@ __device__ __forceinline__ void cat_delta2(const float *hi, const float *lo, int
   float g1h[p];
 #pragma unroll
   for (int i = 0; i < p; i++) g1h[i] = TB::g1(p, m, h * p + i);
-  float ui[S], uj[S], d0[S];
+  float ui[S], uil[S], uj[S], ujl[S], dh[S], dl[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     ui[c] = hi[c * cs];
+    uil[c] = lo[c * cs];
     uj[c] = hi[c * cs + j];
-    d0[c] = (hi[c * cs + j] - hi[c * cs]) + (lo[c * cs + j] - lo[c * cs]);
+    ujl[c] = lo[c * cs + j];
+    dh[c] = uj[c] - ui[c];
+    dl[c] = ujl[c] - uil[c];
   }
   float D[S], Fsum[S], Fprev[S];
   float2 del2[KP][S];
-  DP::dflux(DP::base(ui, adv, gm1), d0, D);  // f(u_j) - f(u_i)
-  const typename DP::Base bj = DP::base(uj, adv, gm1);
+  DP::dflux_pair(DP::base2(ui, uil, adv, gm1), dh, dl, D);  // f(u_j) - f(u_i)
+  const typename DP::Base bj = DP::base2(uj, ujl, adv, gm1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     Fsum[c] = D[c];
@@ -487,15 +536,18 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
   const float gm1 = gamma - 1.0f;
-  float u0[S], u1[S], du[S], D1[S], U[S], d1[S], T0[S], T1[S];
+  float u0[S], u0l[S], u1[S], dh[S], dl[S], du[S], D1[S], U[S], d1[S], T0[S], T1[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     u0[c] = hi[c * cs];
+    u0l[c] = lo[c * cs];
     u1[c] = hi[c * cs + 1];
-    du[c] = (hi[c * cs + 1] - hi[c * cs]) + (lo[c * cs + 1] - lo[c * cs]);
+    dh[c] = u1[c] - u0[c];
+    dl[c] = lo[c * cs + 1] - u0l[c];
+    du[c] = dh[c] + dl[c];
   }
-  const typename DP::Base b0 = DP::base(u0, adv, gm1);
-  DP::dflux(b0, du, D1);
+  const typename DP::Base b0 = DP::base2(u0, u0l, adv, gm1);
+  DP::dflux_pair(b0, dh, dl, D1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
     U[c] = -lam * D1[c];
@@ -771,13 +823,15 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     const long i = i0 + t;
     if (i >= N) break;
     const int k = t + TL::GH;
-    float ui[S], dl[S], B[S];
+    float ui[S], uil[S], dh[S], dl[S], B[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
       ui[c] = sm.thi[c][k];
-      dl[c] = (sm.thi[c][k - 1] - sm.thi[c][k]) + (sm.tlo[c][k - 1] - sm.tlo[c][k]);
+      uil[c] = sm.tlo[c][k];
+      dh[c] = sm.thi[c][k - 1] - ui[c];
+      dl[c] = sm.tlo[c][k - 1] - uil[c];
     }
-    DP::dflux(DP::base(ui, adv, gm1), dl, B);  // f(u_{i-1}) - f(u_i)
+    DP::dflux_pair(DP::base2(ui, uil, adv, gm1), dh, dl, B);  // f(u_{i-1}) - f(u_i)
     float un[S], lo_[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {

@@ -59,9 +59,17 @@ struct Phys2<ACAT_FLUX_LINEAR> {
   __device__ static __forceinline__ Base base(const float *, float ax, float ay, float) {
     return Base{ax, ay};
   }
+  __device__ static __forceinline__ Base base2(const float *, const float *, float ax, float ay, float) {
+    return Base{ax, ay};
+  }
   __device__ static __forceinline__ void dflux2(const Base &B, const float *d, float *df, float *dg) {
     df[0] = B.ax * d[0];
     dg[0] = B.ay * d[0];
+  }
+  __device__ static __forceinline__ void dflux2_pair(const Base &B, const float *dh, const float *dl, float *df,
+                                                     float *dg) {
+    const float d[1] = {dh[0] + dl[0]};
+    dflux2(B, d, df, dg);
   }
   __device__ static __forceinline__ void dflux2_x2(const Base &B, const float2 *d, float2 *df, float2 *dg) {
     df[0] = f2mul(f2dup(B.ax), d[0]);
@@ -114,7 +122,7 @@ struct Phys2<ACAT_FLUX_EULER2D> {
     lmax = vn + c;
   }
   struct Base {
-    float mx, my, v, w, H, rho, gm1;
+    float mx, my, v, w, vl, wl, H, rho, gm1;  // v + vl, w + wl: float-float velocities
   };
   __device__ static __forceinline__ Base base(const float *u, float, float, float gm1) {
     Base b;
@@ -124,8 +132,28 @@ struct Phys2<ACAT_FLUX_EULER2D> {
     const float ri = recip(u[0]);
     b.v = u[1] * ri;
     b.w = u[2] * ri;
+    b.vl = b.wl = 0.0f;
     const float p = gm1 * (u[3] - 0.5f * fmaf(u[1], b.v, u[2] * b.w));
     b.H = u[3] + p;
+    b.gm1 = gm1;
+    return b;
+  }
+  // The base of a compensated state hi + lo with both velocities to
+  // float-float accuracy (the 1D base2: at constant velocity the numerators
+  // b - v a of the velocity increments cancel, and a velocity rounded to float
+  // would leave eps32 |v a| of noise in the increments).
+  __device__ static __forceinline__ Base base2(const float *h, const float *l, float, float, float gm1) {
+    Base b;
+    b.rho = h[0];
+    b.mx = h[1];
+    b.my = h[2];
+    const float ri = recip(h[0]);
+    b.v = h[1] * ri;
+    b.w = h[2] * ri;
+    b.vl = (fmaf(-b.v, h[0], h[1]) + fmaf(-b.v, l[0], l[1])) * ri;
+    b.wl = (fmaf(-b.w, h[0], h[2]) + fmaf(-b.w, l[0], l[2])) * ri;
+    const float p = gm1 * (h[3] - 0.5f * fmaf(h[1], b.v, h[2] * b.w));
+    b.H = h[3] + p;
     b.gm1 = gm1;
     return b;
   }
@@ -135,7 +163,22 @@ struct Phys2<ACAT_FLUX_EULER2D> {
   //   d(mx w) = mx dw + bx (w + dw), dp = (gamma - 1)(c - (d(mx v) + d(my w))/2)
   __device__ static __forceinline__ void dflux2(const Base &B, const float *d, float *df, float *dg) {
     const float ri = recip(B.rho + d[0]);
-    const float dv = fmaf(-B.v, d[0], d[1]) * ri, dw = fmaf(-B.w, d[0], d[2]) * ri;
+    const float dv = fmaf(-B.vl, d[0], fmaf(-B.v, d[0], d[1])) * ri;
+    const float dw = fmaf(-B.wl, d[0], fmaf(-B.w, d[0], d[2])) * ri;
+    dflux2_rest(B, d, dv, dw, df, dg);
+  }
+  // the increment d = dh + dl as an unevaluated pair (differences of the hi
+  // and of the lo parts): the cancelling numerators take both parts
+  __device__ static __forceinline__ void dflux2_pair(const Base &B, const float *dh, const float *dl, float *df,
+                                                     float *dg) {
+    const float d[4] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2], dh[3] + dl[3]};
+    const float ri = recip(B.rho + d[0]);
+    const float dv = fmaf(-B.vl, dh[0], fmaf(-B.v, dh[0], dh[1]) + fmaf(-B.v, dl[0], dl[1])) * ri;
+    const float dw = fmaf(-B.wl, dh[0], fmaf(-B.w, dh[0], dh[2]) + fmaf(-B.w, dl[0], dl[2])) * ri;
+    dflux2_rest(B, d, dv, dw, df, dg);
+  }
+  __device__ static __forceinline__ void dflux2_rest(const Base &B, const float *d, float dv, float dw, float *df,
+                                                     float *dg) {
     const float vn = B.v + dv, wn = B.w + dw;
     const float dmv = fmaf(B.mx, dv, d[1] * vn), dmw = fmaf(B.my, dw, d[2] * wn);
     const float dxy = fmaf(B.mx, dw, d[1] * wn);
@@ -154,7 +197,8 @@ struct Phys2<ACAT_FLUX_EULER2D> {
   __device__ static __forceinline__ void dflux2_x2(const Base &B, const float2 *d, float2 *df, float2 *dg) {
     const float2 den = f2add(f2dup(B.rho), d[0]);
     const float2 ri = make_float2(recip(den.x), recip(den.y));
-    const float2 dv = f2mul(f2fma(f2dup(-B.v), d[0], d[1]), ri), dw = f2mul(f2fma(f2dup(-B.w), d[0], d[2]), ri);
+    const float2 dv = f2mul(f2fma(f2dup(-B.vl), d[0], f2fma(f2dup(-B.v), d[0], d[1])), ri);
+    const float2 dw = f2mul(f2fma(f2dup(-B.wl), d[0], f2fma(f2dup(-B.w), d[0], d[2])), ri);
     const float2 vn = f2add(f2dup(B.v), dv), wn = f2add(f2dup(B.w), dw);
     const float2 dmv = f2fma(f2dup(B.mx), dv, f2mul(d[1], vn)), dmw = f2fma(f2dup(B.my), dw, f2mul(d[2], wn));
     const float2 dxy = f2fma(f2dup(B.mx), dw, f2mul(d[1], wn));
@@ -296,16 +340,19 @@ __device__ __forceinline__ void cat2d_f32(const float *hi, const float *lo, int 
     gx[r] = TB::g1(p, a1, r);
     gy[r] = TB::g1(p, b1, r);
   }
-  float ua[S], uj[S], d0[S];
+  float ua[S], ual[S], uj[S], ujl[S], dh[S], dl[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     ua[c] = hi[c * cs];
+    ual[c] = lo[c * cs];
     uj[c] = hi[c * cs + off];
-    d0[c] = (hi[c * cs + off] - hi[c * cs]) + (lo[c * cs + off] - lo[c * cs]);
+    ujl[c] = lo[c * cs + off];
+    dh[c] = uj[c] - ua[c];
+    dl[c] = ujl[c] - ual[c];
   }
   float Df[S], Dg[S];
-  PH::dflux2(PH::base(ua, ax, ay, gm1), d0, Df, Dg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
-  const typename PH::Base bj = PH::base(uj, ax, ay, gm1);
+  PH::dflux2_pair(PH::base2(ua, ual, ax, ay, gm1), dh, dl, Df, Dg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
+  const typename PH::Base bj = PH::base2(uj, ujl, ax, ay, gm1);
   // the 2p - 1 levels r != 0 in pairs packed in float2 lanes, the last alone
   constexpr int NL = n - 1, NP = NL / 2;
   float Ff[S], Fg[S], Pf[S], Pg[S], dels[S];
@@ -522,22 +569,30 @@ __device__ __forceinline__ void flcat2_2d_f32(const float *hi, const float *lo, 
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   const bool roe_linear = FLUX == ACAT_FLUX_LINEAR && limiter_form == 0;
-  float ua[S], d10[S], d01[S], d11[S], u10[S], u01[S];
+  float ua[S], ual[S], d10[S], d01[S], d11[S], u10[S], u01[S];
+  float h10[S], l10[S], h01[S], l01[S], h11[S], l11[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const int o = c * cs;
     ua[c] = hi[o];
+    ual[c] = lo[o];
     u10[c] = hi[o + 1];
     u01[c] = hi[o + rs];
-    d10[c] = (hi[o + 1] - hi[o]) + (lo[o + 1] - lo[o]);
-    d01[c] = (hi[o + rs] - hi[o]) + (lo[o + rs] - lo[o]);
-    d11[c] = (hi[o + rs + 1] - hi[o]) + (lo[o + rs + 1] - lo[o]);
+    h10[c] = hi[o + 1] - hi[o];
+    l10[c] = lo[o + 1] - lo[o];
+    h01[c] = hi[o + rs] - hi[o];
+    l01[c] = lo[o + rs] - lo[o];
+    h11[c] = hi[o + rs + 1] - hi[o];
+    l11[c] = lo[o + rs + 1] - lo[o];
+    d10[c] = h10[c] + l10[c];
+    d01[c] = h01[c] + l01[c];
+    d11[c] = h11[c] + l11[c];
   }
-  const typename PH::Base B = PH::base(ua, ax, ay, gm1);
+  const typename PH::Base B = PH::base2(ua, ual, ax, ay, gm1);
   float Df10[S], Dg10[S], Df01[S], Dg01[S], Df11[S], Dg11[S];
-  PH::dflux2(B, d10, Df10, Dg10);
-  PH::dflux2(B, d01, Df01, Dg01);
-  PH::dflux2(B, d11, Df11, Dg11);
+  PH::dflux2_pair(B, h10, l10, Df10, Dg10);
+  PH::dflux2_pair(B, h01, l01, Df01, Dg01);
+  PH::dflux2_pair(B, h11, l11, Df11, Dg11);
   float U00[S];
 #pragma unroll
   for (int c = 0; c < S; c++) U00[c] = -lx * Df10[c] - ly * Dg01[c];
@@ -775,16 +830,19 @@ __global__ void __launch_bounds__(NT, F32 ? 3 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
     const int tx = cx + GH2, ty = cy + GH2;
     double un[S];
     if constexpr (F32) {
-      float uc[S], dlx[S], dly[S], Bx[S], By[S], junk[S], hf[S], lf[S];
+      float uc[S], ucl[S], hx[S], lx_[S], hy[S], ly_[S], Bx[S], By[S], junk[S], hf[S], lf[S];
 #pragma unroll
       for (int c = 0; c < S; c++) {
         uc[c] = thi[c][ty][tx];
-        dlx[c] = (thi[c][ty][tx - 1] - thi[c][ty][tx]) + (tlo[c][ty][tx - 1] - tlo[c][ty][tx]);
-        dly[c] = (thi[c][ty - 1][tx] - thi[c][ty][tx]) + (tlo[c][ty - 1][tx] - tlo[c][ty][tx]);
+        ucl[c] = tlo[c][ty][tx];
+        hx[c] = thi[c][ty][tx - 1] - uc[c];
+        lx_[c] = tlo[c][ty][tx - 1] - ucl[c];
+        hy[c] = thi[c][ty - 1][tx] - uc[c];
+        ly_[c] = tlo[c][ty - 1][tx] - ucl[c];
       }
-      const typename PH::Base B = PH::base(uc, a.advf[0], a.advf[1], a.gm1f);
-      PH::dflux2(B, dlx, Bx, junk);  // f(u_{x-1,y}) - f(u)
-      PH::dflux2(B, dly, junk, By);  // g(u_{x,y-1}) - g(u)
+      const typename PH::Base B = PH::base2(uc, ucl, a.advf[0], a.advf[1], a.gm1f);
+      PH::dflux2_pair(B, hx, lx_, Bx, junk);  // f(u_{x-1,y}) - f(u)
+      PH::dflux2_pair(B, hy, ly_, junk, By);  // g(u_{x,y-1}) - g(u)
       float *uo = static_cast<float *>(a.u_out);
       const float lx = s_lxf, ly = s_lyf;
 #pragma unroll
@@ -1401,15 +1459,18 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
     typename PH::Base bj;
     if (act) {
       const int tx = ax + P - p1 + 1 + ia, ty = ay + P - p2 + 1 + ib;
-      float ua[S], uj[S], d0[S];
+      float ua[S], ual[S], uj[S], ujl[S], dh[S], dl[S];
 #pragma unroll
       for (int c = 0; c < S; c++) {
         ua[c] = sm.thi[c][ay + P][ax + P];
+        ual[c] = sm.tlo[c][ay + P][ax + P];
         uj[c] = sm.thi[c][ty][tx];
-        d0[c] = (sm.thi[c][ty][tx] - sm.thi[c][ay + P][ax + P]) + (sm.tlo[c][ty][tx] - sm.tlo[c][ay + P][ax + P]);
+        ujl[c] = sm.tlo[c][ty][tx];
+        dh[c] = uj[c] - ua[c];
+        dl[c] = ujl[c] - ual[c];
       }
-      PH::dflux2(PH::base(ua, axv, ayv, gm1), d0, Ff, Fg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
-      bj = PH::base(uj, axv, ayv, gm1);
+      PH::dflux2_pair(PH::base2(ua, ual, axv, ayv, gm1), dh, dl, Ff, Fg);  // f(u_j) - f(u_a), g(u_j) - g(u_a)
+      bj = PH::base2(uj, ujl, axv, ayv, gm1);
     } else {
       float z[S];
 #pragma unroll
@@ -1621,16 +1682,19 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
     const long gx = x0 + cx, gy = y0 + cy;
     if (gx >= NXl || gy >= NYl) continue;
     const int tx = cx + P, ty = cy + P;
-    float uc[S], dlx[S], dly[S], Bx[S], By[S], junk[S], hf[S], lf[S];
+    float uc[S], ucl[S], hx[S], lx_[S], hy[S], ly_[S], Bx[S], By[S], junk[S], hf[S], lf[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
       uc[c] = sm.thi[c][ty][tx];
-      dlx[c] = (sm.thi[c][ty][tx - 1] - sm.thi[c][ty][tx]) + (sm.tlo[c][ty][tx - 1] - sm.tlo[c][ty][tx]);
-      dly[c] = (sm.thi[c][ty - 1][tx] - sm.thi[c][ty][tx]) + (sm.tlo[c][ty - 1][tx] - sm.tlo[c][ty][tx]);
+      ucl[c] = sm.tlo[c][ty][tx];
+      hx[c] = sm.thi[c][ty][tx - 1] - uc[c];
+      lx_[c] = sm.tlo[c][ty][tx - 1] - ucl[c];
+      hy[c] = sm.thi[c][ty - 1][tx] - uc[c];
+      ly_[c] = sm.tlo[c][ty - 1][tx] - ucl[c];
     }
-    const typename PH::Base B = PH::base(uc, a.advf[0], a.advf[1], a.gm1f);
-    PH::dflux2(B, dlx, Bx, junk);  // f(u_{x-1,y}) - f(u)
-    PH::dflux2(B, dly, junk, By);  // g(u_{x,y-1}) - g(u)
+    const typename PH::Base B = PH::base2(uc, ucl, a.advf[0], a.advf[1], a.gm1f);
+    PH::dflux2_pair(B, hx, lx_, Bx, junk);  // f(u_{x-1,y}) - f(u)
+    PH::dflux2_pair(B, hy, ly_, junk, By);  // g(u_{x,y-1}) - g(u)
 #pragma unroll
     for (int c = 0; c < S; c++) {
       const float dx_ = __fmul_rn(lx, __fadd_rn(Bx[c], __fsub_rn(sm.Fx[cy][cx][c], sm.Fx[cy][cx + 1][c])));

@@ -117,6 +117,7 @@ def lib():
         _lib.or_flux_weights.argtypes = [i, d]
         _lib.or_flux_x.argtypes = [pp, d, d]
         _lib.or_flux_y.argtypes = [pp, d, d]
+        _lib.or_cell_flux_1d.argtypes = [pp, d, d]
         _lib.or_dt_1d.argtypes = [pp, d]
         _lib.or_dt_1d.restype = ctypes.c_double
         _lib.or_dt_2d.argtypes = [pp, d]
@@ -182,6 +183,15 @@ def flux_y(prob: Problem, u) -> np.ndarray:
     f = np.zeros(prob.nvars)
     pr = prob._c()
     lib().or_flux_y(ctypes.byref(pr), _dp(u), _dp(f))
+    return f
+
+
+def cell_flux_1d(prob: Problem, u) -> np.ndarray:
+    """The physical flux f(u_i) of every cell of a 1D state u[s, nx]."""
+    u = _f64(u)
+    f = np.empty_like(u)
+    pr = prob._c()
+    lib().or_cell_flux_1d(ctypes.byref(pr), _dp(u), _dp(f))
     return f
 
 

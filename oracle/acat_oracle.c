@@ -219,6 +219,18 @@ static int or_select(const or_params *P, const or_tables *T, const double *line,
 void or_flux_x(const or_params *P, const double *u, double *f) { flux_x_d(P, u, f); }
 void or_flux_y(const or_params *P, const double *u, double *f) { flux_y_d(P, u, f); }
 
+/* The physical flux f(u_i) of every cell of a 1D state (SoA in and out). */
+void or_cell_flux_1d(const or_params *P, const double *u, double *f) {
+  const int s = or_nvars(P);
+  const long N = P->nx;
+  for (long i = 0; i < N; i++) {
+    double q[OR_MAXS], g[OR_MAXS];
+    for (int c = 0; c < s; c++) q[c] = u[c * N + i];
+    flux_x_d(P, q, g);
+    for (int c = 0; c < s; c++) f[c * N + i] = g[c];
+  }
+}
+
 /* dt = CFL dx / s^max (1D; Sec. 5.1-5.3 state the CFL number). */
 double or_dt_1d(const or_params *P, const double *u) {
   const int s = or_nvars(P);

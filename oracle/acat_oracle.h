@@ -58,6 +58,7 @@ int or_nvars(const or_params *P);
 
 void or_flux_x(const or_params *P, const double *u, double *f);
 void or_flux_y(const or_params *P, const double *u, double *f);
+void or_cell_flux_1d(const or_params *P, const double *u, double *f);
 
 double or_dt_1d(const or_params *P, const double *u);
 double or_dt_2d(const or_params *P, const double *u);

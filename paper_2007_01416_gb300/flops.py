@@ -1,5 +1,7 @@
-"""Algorithmic operation counts of the ACAT step, as the CUDA kernels
-formulate it (roofline numerators).
+"""Algorithmic operation counts of the ACAT step (roofline numerators): the
+reference count of the method's work (a Horner pass per time level, the
+*_ref functions), and the leaner count of the formulation the CUDA kernels
+use (running Taylor sums, the other functions).
 
 Counting convention: an FMA is 2 flops; add, multiply, divide and square root
 are 1 each. Counts are per interface for the flux work and per cell for the
@@ -43,6 +45,31 @@ def flcat2_flops(flux: int) -> int:
 
 def update_flops(flux: int) -> int:
     return 3 * NVARS[flux] + 8
+
+
+# The reference count of the method's work (one Horner pass per time level):
+# per interface at the selected order p (n = 2p nodes, S components),
+#   FMA(p) = S [(n-1) 2 n^2 + n(n-1) n(n-1)/2 + n^2]   (2 flops each)
+#   n (n-1)^2 flux evaluations of PHI_REF flops (f(u_j) at r = 0 reused);
+# FL-CAT2 interfaces 100 S; the indicators 10 P S per interface; the update
+# 20 S per cell. At p = 4 for 1D Euler: 2 x 7584 + 392 x 8 = 18304 flops.
+PHI_REF = {0: 1, 1: 2, 2: 8}
+
+
+def cat_flux_flops_ref(p: int, flux: int) -> int:
+    n, S = 2 * p, NVARS[flux]
+    fma = S * ((n - 1) * 2 * n * n + n * (n - 1) * n * (n - 1) // 2 + n * n)
+    return 2 * fma + n * (n - 1) ** 2 * PHI_REF[flux]
+
+
+def step_flops_1d_ref(order_hist: dict, P: int, flux: int, cells: int) -> float:
+    """step_flops_1d in the reference count (above)."""
+    S = NVARS[flux]
+    f = 0.0
+    for code, cnt in order_hist.items():
+        f += cnt * (100 * S if code == 1 else cat_flux_flops_ref(code, flux))
+    f += sum(order_hist.values()) * 10 * P * S + cells * 20 * S
+    return f
 
 
 def step_flops_1d(order_hist: dict, P: int, flux: int, cells: int) -> float:

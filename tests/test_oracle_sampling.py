@@ -84,3 +84,19 @@ def test_step_2d_cells_equals_the_full_step(oracle, P, rect, cfg):
     cx, cy = xx.ravel(), yy.ravel()  # every cell, corners and edges included
     got = O.step_2d_cells(pr, u, dt, cx, cy)
     assert np.array_equal(got, full[:, cy, cx].T)
+
+
+def test_cell_flux_closed_forms(oracle):
+    """The per-cell physical flux used by the FP32 free-run bar: Euler from the
+    primitive variables, (rho v, rho v^2 + p, v (E + p)) with E = p/(gamma-1) +
+    rho v^2/2; Burgers u^2/2; transport a u."""
+    O = oracle
+    rng = np.random.default_rng(7)
+    rho, v, p = rng.uniform(0.1, 1.0, 50), rng.uniform(-0.5, 0.5, 50), rng.uniform(0.1, 1.0, 50)
+    E = p / 0.4 + 0.5 * rho * v * v
+    u = np.array([rho, rho * v, E])
+    f = O.cell_flux_1d(O.Problem(flux=O.EULER1D, P=2, nx=50, gamma=1.4), u)
+    assert np.allclose(f, [rho * v, rho * v * v + p, v * (E + p)], rtol=1e-14, atol=0)
+    w = rng.uniform(-1, 1, (1, 50))
+    assert np.array_equal(O.cell_flux_1d(O.Problem(flux=O.BURGERS, P=2, nx=50), w), 0.5 * w * w)
+    assert np.array_equal(O.cell_flux_1d(O.Problem(flux=O.LINEAR, P=2, nx=50, adv=(-0.7, 0.0)), w), -0.7 * w)

@@ -7,9 +7,12 @@ match the FP64 oracle bit for bit from the same state value hi + lo (the
 decisions are taken in FP64 on that exact value); one step agrees with the
 oracle within 1e-7 of max|u| (float rounding of flux increments, at most
 O(1) across a discontinuity: eps32 * lambda * |jump of f| * 4 < 1e-7).
-Free runs are compared in L1 (relative, steps x 1e-7): the scheme is a discontinuous
-map of the state (order thresholds), so trajectories that differ by rounding
-split locally where a decision is near its threshold; Linf is reported.
+Free runs: the scheme is a discontinuous map of the state (order thresholds),
+so trajectories that differ by rounding split locally where a decision is near
+its threshold. The FP64 GPU run shows the same against the oracle, so the FP32
+run's L1 and Linf distances to the oracle are bounded by SPLIT_K times the FP64
+run's plus the accumulated FP32 rounding bound, and its order histogram must
+track the FP64 run's (see test_free_run_f32_against_oracle).
 """
 import numpy as np
 import pytest
@@ -18,6 +21,10 @@ from paper_2007_01416_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 STEP_TOL = 1e-7
+EPS32 = 2.0 ** -24
+ROUND_C = 8.0     # float roundings an increment of the FP32 update carries, at most
+SPLIT_K = 4.0     # free runs: FP32 may deviate from the oracle 4x as much as the FP64 run
+HIST_TOL = 0.005  # free runs: order histograms within 0.5 % of the interfaces per order
 
 
 @pytest.fixture(scope="module")
@@ -98,43 +105,81 @@ def test_teacher_forced_f32(env, lpn):
     assert worst < STEP_TOL, worst
 
 
-@pytest.mark.parametrize("P,nx,steps,lpn", [(4, 4096, 1000, 1), (2, 4096, 1000, 1), (4, 4096, 1000, 2)])
-def test_free_run_f32_against_oracle(env, P, nx, steps, lpn):
-    """Free-running FP32 and FP64 GPU runs of the 1D Euler workload shape
-    against the oracle run: L1 and Linf of the final state.
+def _cell_left(a, bc):
+    """a[:, i-1] with the boundary's ghost at i = 0 (periodic wrap or copy)."""
+    g = a[:, -1:] if bc == 0 else a[:, :1]
+    return np.concatenate([g, a[:, :-1]], axis=1)
 
-    FP32: the per-step bound STEP_TOL accumulated linearly over the run,
-    steps x 1e-7 = 1e-4 in relative L1 (observed about 1e-5). FP64: 1e-5
-    relative L1, far above the 1e-12 per-step rounding: the FP64 runs split
-    from the oracle's only where an order decision is near its threshold
-    (observed about 5e-6). Linf below 1e-2 for both: a split is local."""
+
+def _rounding_bound(O, pr, u, dt):
+    """Per-cell bound of the FP32 path's rounding in one step from u: the
+    update adds lam (B + G_l - G_r), B = f(u_{i-1}) - f(u_i), G_l =
+    F_{i-1/2} - f(u_{i-1}), G_r = F_{i+1/2} - f(u_i), each a float increment
+    carrying at most ROUND_C float roundings relative to itself; the
+    compensated pair itself rounds at eps32^2 |u_i|. Returns (u_next, bound)."""
+    new, _, orders, F = O.step_1d(pr, u, dt, want_flux=True)
+    f = O.cell_flux_1d(pr, u)
+    fl = _cell_left(f, pr.bc)
+    lam = dt / pr.dx
+    b = ROUND_C * EPS32 * lam * (np.abs(fl - f) + np.abs(F[:-1].T - fl) + np.abs(F[1:].T - f)) + \
+        EPS32 ** 2 * np.abs(u)
+    return new, b
+
+
+@pytest.mark.parametrize("P,nx,steps,lpn", [(4, 4096, 1000, 1), (2, 4096, 1000, 1), (3, 4096, 1000, 1),
+                                            (4, 4096, 1000, 2), (4, 16384, 4000, 1)])
+def test_free_run_f32_against_oracle(env, P, nx, steps, lpn):
+    """Free-running FP32 and FP64 GPU runs of the 1D Euler workload (the last
+    case at the benchmark's size and step count) against the oracle run.
+
+    The scheme is a discontinuous map of the state (the order thresholds of
+    Eq. 3.2, the limiter's pieces): two evaluations that differ only in
+    rounding split where a decision is near its threshold, and the split
+    persists. The FP64 GPU run (pinned to 1e-12 per step) shows this against
+    the oracle, so the FP32 bars are set from it, per component:
+      L1, Linf of FP32 - oracle <= SPLIT_K x (those of FP64 - oracle)
+                                   + the accumulated FP32 rounding bound;
+      the order histograms of the two GPU runs' last step within HIST_TOL of
+      the interfaces per order, and the interfaces where the two trajectories'
+      orders differ at most SPLIT_K x as many as where the FP64 run's differ
+      from the oracle's (or HIST_TOL of the interfaces)."""
     torch, O, acat = env
     c = W.euler1d_riemann_entropy(nx=nx, seed=0, P=P, steps=steps)
     kw = c.problem_kwargs()
     pr = O.Problem(**kw)
     ref = c.u0.copy()
+    b1, binf = np.zeros(3), np.zeros(3)
     for _ in range(steps):
-        ref, _, _ = O.step_1d(pr, ref)
-    scale = np.abs(ref).max()
+        ref, b = _rounding_bound(O, pr, ref, O.dt_cfl(pr, ref))
+        b1 += b.sum(1)
+        binf += b.max(1)
+    _, _, ord_ref = O.step_1d(pr, ref)
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
         ctx.acat_set_launch_shape(8, lpn, 0)
         u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
         ctx.acat_run(u, steps)
         torch.cuda.synchronize()
         assert ctx.acat_status() == 0
+        _, _, ord32 = _step32(env, ctx, u.cpu().numpy(), nx)
         got32 = acat.from_pair(u.cpu().numpy())
     with acat.Context(**kw) as ctx:
         u = torch.from_numpy(c.u0.copy()).cuda()
         ctx.acat_run(u, steps)
         torch.cuda.synchronize()
+        _, _, ord64 = _step32(env, ctx, u.cpu().numpy(), nx)
         got64 = u.cpu().numpy()
-    l1_32 = np.abs(got32 - ref).mean() / np.abs(ref).mean()
-    li_32 = np.abs(got32 - ref).max() / scale
-    l1_64 = np.abs(got64 - ref).mean() / np.abs(ref).mean()
-    li_64 = np.abs(got64 - ref).max() / scale
-    print(f"P={P} lpn={lpn}: FP32 L1 {l1_32:.2e} Linf {li_32:.2e}; FP64 L1 {l1_64:.2e} Linf {li_64:.2e}")
-    assert l1_32 < steps * STEP_TOL and l1_64 < 1e-5
-    assert li_32 < 1e-2 and li_64 < 1e-2
+    s1 = np.abs(ref).sum(1)
+    l1_32, l1_64 = np.abs(got32 - ref).sum(1) / s1, np.abs(got64 - ref).sum(1) / s1
+    li_32, li_64 = np.abs(got32 - ref).max(1), np.abs(got64 - ref).max(1)
+    h32, h64 = np.bincount(ord32, minlength=5), np.bincount(ord64, minlength=5)
+    mis32, mis64 = int((ord32 != ord64).sum()), int((ord64 != ord_ref).sum())
+    print(f"P={P} nx={nx} steps={steps} lpn={lpn}: L1 FP32 {l1_32} FP64 {l1_64} bound {b1 / s1}; "
+          f"Linf FP32 {li_32} FP64 {li_64} bound {binf}; orders FP32 {h32} FP64 {h64}; "
+          f"mismatch FP32-FP64 {mis32}, FP64-oracle {mis64}")
+    assert (l1_32 <= SPLIT_K * l1_64 + b1 / s1).all()
+    assert (li_32 <= SPLIT_K * li_64 + binf).all()
+    assert (np.abs(h32 - h64) <= HIST_TOL * (nx + 1)).all()
+    assert mis32 <= max(SPLIT_K * mis64, HIST_TOL * (nx + 1))
 
 
 def test_run_host_f32(env):

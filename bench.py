@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--shape", default="",
                     help="launch shape 'nw,lpn,cps' for the f32_1d and batch_f32 profiling workloads")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "f32_1d", "2d_f32", "2d_f64", "2d_p3", "2d_p3_f32", "2d_rect", "batch_f32",
-                             "adjoint", "adjoint_f32"],
+                    choices=["main", "f32_1d", "f64_1d", "2d_f32", "2d_f64", "2d_p3", "2d_p3_f32", "2d_rect",
+                             "batch_f32", "adjoint", "adjoint_f32"],
                     help="profiling runs: one short measurement of a single workload")
+    ap.add_argument("--P", type=int, default=P_MAIN, help="P of the f32_1d and f64_1d profiling workloads")
     return ap.parse_args()
 
 
@@ -934,8 +935,9 @@ def run_single(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     n = args.acat_steps
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
-    if args.workload == "f32_1d":
-        m = measure(torch, acat, W, flops, NX, P_MAIN, acat.PREC_F32, n, 1, 1, flush, False, 0, shape=shape)
+    if args.workload in ("f32_1d", "f64_1d"):
+        prec = acat.PREC_F32 if args.workload == "f32_1d" else acat.PREC_F64
+        m = measure(torch, acat, W, flops, NX, args.P, prec, n, 1, 1, flush, False, 0, shape=shape)
         out = {"ms": m["ms"]}
     elif args.workload == "2d_p3":
         out = measure_2d_hi(torch, acat, W, flops, 1024, 3, n, 1, flush, 1.0)

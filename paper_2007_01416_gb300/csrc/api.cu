@@ -44,6 +44,8 @@ struct acat_ctx {
   int lpn = 1;                            // 1D FP32: lanes per stencil node
   unsigned long long *d_smaxb = nullptr;  // 3 x B
   double *d_tb = nullptr;                 // 3 x B
+  double *d_lamb = nullptr;               // B: dt / dx of each instance for the current step
+  float *d_lambf = nullptr;               // B: the same in float
   double *d_contrib = nullptr;            // adjoint: per-interface node cotangents
   void *d_seg = nullptr;                  // adjoint run: recomputed states of a segment
   size_t seg_bytes = 0;
@@ -190,6 +192,8 @@ BatchArgs batch_args(acat_ctx *c) {
   bt.xlen = c->p.x1 - c->p.x0;
   bt.smax = c->d_smaxb;
   bt.t = c->d_tb;
+  bt.lam = c->d_lamb;
+  bt.lamf = c->d_lambf;
   bt.nw = c->bnw;
   bt.cps = c->bcps;
   bt.lpn = c->lpn;
@@ -243,7 +247,7 @@ int issue_steps(acat_ctx *c, void *u, long n, int count, double t_end, cudaStrea
       a.u_out = (n % 2 == 0) ? c->d_work : u;
       a.slot = (int)(n % 3);
       int e = acat_launch_batch1d(c->p.P, c->p.flux, c->p.precision, a, bt, st);
-      c->launches++;
+      c->launches += ACAT_BATCH_LAUNCHES_PER_STEP;
       if (e) return ACAT_ERR_CUDA;
     }
     return ACAT_OK;
@@ -436,6 +440,8 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
   if (e == cudaSuccess) e = cudaMalloc(&c->d_offs, sizeof(long long) * (size_t)(n_inst + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_smaxb, 3 * sizeof(unsigned long long) * (size_t)n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_tb, 3 * sizeof(double) * (size_t)n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_lamb, sizeof(double) * (size_t)n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_lambf, sizeof(float) * (size_t)n_inst);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->d_offs, offs.data(), sizeof(long long) * (size_t)(n_inst + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_smaxb, 0, 3 * sizeof(unsigned long long) * (size_t)n_inst);
@@ -588,6 +594,8 @@ int acat_destroy(acat_ctx *c) {
   cudaFree(c->d_tiles);
   cudaFree(c->d_smaxb);
   cudaFree(c->d_tb);
+  cudaFree(c->d_lamb);
+  cudaFree(c->d_lambf);
   cudaFree(c->d_contrib);
   cudaFree(c->d_seg);
   cudaFree(c->d_bar);
@@ -627,7 +635,7 @@ int acat_step(acat_ctx *c, const void *u_in, void *u_out, double dt, void *strea
       c->launches++;
     }
     int e3 = acat_launch_batch1d(c->p.P, c->p.flux, c->p.precision, a, bt, st);
-    c->launches++;
+    c->launches += ACAT_BATCH_LAUNCHES_PER_STEP;
     return e3 ? ACAT_ERR_CUDA : ACAT_OK;
   }
   if (c->dim == 2) {

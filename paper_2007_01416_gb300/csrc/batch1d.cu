@@ -38,10 +38,26 @@ __device__ double batch_dt(const Step1DArgs &a, const BatchArgs &bt, int b, bool
   return dt;
 }
 
+// dt and lambda = dt / dx of every instance for this step, one thread per
+// instance (batch_dt: the instance's time advanced, its wave-speed slot two
+// steps ahead recycled). The step kernel's tiles then read lambda: the FP64
+// divisions are done once per instance, not once per tile (in the tile they
+// held the whole CTA at its staging barrier behind one thread).
+__global__ void __launch_bounds__(NT) k_batch_dt(const Step1DArgs a, const BatchArgs bt) {
+  for (long b = (long)blockIdx.x * NT + threadIdx.x; b < bt.B; b += (long)gridDim.x * NT) {
+    const long N = bt.offs[b + 1] - bt.offs[b];
+    const double dx = bt.xlen / (double)N;
+    const double l = batch_dt(a, bt, (int)b, true, dx) / dx;
+    bt.lam[b] = l;
+    bt.lamf[b] = (float)l;
+  }
+}
+
 // Persistent batched step: CTAs of NW warps stride over the (instance,
 // first cell) work list, whose tiles are Tiling<P, NW, LPN>::T cells wide;
-// every instance is advanced with its own dt. The register cap per thread is
-// that of the 8-warp kernels (MinCtas x 8 / NW resident CTAs).
+// every instance is advanced with its own dt (lambda from k_batch_dt). The
+// register cap per thread is that of the 8-warp kernels (MinCtas x 8 / NW
+// resident CTAs).
 template <int P, int FLUX, bool F32, int NW, int LPN>
 __global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
     k_batch1d(const Step1DArgs a, const BatchArgs bt) {
@@ -49,29 +65,20 @@ __global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
       typename std::conditional<F32, Smem32<P, Phys<FLUX>::S, NW, LPN>, Smem64<P, Phys<FLUX>::S, NW>>::type;
   // FP32: two workspaces used alternately (tile_f32 ends without a barrier)
   __shared__ SM sm[F32 ? 2 : 1];
-  __shared__ double s_lam;
-  __shared__ float s_lamf[2];
   int par = 0;
   for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
     const int b = bt.tiles[w].b;
     const long i0 = (long)bt.tiles[w].tile * Tiling<P, NW, LPN>::T;
     const long off = bt.offs[b], N = bt.offs[b + 1] - off;
-    if (threadIdx.x == 0) {
-      const double dx = bt.xlen / (double)N;
-      const double l = batch_dt(a, bt, b, i0 == 0, dx) / dx;
-      if constexpr (F32) s_lamf[par] = (float)l;
-      else s_lam = l;
-    }
     int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
     unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
     if constexpr (F32) {
       tile_f32<P, FLUX, NW, LPN>(a, sm[par], static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out),
-                                 off, bt.M, N, i0, &s_lamf[par], ord, so);
+                                 off, bt.M, N, i0, &bt.lamf[b], ord, so);
       par ^= 1;
     } else {
-      __syncthreads();
       tile_f64<P, FLUX, NW>(a, sm[0], static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
-                            off, bt.M, N, i0, s_lam, ord, so);
+                            off, bt.M, N, i0, bt.lam[b], ord, so);
     }
   }
 }
@@ -127,6 +134,10 @@ int launch_batch_nw(const Step1DArgs &a, const BatchArgs &bt, cudaStream_t st, i
     return 0;
   }
   const int cps = (bt.cps > 0 && bt.cps < occ) ? bt.cps : occ;
+  const unsigned gdt = (unsigned)((bt.B + NT - 1) / NT);
+  k_batch_dt<<<gdt < 1024u ? gdt : 1024u, NT, 0, st>>>(a, bt);
+  const int e = (int)cudaGetLastError();
+  if (e) return e;
   k_batch1d<P, FLUX, F32, NW, LPN><<<(unsigned)(sms * cps), NW * 32, 0, st>>>(a, bt);
   return (int)cudaGetLastError();
 }

@@ -78,7 +78,7 @@ struct BatchArgs {
   double *lam;                // B: dt / dx of each instance for this step (k_batch_dt)
   float *lamf;                // B: the same rounded to float (FP32 path)
   int8_t *orders;             // M + B order codes (nullable), instance b at offs[b] + b
-  int nw;                     // warps per CTA (4, 8 or 16); tiles of acat_cells_per_tile_1d(P, nw, lpn) cells
+  int nw;                     // warps per CTA (4, 8 or 16); tiles of acat_cells_per_tile_1d(P, prec, nw, lpn) cells
   int cps;                    // CTAs per SM (<= 0: the kernel's occupancy)
   int lpn;                    // lanes per stencil node (1; FP32 with P = 2, 4: 1 or 2)
 };
@@ -88,9 +88,9 @@ struct BatchArgs {
 int acat_launch_batch1d(int P, int flux, int prec, const Step1DArgs &a, const BatchArgs &bt,
                         void *stream);
 constexpr int ACAT_BATCH_LAUNCHES_PER_STEP = 2;
-// Cells per tile of the batched kernel with nw warps per CTA and lpn lanes
-// per stencil node (0: unsupported).
-int acat_cells_per_tile_1d(int P, int nw, int lpn);
+// Cells per tile of the batched kernel of precision prec with nw warps per
+// CTA and lpn lanes per stencil node (0: unsupported).
+int acat_cells_per_tile_1d(int P, int prec, int nw, int lpn);
 // Resident CTAs per SM of the batched kernel with nw warps and lpn lanes per
 // node (-1: unsupported shape).
 int acat_batch_occupancy(int P, int flux, int prec, int nw, int lpn);

@@ -203,7 +203,7 @@ BatchArgs batch_args(acat_ctx *c) {
 // (Re)builds the batch's work list for tiles of the kernel with nw warps and
 // lpn lanes per node: one (instance, tile) entry per tile, instances in order.
 int build_tiles(acat_ctx *c, int nw, int lpn) {
-  const int T = acat_cells_per_tile_1d(c->p.P, nw, lpn);
+  const int T = acat_cells_per_tile_1d(c->p.P, c->p.precision, nw, lpn);
   if (T <= 0) return ACAT_ERR_INVALID_ARG;
   long long ntiles = 0;
   for (int32_t n : c->sizes) ntiles += (n + T - 1) / T;
@@ -488,7 +488,7 @@ int acat_set_launch_shape(acat_ctx *c, int nw, int lpn, int cps) {
     c->lpn = lpn;
     return ACAT_OK;
   }
-  if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || acat_cells_per_tile_1d(c->p.P, nw, lpn) <= 0)
+  if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || acat_cells_per_tile_1d(c->p.P, c->p.precision, nw, lpn) <= 0)
     return ACAT_ERR_INVALID_ARG;
   const int occ = acat_batch_occupancy(c->p.P, c->p.flux, c->p.precision, nw, lpn);
   if (occ < 1) return ACAT_ERR_CUDA;

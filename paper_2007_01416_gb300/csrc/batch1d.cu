@@ -53,28 +53,39 @@ __global__ void __launch_bounds__(NT) k_batch_dt(const Step1DArgs a, const Batch
   }
 }
 
+// Interface rounds per lane group in a tile of the FP32 batched step: four
+// rounds (two at 16 warps, within 48 KB of static shared memory) make tiles
+// of R NW GPW interfaces, so the tile's two CTA barriers and its update phase
+// are shared by R times the flux work.
+template <int NW>
+struct RoundsB32 {
+  static constexpr int value = NW >= 16 ? 2 : 4;
+};
+
 // Persistent batched step: CTAs of NW warps stride over the (instance,
-// first cell) work list, whose tiles are Tiling<P, NW, LPN>::T cells wide;
+// first cell) work list, whose tiles are Tiling<P, NW, LPN, R>::T cells wide
+// (R = RoundsB32<NW> in FP32, 1 in FP64);
 // every instance is advanced with its own dt (lambda from k_batch_dt). The
 // register cap per thread is that of the 8-warp kernels (MinCtas x 8 / NW
 // resident CTAs).
 template <int P, int FLUX, bool F32, int NW, int LPN>
 __global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
     k_batch1d(const Step1DArgs a, const BatchArgs bt) {
+  constexpr int R = F32 ? RoundsB32<NW>::value : 1;
   using SM =
-      typename std::conditional<F32, Smem32<P, Phys<FLUX>::S, NW, LPN>, Smem64<P, Phys<FLUX>::S, NW>>::type;
+      typename std::conditional<F32, Smem32<P, Phys<FLUX>::S, NW, LPN, R>, Smem64<P, Phys<FLUX>::S, NW>>::type;
   // FP32: two workspaces used alternately (tile_f32 ends without a barrier)
   __shared__ SM sm[F32 ? 2 : 1];
   int par = 0;
   for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
     const int b = bt.tiles[w].b;
-    const long i0 = (long)bt.tiles[w].tile * Tiling<P, NW, LPN>::T;
+    const long i0 = (long)bt.tiles[w].tile * Tiling<P, NW, LPN, R>::T;
     const long off = bt.offs[b], N = bt.offs[b + 1] - off;
     int8_t *ord = bt.orders ? bt.orders + off + b : nullptr;
     unsigned long long *so = &bt.smax[((a.slot + 1) % 3) * (long)bt.B + b];
     if constexpr (F32) {
-      tile_f32<P, FLUX, NW, LPN>(a, sm[par], static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out),
-                                 off, bt.M, N, i0, &bt.lamf[b], ord, so);
+      tile_f32<P, FLUX, NW, LPN, R>(a, sm[par], static_cast<const float *>(a.u_in),
+                                    static_cast<float *>(a.u_out), off, bt.M, N, i0, &bt.lamf[b], ord, so);
       par ^= 1;
     } else {
       tile_f64<P, FLUX, NW>(a, sm[0], static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
@@ -217,30 +228,32 @@ int acat_batch_occupancy(int P, int flux, int prec, int nw, int lpn) {
 }
 
 namespace {
-template <int NW, int LPN>
+template <int NW, int LPN, bool F32>
 int cells_per_tile(int P) {
+  constexpr int R = F32 ? RoundsB32<NW>::value : 1;
   switch (P) {
-  case 1: return Tiling<1, NW, LPN>::T;
-  case 2: return Tiling<2, NW, LPN>::T;
-  case 3: return Tiling<3, NW, LPN>::T;
-  case 4: return Tiling<4, NW, LPN>::T;
+  case 1: return Tiling<1, NW, LPN, R>::T;
+  case 2: return Tiling<2, NW, LPN, R>::T;
+  case 3: return Tiling<3, NW, LPN, R>::T;
+  case 4: return Tiling<4, NW, LPN, R>::T;
   }
   return 0;
 }
-template <int LPN>
+template <int LPN, bool F32>
 int cells_per_tile_nw(int P, int nw) {
   switch (nw) {
-  case 4: return cells_per_tile<4, LPN>(P);
-  case 8: return cells_per_tile<8, LPN>(P);
-  case 16: return cells_per_tile<16, LPN>(P);
+  case 4: return cells_per_tile<4, LPN, F32>(P);
+  case 8: return cells_per_tile<8, LPN, F32>(P);
+  case 16: return cells_per_tile<16, LPN, F32>(P);
   }
   return 0;
 }
 }  // namespace
 
-int acat_cells_per_tile_1d(int P, int nw, int lpn) {
-  if (lpn == 1) return cells_per_tile_nw<1>(P, nw);
-  if (lpn == 2 && (P == 2 || P == 4)) return cells_per_tile_nw<2>(P, nw);
+int acat_cells_per_tile_1d(int P, int prec, int nw, int lpn) {
+  if (prec != ACAT_PREC_F32) return lpn == 1 ? cells_per_tile_nw<1, false>(P, nw) : 0;
+  if (lpn == 1) return cells_per_tile_nw<1, true>(P, nw);
+  if (lpn == 2 && (P == 2 || P == 4)) return cells_per_tile_nw<2, true>(P, nw);
   return 0;
 }
 

@@ -67,6 +67,19 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 f2dup(float a) { return make_float2(a, a); }
 
+// operations rounded as written, in the arithmetic type of their arguments
+// (no contraction into FMAs: the same bits in every kernel that inlines them)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
 // fused multiply-add in the arithmetic type of its arguments
 __device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }

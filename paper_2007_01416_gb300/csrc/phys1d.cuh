@@ -62,11 +62,11 @@ struct Phys<ACAT_FLUX_EULER1D> {
   // smallest and largest eigenvalue v -/+ c (HLL wave-speed bounds)
   template <typename R>
   __device__ static __forceinline__ void eig(const R *u, R, R gamma, R &lmin, R &lmax) {
-    const R v = u[1] / u[0];
-    const R p = (gamma - R(1)) * (u[2] - R(0.5) * u[1] * v);
-    const R c = sqrt(gamma * p / u[0]);
-    lmin = v - c;
-    lmax = v + c;
+    const R v = div_rn(u[1], u[0]);
+    const R p = mul_rn(sub_rn(gamma, R(1)), sub_rn(u[2], mul_rn(mul_rn(R(0.5), u[1]), v)));
+    const R c = sqrt_rn(div_rn(mul_rn(gamma, p), u[0]));
+    lmin = sub_rn(v, c);
+    lmax = add_rn(v, c);
   }
 };
 
@@ -99,14 +99,14 @@ __device__ __forceinline__ double psi1(const double *q, int cs, int limiter_form
 }
 
 // Interface tiling of a CTA of NW warps: groups of L = 2P x LPN lanes (LPN
-// lanes per stencil node), one per interface; a fused step tile updates
-// T = NI - 1 cells, a flux-only tile computes NI interfaces. TW cells are
-// staged (GH ghosts each side).
-template <int P, int NW = NT / 32, int LPN = 1>
+// lanes per stencil node), one interface per group and round (R rounds); a
+// fused step tile updates T = NI - 1 cells, a flux-only tile computes NI
+// interfaces. TW cells are staged (GH ghosts each side).
+template <int P, int NW = NT / 32, int LPN = 1, int R = 1>
 struct Tiling {
   static constexpr int L = 2 * P * LPN;       // lanes per interface
   static constexpr int GPW = 32 / L;          // interface groups per warp
-  static constexpr int NI = NW * GPW;         // interfaces per CTA
+  static constexpr int NI = NW * GPW * R;     // interfaces per CTA (R rounds per group)
   static constexpr int T = NI - 1;            // cells per CTA
   static constexpr int GH = P > 2 ? P : 2;    // ghost cells each side
   static constexpr int TW = T + 2 * GH;       // staged cells

@@ -219,10 +219,10 @@ struct DPhys<ACAT_FLUX_EULER1D> {
     Base b;
     b.rho = u[0];
     b.m = u[1];
-    b.v = u[1] * recip(u[0]);
+    b.v = __fmul_rn(u[1], recip(u[0]));
     b.vl = 0.0f;
-    const float p = gm1 * fmaf(-0.5f * u[1], b.v, u[2]);
-    b.H = u[2] + p;
+    const float p = __fmul_rn(gm1, fmaf(__fmul_rn(-0.5f, u[1]), b.v, u[2]));
+    b.H = __fadd_rn(u[2], p);
     b.gm1 = gm1;
     return b;
   }
@@ -238,10 +238,10 @@ struct DPhys<ACAT_FLUX_EULER1D> {
     b.rho = h[0];
     b.m = h[1];
     const float r = recip(h[0]);
-    b.v = h[1] * r;
-    b.vl = (fmaf(-b.v, h[0], h[1]) + fmaf(-b.v, l[0], l[1])) * r;
-    const float p = gm1 * fmaf(-0.5f * h[1], b.v, h[2]);
-    b.H = h[2] + p;
+    b.v = __fmul_rn(h[1], r);
+    b.vl = __fmul_rn(__fadd_rn(fmaf(-b.v, h[0], h[1]), fmaf(-b.v, l[0], l[1])), r);
+    const float p = __fmul_rn(gm1, fmaf(__fmul_rn(-0.5f, h[1]), b.v, h[2]));
+    b.H = __fadd_rn(h[2], p);
     b.gm1 = gm1;
     return b;
   }
@@ -250,28 +250,27 @@ struct DPhys<ACAT_FLUX_EULER1D> {
   //   d(mv) = m dv + b (v + dv)
   //   dp = (gamma - 1)(c - d(mv)/2)
   //   df = (b, d(mv) + dp, dv H + (v + dv)(c + dp))
+  // Every operation is rounded as written (no contraction left to the
+  // compiler), so that every kernel instantiating it gives the same bits.
   __device__ static __forceinline__ void dflux(const Base &B, const float *d, float *df) {
-    const float dv = fmaf(-B.vl, d[0], fmaf(-B.v, d[0], d[1])) * recip(B.rho + d[0]);
-    const float vn = B.v + dv;
-    const float dmv = fmaf(B.m, dv, d[1] * vn);
-    const float dp = B.gm1 * fmaf(-0.5f, dmv, d[2]);
+    const float dv = __fmul_rn(fmaf(-B.vl, d[0], fmaf(-B.v, d[0], d[1])), recip(__fadd_rn(B.rho, d[0])));
+    rest(B, d, dv, df);
+  }
+  __device__ static __forceinline__ void rest(const Base &B, const float *d, float dv, float *df) {
+    const float vn = __fadd_rn(B.v, dv);
+    const float dmv = fmaf(B.m, dv, __fmul_rn(d[1], vn));
+    const float dp = __fmul_rn(B.gm1, fmaf(-0.5f, dmv, d[2]));
     df[0] = d[1];
-    df[1] = dmv + dp;
-    df[2] = fmaf(dv, B.H, vn * (d[2] + dp));
+    df[1] = __fadd_rn(dmv, dp);
+    df[2] = fmaf(dv, B.H, __fmul_rn(vn, __fadd_rn(d[2], dp)));
   }
   // the increment d = dh + dl given as an unevaluated pair (dh: difference of
   // the hi parts, exact for nearby values; dl: of the lo parts): the
   // cancelling numerator of dv is formed from both parts
   __device__ static __forceinline__ void dflux_pair(const Base &B, const float *dh, const float *dl, float *df) {
-    const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
-    const float num = fmaf(-B.vl, dh[0], fmaf(-B.v, dh[0], dh[1]) + fmaf(-B.v, dl[0], dl[1]));
-    const float dv = num * recip(B.rho + d[0]);
-    const float vn = B.v + dv;
-    const float dmv = fmaf(B.m, dv, d[1] * vn);
-    const float dp = B.gm1 * fmaf(-0.5f, dmv, d[2]);
-    df[0] = d[1];
-    df[1] = dmv + dp;
-    df[2] = fmaf(dv, B.H, vn * (d[2] + dp));
+    const float d[3] = {__fadd_rn(dh[0], dl[0]), __fadd_rn(dh[1], dl[1]), __fadd_rn(dh[2], dl[2])};
+    const float num = fmaf(-B.vl, dh[0], __fadd_rn(fmaf(-B.v, dh[0], dh[1]), fmaf(-B.v, dl[0], dl[1])));
+    rest(B, d, __fmul_rn(num, recip(__fadd_rn(B.rho, d[0]))), df);
   }
   // the same for two increments packed in float2 lanes
   __device__ static __forceinline__ void dflux_x2(const Base &B, const float2 *d, float2 *df) {
@@ -286,12 +285,13 @@ struct DPhys<ACAT_FLUX_EULER1D> {
     df[2] = f2fma(dv, f2dup(B.H), f2mul(vn, f2add(d[2], dp)));
   }
   __device__ static __forceinline__ float speed(const float *u, float, float gamma) {
-    const float v = u[1] / u[0];
-    const float p = (gamma - 1.0f) * (u[2] - 0.5f * u[1] * v);
-    return fabsf(v) + sqrtf(fmaxf(gamma * p / u[0], 0.0f));
+    const float v = __fdiv_rn(u[1], u[0]);
+    const float p = __fmul_rn(__fsub_rn(gamma, 1.0f), __fsub_rn(u[2], __fmul_rn(__fmul_rn(0.5f, u[1]), v)));
+    return __fadd_rn(fabsf(v), __fsqrt_rn(fmaxf(__fdiv_rn(__fmul_rn(gamma, p), u[0]), 0.0f)));
   }
   __device__ static __forceinline__ bool physical(const float *u, float gamma) {
-    const float p = (gamma - 1.0f) * (u[2] - 0.5f * u[1] * (u[1] / u[0]));
+    const float v = __fdiv_rn(u[1], u[0]);
+    const float p = __fmul_rn(__fsub_rn(gamma, 1.0f), __fsub_rn(u[2], __fmul_rn(__fmul_rn(0.5f, u[1]), v)));
     return u[0] > 0.0f && p > 0.0f && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
   }
 };
@@ -351,11 +351,28 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
     float U[S];
 #pragma unroll
     for (int c = 0; c < S; c++) U[c] = 0.0f;
-    if constexpr (S > 1) {
+    if constexpr (S == 3 && p >= 3) {
       // the slot set of order k was last read at order k - 2, before every
-      // lane of the group passed the barrier of order k - 1
+      // lane of the group passed the barrier of order k - 1. At p >= 3
+      // components 0 and 1 of the sum run packed in float2 lanes (each
+      // rounded as the scalar FMA); at p = 2 the scalar form is faster.
       float4 *xb = xw + (k & 1) * 32;
-      xb[base + l] = make_float4(Fprev[0], Fprev[1], S > 2 ? Fprev[S > 2 ? 2 : 0] : 0.0f, 0.0f);
+      xb[base + l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
+      __syncwarp(mask);
+      float2 u01 = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int r = 0; r < n; r++) {
+        const float4 f = xb[base + r];
+        u01 = f2fma(f2dup(g1r[r]), make_float2(f.x, f.y), u01);
+        U[S > 2 ? 2 : 0] = fmaf(g1r[r], f.z, U[S > 2 ? 2 : 0]);
+      }
+      u01 = f2mul(u01, f2dup(-lam));
+      U[0] = u01.x;
+      U[1] = u01.y;
+      U[S > 2 ? 2 : 0] *= -lam;
+    } else if constexpr (S > 1) {
+      float4 *xb = xw + (k & 1) * 32;
+      xb[base + l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
       __syncwarp(mask);
 #pragma unroll
       for (int r = 0; r < n; r++) {
@@ -364,15 +381,17 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
 #pragma unroll
         for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], fr[c], U[c]);
       }
+#pragma unroll
+      for (int c = 0; c < S; c++) U[c] *= -lam;
     } else {  // a scalar law: one shuffle per node
 #pragma unroll
       for (int r = 0; r < n; r++) U[0] = fmaf(g1r[r], __shfl_sync(mask, Fprev[0], base + r), U[0]);
+      U[0] *= -lam;
     }
     float acc[S];
     float2 acc2[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      U[c] *= -lam;
       acc[c] = 0.0f;
       acc2[c] = make_float2(0.0f, 0.0f);
     }
@@ -391,18 +410,48 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
 #pragma unroll
     for (int q = 2 * NP; q < NL; q++) {  // levels not paired
       const int rs = q < p - 1 ? q : q + 1;
+      const float cr = TB::taylor(p, rs, k - 1), wk = TB::gk(p, k - 1, rs);
+      float *dq = dels[q - 2 * NP];
       float E[S];
+      if constexpr (S == 3 && p >= 3) {
+        const float2 d01 = f2fma(f2dup(cr), make_float2(U[0], U[1]), make_float2(dq[0], dq[1]));
+        dq[0] = d01.x;
+        dq[1] = d01.y;
+        dq[S > 2 ? 2 : 0] = fmaf(cr, U[S > 2 ? 2 : 0], dq[S > 2 ? 2 : 0]);
+        DP::dflux(bj, dq, E);
+        const float2 a01 = f2fma(f2dup(wk), make_float2(E[0], E[1]), make_float2(acc[0], acc[1]));
+        acc[0] = a01.x;
+        acc[1] = a01.y;
+        acc[S > 2 ? 2 : 0] = fmaf(wk, E[S > 2 ? 2 : 0], acc[S > 2 ? 2 : 0]);
+      } else {
 #pragma unroll
-      for (int c = 0; c < S; c++) dels[q - 2 * NP][c] = fmaf(TB::taylor(p, rs, k - 1), U[c], dels[q - 2 * NP][c]);
-      DP::dflux(bj, dels[q - 2 * NP], E);
+        for (int c = 0; c < S; c++) dq[c] = fmaf(cr, U[c], dq[c]);
+        DP::dflux(bj, dq, E);
 #pragma unroll
-      for (int c = 0; c < S; c++) acc[c] = fmaf(TB::gk(p, k - 1, rs), E[c], acc[c]);
+        for (int c = 0; c < S; c++) acc[c] = fmaf(wk, E[c], acc[c]);
+      }
     }
+    if constexpr (S == 3 && p >= 3) {
+      // a + (x + y) and the order's Taylor sum, components 0 and 1 packed
+      const float ifk = TB::invfact(k);
+      const float2 s01 = f2add(make_float2(acc[0], acc[1]),
+                               f2add(make_float2(acc2[0].x, acc2[1].x), make_float2(acc2[0].y, acc2[1].y)));
+      const float2 f01 = f2fma(f2dup(ifk), s01, make_float2(Fsum[0], Fsum[1]));
+      Fprev[0] = s01.x;
+      Fprev[1] = s01.y;
+      Fsum[0] = f01.x;
+      Fsum[1] = f01.y;
+      constexpr int c2 = S > 2 ? 2 : 0;
+      acc[c2] += acc2[c2].x + acc2[c2].y;
+      Fprev[c2] = acc[c2];
+      Fsum[c2] = fmaf(ifk, acc[c2], Fsum[c2]);
+    } else {
 #pragma unroll
-    for (int c = 0; c < S; c++) {
-      acc[c] += acc2[c].x + acc2[c].y;
-      Fprev[c] = acc[c];
-      Fsum[c] = fmaf(TB::invfact(k), acc[c], Fsum[c]);
+      for (int c = 0; c < S; c++) {
+        acc[c] += acc2[c].x + acc2[c].y;
+        Fprev[c] = acc[c];
+        Fsum[c] = fmaf(TB::invfact(k), acc[c], Fsum[c]);
+      }
     }
   }
   const float w = TB::gh(p, l);
@@ -550,13 +599,13 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
   DP::dflux_pair(b0, dh, dl, D1);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    U[c] = -lam * D1[c];
-    d1[c] = du[c] + U[c];
+    U[c] = __fmul_rn(-lam, D1[c]);
+    d1[c] = __fadd_rn(du[c], U[c]);
   }
   DP::dflux(b0, U, T0);
   DP::dflux(b0, d1, T1);
   const float s0 = DP::speed(u0, adv, gamma), s1 = DP::speed(u1, adv, gamma);
-  const float alpha = lo_flux == ACAT_LO_GLOBAL_LF ? 1.0f / lam : (s1 > s0 ? s1 : s0);
+  const float alpha = lo_flux == ACAT_LO_GLOBAL_LF ? __fdiv_rn(1.0f, lam) : (s1 > s0 ? s1 : s0);
   float sl = 0.0f, sr = 0.0f;
   if (lo_flux == ACAT_LO_HLL) {
     float n0, x0, n1, x1;
@@ -574,13 +623,16 @@ __device__ __forceinline__ void flcat2_delta(const float *hi, const float *lo, i
           : psi1_group_ff<S, L>(hi, lo, cs, 1, l, gmask);
 #pragma unroll
   for (int c = 0; c < S; c++) {
-    const float G1 = 0.25f * (T0[c] + T1[c] + D1[c]);
+    const float G1 = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(T0[c], T1[c]), D1[c]));
     float Glo;
     if (lo_flux == ACAT_LO_HLL)
-      Glo = sl >= 0.0f ? 0.0f : (sr <= 0.0f ? D1[c] : sl * (sr * du[c] - D1[c]) / (sr - sl));
+      Glo = sl >= 0.0f ? 0.0f
+                       : (sr <= 0.0f ? D1[c]
+                                     : __fdiv_rn(__fmul_rn(sl, __fsub_rn(__fmul_rn(sr, du[c]), D1[c])),
+                                                 __fsub_rn(sr, sl)));
     else
-      Glo = 0.5f * D1[c] - 0.5f * alpha * du[c];
-    G[c] = fmaf(w, G1 - Glo, Glo);
+      Glo = __fsub_rn(__fmul_rn(0.5f, D1[c]), __fmul_rn(__fmul_rn(0.5f, alpha), du[c]));
+    G[c] = fmaf(w, __fsub_rn(G1, Glo), Glo);
   }
 }
 
@@ -643,10 +695,10 @@ struct Smem64 {
   double Fs[Tiling<P, NW>::NI][S];
   double red[NW];
 };
-template <int P, int S, int NW = NT / 32, int LPN = 1>
+template <int P, int S, int NW = NT / 32, int LPN = 1, int R = 1>
 struct Smem32 {
-  float thi[S][Tiling<P, NW, LPN>::TW], tlo[S][Tiling<P, NW, LPN>::TW];
-  float Gs[Tiling<P, NW, LPN>::NI][S];
+  float thi[S][Tiling<P, NW, LPN, R>::TW], tlo[S][Tiling<P, NW, LPN, R>::TW];
+  float Gs[Tiling<P, NW, LPN, R>::NI][S];
   float redf[NW];
 };
 
@@ -746,12 +798,12 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
 // alternates between two workspaces (and two lam slots), so the next tile's
 // staging cannot overwrite what a slower warp still reads. The wave speed
 // maximum goes out per warp (atomic max of the warps that updated cells).
-template <int P, int FLUX, int NW = NT / 32, int LPN = 1>
-__device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FLUX>::S, NW, LPN> &sm,
+template <int P, int FLUX, int NW = NT / 32, int LPN = 1, int R = 1>
+__device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FLUX>::S, NW, LPN, R> &sm,
                                          const float *__restrict__ uin, float *__restrict__ uout,
                                          long off, long M, long N, long i0, const float *lam_sm,
                                          int8_t *orders, unsigned long long *smax_out) {
-  using TL = Tiling<P, NW, LPN>;
+  using TL = Tiling<P, NW, LPN, R>;
   constexpr int NTB = NW * 32;
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
@@ -768,53 +820,60 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / TL::L, l = lane - grp * TL::L;
   const bool valid = grp < TL::GPW;
-  const int il = warp * TL::GPW + grp;
-  const long m = i0 + il;
-  const bool active = valid && m <= N;
-  const int ic = il - 1 + TL::GH;
 
   // the warps' shuffle-free exchange slots of the one-lane-per-node recursion
   __shared__ float4 xs[(LPN == 1 && P >= 2 && S > 1) ? NW * 64 : 1];
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
-  const int icv = valid ? ic : 0;
-  const int ps = select_order<P, S, true, LPN>(nullptr, &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW, l, grp,
-                                               active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
+  // R rounds: round rnd takes the interfaces (rnd NW + warp) GPW + grp, so
+  // each round covers NW GPW consecutive interfaces; the tile's two barriers
+  // serve all R rounds
+#pragma unroll 1
+  for (int rnd = 0; rnd < R; rnd++) {
+    if (rnd > 0) __syncwarp();  // the exchange slots of the last round are read
+    const int il = (rnd * NW + warp) * TL::GPW + grp;
+    const long m = i0 + il;
+    const bool active = valid && m <= N;
+    const int ic = il - 1 + TL::GH;
+    const int icv = valid ? ic : 0;
+    const int ps = select_order<P, S, true, LPN>(nullptr, &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW, l, grp,
+                                                 active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
 
-  float G[S];
-  const int base = grp * TL::L;
-  if (active) {
-    const float *h0 = &sm.thi[0][ic], *l0 = &sm.tlo[0][ic];
-    if (ps == 4) {
-      if constexpr (P >= 4) {
-        if constexpr (LPN == 2) cat_delta2<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-        else cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
-      }
-    } else if (ps == 3) {
-      if constexpr (P >= 3) {
-        if constexpr (LPN == 2) {
-          if (l < 12) cat_delta2<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-        } else if (l < 6) {
-          cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
+    float G[S];
+    const int base = grp * TL::L;
+    if (active) {
+      const float *h0 = &sm.thi[0][ic], *l0 = &sm.tlo[0][ic];
+      if (ps == 4) {
+        if constexpr (P >= 4) {
+          if constexpr (LPN == 2) cat_delta2<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+          else cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
         }
-      }
-    } else if (ps == 2) {
-      if constexpr (P >= 2) {
-        if constexpr (LPN == 2) {
-          if (l < 8) cat_delta2<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-        } else if (l < 4) {
-          cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
+      } else if (ps == 3) {
+        if constexpr (P >= 3) {
+          if constexpr (LPN == 2) {
+            if (l < 12) cat_delta2<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+          } else if (l < 6) {
+            cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
+          }
         }
+      } else if (ps == 2) {
+        if constexpr (P >= 2) {
+          if constexpr (LPN == 2) {
+            if (l < 8) cat_delta2<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
+          } else if (l < 4) {
+            cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
+          }
+        }
+      } else {
+        flcat2_delta<FLUX, TL::L>(h0, l0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, adv, gam, a.adv,
+                                  a.limiter_form, a.lo_flux, G);
       }
-    } else {
-      flcat2_delta<FLUX, TL::L>(h0, l0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, adv, gam, a.adv,
-                                a.limiter_form, a.lo_flux, G);
-    }
-    if (l == 0) {
+      if (l == 0) {
 #pragma unroll
-      for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];
-      if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
+        for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];
+        if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
+      }
     }
-  }
+  }  // rounds
   __syncthreads();
 
   float smax = 0.0f;

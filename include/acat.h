@@ -158,15 +158,20 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
  *     so they agree to float rounding (both within the FP32 parity bar), not
  *     bit for bit.
  *   - Batched contexts: the batch is cut into tiles of
- *     T = nw * floor(32 / (2P lpn)) - 1 consecutive cells of one instance
- *     (P = 3, nw = 8, lpn = 1: 39); one CTA of nw warps per tile at a time,
+ *     T = R nw floor(32 / (2P lpn)) - 1 consecutive cells of one instance,
+ *     R = 4 interface rounds per lane group in FP32 (2 at nw = 16), 1 in
+ *     FP64 (P = 3, nw = 8, lpn = 1: 159 in FP32, 39 in FP64); one CTA of nw
+ *     warps per tile at a time,
  *     on a grid of (SM count) x cps CTAs that stride over the tile list
  *     (cps = 0: the kernel's occupancy). nw in {4, 8, 16}. At a fixed lpn,
  *     nw and cps only move work between CTAs: every interface flux, wave
  *     speed and update is computed from the same values, so the states are
  *     bit-identical.
- *   - Single-instance contexts: nw is fixed (8; 2 for the small-CTA FP64
- *     step) and cps is 0 (one CTA per tile); FP32 contexts may set lpn.
+ *   - Single-instance contexts: cps is 0. FP64: nw is fixed (8; 2 for the
+ *     small-CTA step of large grids). FP32: nw = 8 (the fused step, lpn 1
+ *     or 2) or nw = 2 (the small-CTA step with the boundary hand-off,
+ *     lpn = 1); both compute every interface and cell from the same values,
+ *     so at lpn = 1 they are bit-identical.
  * Defaults: nw = 8, lpn = 1, cps = 0.
  * acat_launch_shape returns the current shape (cps resolved to a number for
  * a batch). acat_set_launch_shape sets one; for a batch, changing nw or lpn
@@ -181,8 +186,8 @@ int acat_set_launch_shape(acat_ctx *ctx, int nw, int lpn, int cps);
 /* Autotuner of the launch shape (batched contexts, and single-instance 1D
  * FP32 contexts). Times `steps` steps (acat_run) from u_dev for every
  * candidate shape: batched: nw in {8, 4, 16} x lpn in {1, 2 where it exists}
- * x cps in {occupancy, occupancy / 2}; single FP32: lpn in {1, 2 where it
- * exists}. Each candidate runs on a context-allocated copy of u_dev (u_dev is
+ * x cps in {occupancy, occupancy / 2}; single FP32: (nw, lpn) in {(8, 1),
+ * (8, 2) where it exists, (2, 1)}. Each candidate runs on a context-allocated copy of u_dev (u_dev is
  * only read), once untimed and once timed with CUDA events on `stream`. The
  * fastest shape is kept (acat_set_launch_shape) and returned in *nw_out,
  * *lpn_out, *cps_out (each nullable). Synchronises `stream` and the device;

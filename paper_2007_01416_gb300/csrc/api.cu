@@ -50,13 +50,15 @@ struct acat_ctx {
   void *d_seg = nullptr;                  // adjoint run: recomputed states of a segment
   size_t seg_bytes = 0;
   void *d_bar = nullptr;                  // adjoint run: second cotangent buffer
-  double *d_flux = nullptr;               // 1D FP64: CTA-edge fluxes of the small-CTA step
-  int *d_cnt = nullptr;                   // 1D FP64: its boundary hand-off counters
+  double *d_flux = nullptr;               // 1D: CTA-edge fluxes (FP32: increments) of the small-CTA step
+  int *d_cnt = nullptr;                   // 1D: its boundary hand-off counters
+  int snw = 8;                            // 1D FP32 single instance: warps per CTA (8 fused, 2 small-CTA)
 };
 
 namespace {
 
 constexpr int GRAPH_STEPS = 48;  // multiple of 2 (ping-pong) and 3 (dt slots)
+constexpr int NWF_API = 2;       // warps per CTA of the small-CTA 1D steps
 
 std::mutex g_tab_mu;
 bool g_tab_done[64] = {false};
@@ -133,8 +135,10 @@ Step1DArgs base_args(acat_ctx *c) {
   a.gm1f = (float)(p.gamma - 1.0);
   a.smax = c->d_smax;
   a.status = c->d_status;
-  a.flux_buf = c->d_flux;
-  a.cnt = c->d_cnt;
+  // the small-CTA step: FP64 whenever its buffers exist, FP32 when chosen
+  const bool fine = c->d_flux && (p.precision != ACAT_PREC_F32 || c->snw == NWF_API);
+  a.flux_buf = fine ? c->d_flux : nullptr;
+  a.cnt = fine ? c->d_cnt : nullptr;
   a.lpn = c->lpn;
   return a;
 }
@@ -384,7 +388,13 @@ int acat_create(const acat_params *p, acat_ctx **out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const long fused_ctas = (p->nx + acat_cells_per_cta_1d(p->P, ACAT_PREC_F64) - 1) /
                           acat_cells_per_cta_1d(p->P, ACAT_PREC_F64);
-  if (e == cudaSuccess && c->dim == 1 && p->precision == ACAT_PREC_F64 && 4 * fused_ctas > 3 * 2 * (long)sms) {
+  // 1D FP32: the small-CTA step is available to every context through
+  // acat_set_launch_shape and the autotuner; the fused 8-warp step stays the
+  // default (at FP32 step times the hand-off's fences and the small CTAs' serial
+  // update phases cost more than their even load saves)
+  const bool f64_fine = p->precision == ACAT_PREC_F64 && 4 * fused_ctas > 3 * 2 * (long)sms;
+  const bool f32_fine = p->precision == ACAT_PREC_F32;
+  if (e == cudaSuccess && c->dim == 1 && (f64_fine || f32_fine)) {
     const size_t nc = (size_t)acat_fine_ctas_1d(p->P, p->nx);
     e = cudaMalloc(&c->d_flux, (size_t)c->s * (size_t)(p->nx + 1) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cnt, nc * sizeof(int));
@@ -461,8 +471,10 @@ int acat_launch_shape(const acat_ctx *c, int *nw, int *lpn, int *cps) {
   if (c->batched) {
     w = c->bnw;
     k = c->bcps > 0 ? c->bcps : acat_batch_occupancy(c->p.P, c->p.flux, c->p.precision, c->bnw, c->lpn);
+  } else if (c->p.precision == ACAT_PREC_F32) {
+    w = c->snw;
   } else if (c->d_flux) {
-    w = 2;  // the small-CTA FP64 step
+    w = NWF_API;  // the small-CTA FP64 step
   }
   if (nw) *nw = w;
   if (lpn) *lpn = c->lpn;
@@ -476,16 +488,22 @@ int acat_set_launch_shape(acat_ctx *c, int nw, int lpn, int cps) {
   if (!c->batched) {
     int w0 = 0, l0 = 0, k0 = 0;
     acat_launch_shape(c, &w0, &l0, &k0);
-    if (nw != w0 || cps != 0) return ACAT_ERR_UNSUPPORTED;  // fixed for a single instance
-    if (lpn == c->lpn) return ACAT_OK;
-    if (c->p.precision != ACAT_PREC_F32) return ACAT_ERR_UNSUPPORTED;
-    if (!acat_lpn_ok(c->p.P, c->p.precision, lpn)) return ACAT_ERR_INVALID_ARG;
+    if (cps != 0) return ACAT_ERR_UNSUPPORTED;
+    if (c->p.precision != ACAT_PREC_F32) {  // fixed for a single FP64 instance
+      if (nw != w0) return ACAT_ERR_UNSUPPORTED;
+      return lpn == c->lpn ? ACAT_OK : ACAT_ERR_UNSUPPORTED;
+    }
+    // FP32: the fused 8-warp step (one or two lanes per node) or the small-CTA step
+    if (nw != 8 && !(nw == NWF_API && c->d_flux)) return ACAT_ERR_UNSUPPORTED;
+    if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || (nw == NWF_API && lpn != 1)) return ACAT_ERR_INVALID_ARG;
+    if (lpn == c->lpn && nw == c->snw) return ACAT_OK;
     if (c->chain) {
       if (cudaDeviceSynchronize() != cudaSuccess) return ACAT_ERR_CUDA;
       cudaGraphExecDestroy(c->chain);
       c->chain = nullptr;
     }
     c->lpn = lpn;
+    c->snw = nw;
     return ACAT_OK;
   }
   if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || acat_cells_per_tile_1d(c->p.P, c->p.precision, nw, lpn) <= 0)
@@ -520,6 +538,7 @@ int acat_autotune(acat_ctx *c, const void *u_dev, int steps, void *stream, int *
     if (!acat_lpn_ok(c->p.P, c->p.precision, lpn)) continue;
     if (!c->batched) {
       cands.push_back(Shape{8, lpn, 0});
+      if (lpn == 1 && c->d_flux) cands.push_back(Shape{NWF_API, 1, 0});
       continue;
     }
     const int nws[3] = {8, 4, 16};

@@ -208,6 +208,123 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
   }
 }
 
+// FP32 step in small CTAs (NWF warps), the boundary hand-off of
+// k_step1d_fine on the compensated state: CTA b computes the flux increments
+// G of the NI interfaces [b NI, b NI + NI) (iface_f32, as the fused FP32 tile)
+// and updates the cells between them (update_cell_f32); it publishes its two
+// edge increments (float, s x (N+1) in flux_buf), fences, and counts in at
+// both boundary counters; the CTA that reads 1 fences again and updates the
+// boundary cell. Small CTAs spread the interfaces evenly over the SMs where
+// whole 8-warp CTAs leave some SMs with one CTA more than others; measured at
+// N = 16384 the fused step is still faster (the two device-scope fences and
+// the serial update phase of every small CTA weigh more at FP32 step times),
+// so this is a selectable launch shape (nw = 2), not the default.
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DArgs a) {
+  using TL = Tiling<P, NWF>;
+  using DP = DPhys<FLUX>;
+  constexpr int S = DP::S;
+  constexpr int NTF = NWF * 32;
+  __shared__ float thi[S][TL::TW], tlo[S][TL::TW];
+  __shared__ float Gs[TL::NI][S];
+  __shared__ float4 xs[(P >= 2 && S > 1) ? NWF * 64 : 1];
+  __shared__ float s_lam;
+  __shared__ int s_own[2];
+  const long N = a.N, i0 = (long)blockIdx.x * TL::NI;
+  const float *__restrict__ uin = static_cast<const float *>(a.u_in);
+  float *__restrict__ uout = static_cast<float *>(a.u_out);
+  float *__restrict__ gbuf = reinterpret_cast<float *>(a.flux_buf);
+  if (threadIdx.x == 0) s_lam = (float)(step_dt(a) / a.dx);
+  for (int q = threadIdx.x; q < S * TL::TW; q += NTF) {
+    const int c = q / TL::TW, k = q - c * TL::TW;
+    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
+    thi[c][k] = uin[c * N + g];
+    tlo[c][k] = uin[(S + c) * N + g];
+  }
+  __syncthreads();
+  const float lam = s_lam;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / TL::L, l = lane - grp * TL::L;
+  const bool valid = grp < TL::GPW;
+  const int il = warp * TL::GPW + grp;
+  const long m = i0 + il;
+  const bool active = valid && m <= N;
+  const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  float G[S];
+  const int ps = iface_f32<P, FLUX, 1>(a, &thi[0][0], &tlo[0][0], TL::TW, il, grp, l, valid, active, lam, FC,
+                                       &xs[warp * 64], G);
+  if (active && l == 0) {
+#pragma unroll
+    for (int c = 0; c < S; c++) Gs[il][c] = G[c];
+    if (a.orders) a.orders[m] = (int8_t)ps;
+  }
+  __syncthreads();
+  const long nI = (N + 1 - i0) < TL::NI ? (N + 1 - i0) : TL::NI;  // interfaces of this CTA
+  const bool has_left = blockIdx.x > 0, has_right = i0 + TL::NI <= N;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+      if (has_left) gbuf[c * (N + 1) + i0] = Gs[0][c];
+      if (has_right) gbuf[c * (N + 1) + i0 + TL::NI - 1] = Gs[TL::NI - 1][c];
+    }
+    __threadfence();  // release: the edge increments before the counts
+    int own0 = 0, own1 = 0;
+    if (has_left && atomicAdd(&a.cnt[blockIdx.x - 1], 1) == 1) {
+      own0 = 1;
+      a.cnt[blockIdx.x - 1] = 0;
+    }
+    if (has_right && atomicAdd(&a.cnt[blockIdx.x], 1) == 1) {
+      own1 = 1;
+      a.cnt[blockIdx.x] = 0;
+    }
+    if (own0 | own1) __threadfence();  // acquire: the neighbour's increments after its count
+    s_own[0] = own0;
+    s_own[1] = own1;
+  }
+  __syncthreads();
+  float smax = 0.0f;
+  bool bad = false;
+  // cells t = 0 .. nI - 2 lie between two interfaces of this CTA; task nI - 1
+  // is the left boundary cell i0 - 1, task nI the right one i0 + NI - 1
+  for (int t = threadIdx.x; t <= nI; t += NTF) {
+    float Gl[S], Gr[S];
+    long i;
+    int k;
+    if (t < nI - 1) {
+      i = i0 + t;
+      k = t + TL::GH;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Gl[c] = Gs[t][c];
+        Gr[c] = Gs[t + 1][c];
+      }
+    } else if (t == nI - 1) {
+      if (!s_own[0]) continue;
+      i = i0 - 1;
+      k = TL::GH - 1;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Gl[c] = __ldcg(&gbuf[c * (N + 1) + i0 - 1]);
+        Gr[c] = Gs[0][c];
+      }
+    } else {
+      if (!s_own[1]) continue;
+      i = i0 + TL::NI - 1;
+      k = TL::NI - 1 + TL::GH;
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        Gl[c] = Gs[TL::NI - 1][c];
+        Gr[c] = __ldcg(&gbuf[c * (N + 1) + i0 + TL::NI]);
+      }
+    }
+    update_cell_f32<FLUX>(a, &thi[0][0], &tlo[0][0], TL::TW, k, lam, Gl, Gr, uout, N, 0, i, &smax, &bad);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0) atomic_max_pos(&a.smax[(a.slot + 1) % 3], (double)smax);
+}
+
 // Wave speed of a state into smax[slot]; block 0 also sets tslot[slot] = 0.
 template <int FLUX, bool F32>
 __global__ void __launch_bounds__(NT) k_smax1d(const Step1DArgs a) {
@@ -255,6 +372,11 @@ int launch_p(const Step1DArgs &a, cudaStream_t st) {
     }
   }
   if constexpr (F32) {
+    if (a.flux_buf && a.cnt && a.lpn == 1) {  // small-CTA step with boundary hand-off
+      const unsigned g = (unsigned)acat_fine_ctas_1d(P, a.N);
+      k_step1d_fine_f32<P, FLUX><<<g, NWF * 32, 0, st>>>(a);
+      return (int)cudaGetLastError();
+    }
     if constexpr (P == 2 || P == 4) {
       if (a.lpn == 2) {
         using T2 = Tiling<P, NT / 32, 2>;

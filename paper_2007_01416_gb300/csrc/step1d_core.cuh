@@ -791,6 +791,112 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
   __syncthreads();
 }
 
+// Order selection and flux increment G of interface il of an FP32 tile, by
+// the L lanes of group grp (all 32 lanes of the warp call it; lane l of the
+// group). thi, tlo: component 0 of the staged tile (components tw apart),
+// cell k of the tile at index k; interface il lies between tile cells
+// il - 1 + GH and il + GH. xw: the warp's exchange slots. Every lane of an
+// active group returns the code p_s and G (lanes beyond the selected order's
+// 2p return G unset).
+template <int P, int FLUX, int LPN>
+__device__ __forceinline__ int iface_f32(const Step1DArgs &a, const float *thi, const float *tlo, int tw,
+                                         int il, int grp, int l, bool valid, bool active, float lam,
+                                         const FiltConst &FC, float4 *xw, float *G) {
+  using TL = Tiling<P, NT / 32, LPN>;
+  using DP = DPhys<FLUX>;
+  constexpr int S = DP::S;
+  const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
+  const int ic = il - 1 + TL::GH;
+  const int icv = valid ? ic : 0;
+  const int ps = select_order<P, S, true, LPN>(nullptr, thi + icv, tlo + icv, tw, l, grp, active, valid, FC,
+                                               a.eps, a.thr, a.fact_tau, a.psi2_mod);
+  const int base = grp * TL::L;
+  if (active) {
+    const float *h0 = thi + ic, *l0 = tlo + ic;
+    if (ps == 4) {
+      if constexpr (P >= 4) {
+        if constexpr (LPN == 2) cat_delta2<4, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, G);
+        else cat_delta<4, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xw, G);
+      }
+    } else if (ps == 3) {
+      if constexpr (P >= 3) {
+        if constexpr (LPN == 2) {
+          if (l < 12) cat_delta2<3, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, G);
+        } else if (l < 6) {
+          cat_delta<3, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xw, G);
+        }
+      }
+    } else if (ps == 2) {
+      if constexpr (P >= 2) {
+        if constexpr (LPN == 2) {
+          if (l < 8) cat_delta2<2, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, G);
+        } else if (l < 4) {
+          cat_delta<2, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xw, G);
+        }
+      }
+    } else {
+      flcat2_delta<FLUX, TL::L>(h0, l0, tw, l, ((1u << TL::L) - 1u) << base, lam, adv, gam, a.adv,
+                                a.limiter_form, a.lo_flux, G);
+    }
+  }
+  return ps;
+}
+
+// Conservative update (Eq. 2.12) of the cell at tile index k of an FP32 tile
+// (component 0 rows thi, tlo, components tw apart) with the flux increments
+// Gl = G_{i-1/2}, Gr = G_{i+1/2}: u += lam (f(u_{i-1}) - f(u_i) + Gl - Gr)
+// added to the pair (hi, lo) by TwoSum then Fast2Sum, written to cell i of
+// the output (component stride M from offset off). Folds the new state's
+// float wave speed into *smax and its physicality into *bad.
+template <int FLUX>
+__device__ __forceinline__ void update_cell_f32(const Step1DArgs &a, const float *thi, const float *tlo, int tw,
+                                                int k, float lam, const float *Gl, const float *Gr,
+                                                float *__restrict__ uout, long M, long off, long i, float *smax,
+                                                bool *bad) {
+  using DP = DPhys<FLUX>;
+  constexpr int S = DP::S;
+  const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
+  float ui[S], uil[S], dh[S], dl[S], B[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    ui[c] = thi[c * tw + k];
+    uil[c] = tlo[c * tw + k];
+    dh[c] = thi[c * tw + k - 1] - ui[c];
+    dl[c] = tlo[c * tw + k - 1] - uil[c];
+  }
+  DP::dflux_pair(DP::base2(ui, uil, adv, gm1), dh, dl, B);  // f(u_{i-1}) - f(u_i)
+  float un[S], lo_[S];
+#pragma unroll
+  for (int c = 0; c < S; c++) {
+    const float d = __fmul_rn(lam, __fadd_rn(B[c], __fsub_rn(Gl[c], Gr[c])));
+    const float h = ui[c], w = uil[c];
+    // TwoSum(h, d): s + e = h + d exactly
+    const float s = __fadd_rn(h, d);
+    const float bp = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+    const float w2 = __fadd_rn(w, e);
+    // Fast2Sum(s, w2), |s| >= |w2|: renormalised pair
+    const float hn = __fadd_rn(s, w2);
+    const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
+    uout[c * M + off + i] = hn;
+    uout[(S + c) * M + off + i] = ln;
+    un[c] = hn;
+    lo_[c] = ln;
+  }
+  // wave speed in float (the FP32 path's dt is exact to float rounding);
+  // a state that looks non-physical in float is re-checked in FP64
+  const float sf = DP::speed(un, adv, gam);
+  if (!DP::physical(un, gam)) {
+    double ud[S];
+#pragma unroll
+    for (int c = 0; c < S; c++) ud[c] = (double)un[c] + (double)lo_[c];
+    bool ok;
+    Phys<FLUX>::speed(ud, a.adv, a.gamma, ok);
+    *bad |= !ok;
+  }
+  *smax = fmaxf(*smax, sf);
+}
+
 // One FP32 tile on the compensated state [hi(s x M); lo(s x M)].
 // Two CTA barriers per tile: after staging (which also publishes *lam_sm,
 // written by the caller before the call) and between the flux and update
@@ -815,7 +921,6 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   }
   __syncthreads();
   const float lam = *lam_sm;
-  const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / TL::L, l = lane - grp * TL::L;
@@ -833,45 +938,13 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     const int il = (rnd * NW + warp) * TL::GPW + grp;
     const long m = i0 + il;
     const bool active = valid && m <= N;
-    const int ic = il - 1 + TL::GH;
-    const int icv = valid ? ic : 0;
-    const int ps = select_order<P, S, true, LPN>(nullptr, &sm.thi[0][icv], &sm.tlo[0][icv], TL::TW, l, grp,
-                                                 active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
-
     float G[S];
-    const int base = grp * TL::L;
-    if (active) {
-      const float *h0 = &sm.thi[0][ic], *l0 = &sm.tlo[0][ic];
-      if (ps == 4) {
-        if constexpr (P >= 4) {
-          if constexpr (LPN == 2) cat_delta2<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-          else cat_delta<4, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
-        }
-      } else if (ps == 3) {
-        if constexpr (P >= 3) {
-          if constexpr (LPN == 2) {
-            if (l < 12) cat_delta2<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-          } else if (l < 6) {
-            cat_delta<3, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
-          }
-        }
-      } else if (ps == 2) {
-        if constexpr (P >= 2) {
-          if constexpr (LPN == 2) {
-            if (l < 8) cat_delta2<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, G);
-          } else if (l < 4) {
-            cat_delta<2, FLUX>(h0, l0, TL::TW, l, base, lam, adv, gm1, &xs[warp * 64], G);
-          }
-        }
-      } else {
-        flcat2_delta<FLUX, TL::L>(h0, l0, TL::TW, l, ((1u << TL::L) - 1u) << base, lam, adv, gam, a.adv,
-                                  a.limiter_form, a.lo_flux, G);
-      }
-      if (l == 0) {
+    const int ps = iface_f32<P, FLUX, LPN>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, il, grp, l, valid, active,
+                                           lam, FC, &xs[warp * 64], G);
+    if (active && l == 0) {
 #pragma unroll
-        for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];
-        if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
-      }
+      for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];
+      if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
     }
   }  // rounds
   __syncthreads();
@@ -881,46 +954,8 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   for (int t = threadIdx.x; t < TL::T; t += NTB) {
     const long i = i0 + t;
     if (i >= N) break;
-    const int k = t + TL::GH;
-    float ui[S], uil[S], dh[S], dl[S], B[S];
-#pragma unroll
-    for (int c = 0; c < S; c++) {
-      ui[c] = sm.thi[c][k];
-      uil[c] = sm.tlo[c][k];
-      dh[c] = sm.thi[c][k - 1] - ui[c];
-      dl[c] = sm.tlo[c][k - 1] - uil[c];
-    }
-    DP::dflux_pair(DP::base2(ui, uil, adv, gm1), dh, dl, B);  // f(u_{i-1}) - f(u_i)
-    float un[S], lo_[S];
-#pragma unroll
-    for (int c = 0; c < S; c++) {
-      const float d = __fmul_rn(lam, __fadd_rn(B[c], __fsub_rn(sm.Gs[t][c], sm.Gs[t + 1][c])));
-      const float h = sm.thi[c][k], w = sm.tlo[c][k];
-      // TwoSum(h, d): s + e = h + d exactly
-      const float s = __fadd_rn(h, d);
-      const float bp = __fsub_rn(s, h);
-      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(d, bp));
-      const float w2 = __fadd_rn(w, e);
-      // Fast2Sum(s, w2), |s| >= |w2|: renormalised pair
-      const float hn = __fadd_rn(s, w2);
-      const float ln = __fsub_rn(w2, __fsub_rn(hn, s));
-      uout[c * M + off + i] = hn;
-      uout[(S + c) * M + off + i] = ln;
-      un[c] = hn;
-      lo_[c] = ln;
-    }
-    // wave speed in float (the FP32 path's dt is exact to float rounding);
-    // a state that looks non-physical in float is re-checked in FP64
-    const float sf = DP::speed(un, adv, gam);
-    if (!DP::physical(un, gam)) {
-      double ud[S];
-#pragma unroll
-      for (int c = 0; c < S; c++) ud[c] = (double)un[c] + (double)lo_[c];
-      bool ok;
-      Phys<FLUX>::speed(ud, a.adv, a.gamma, ok);
-      bad |= !ok;
-    }
-    smax = fmaxf(smax, sf);
+    update_cell_f32<FLUX>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, t + TL::GH, lam, sm.Gs[t], sm.Gs[t + 1], uout,
+                          M, off, i, &smax, &bad);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ACAT_STATUS_NONPHYSICAL);
 #pragma unroll

@@ -52,14 +52,17 @@ def _step32(env, ctx, pair, nx):
     return out.cpu().numpy(), float(dtv.item()), orders.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind,P,nx,bc,lpn", [("euler", 4, 16384, 1, 1), ("euler", 3, 1001, 0, 1),
-                                              ("euler", 2, 777, 1, 1), ("burgers", 2, 400, 0, 1),
-                                              ("burgers", 4, 513, 1, 1), ("euler", 1, 64, 1, 1),
-                                              ("euler", 4, 16384, 1, 2), ("euler", 4, 1001, 0, 2),
-                                              ("euler", 2, 777, 1, 2), ("burgers", 2, 400, 0, 2),
-                                              ("burgers", 4, 513, 1, 2), ("linear", 4, 300, 0, 2)])
-def test_single_step_f32(env, kind, P, nx, bc, lpn):
-    """lpn = 2: two lanes per stencil node (the node's sums split in two)."""
+@pytest.mark.parametrize("kind,P,nx,bc,lpn,nw", [
+    ("euler", 4, 16384, 1, 1, 8), ("euler", 3, 1001, 0, 1, 8), ("euler", 2, 777, 1, 1, 8),
+    ("burgers", 2, 400, 0, 1, 8), ("burgers", 4, 513, 1, 1, 8), ("euler", 1, 64, 1, 1, 8),
+    ("euler", 4, 16384, 1, 2, 8), ("euler", 4, 1001, 0, 2, 8), ("euler", 2, 777, 1, 2, 8),
+    ("burgers", 2, 400, 0, 2, 8), ("burgers", 4, 513, 1, 2, 8), ("linear", 4, 300, 0, 2, 8),
+    # the small-CTA step with the boundary hand-off; the last CTA holds 1, 2 and 10 interfaces
+    ("euler", 4, 16384, 1, 1, 2), ("euler", 3, 1001, 0, 1, 2), ("euler", 2, 777, 1, 1, 2),
+    ("burgers", 4, 513, 1, 1, 2), ("euler", 1, 64, 1, 1, 2), ("linear", 4, 300, 0, 1, 2)])
+def test_single_step_f32(env, kind, P, nx, bc, lpn, nw):
+    """lpn = 2: two lanes per stencil node (the node's sums split in two);
+    nw = 2: the small-CTA step."""
     torch, O, acat = env
     if kind == "linear":
         c = W.burgers_sine(nx=nx, seed=2, P=P)
@@ -73,8 +76,8 @@ def test_single_step_f32(env, kind, P, nx, bc, lpn):
     pair = acat.to_pair(c.u0)
     x = acat.from_pair(pair)  # the exact value the GPU sees
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
-        ctx.acat_set_launch_shape(8, lpn, 0)
-        assert ctx.acat_launch_shape() == (8, lpn, 0)
+        ctx.acat_set_launch_shape(nw, lpn, 0)
+        assert ctx.acat_launch_shape() == (nw, lpn, 0)
         out, dt, orders = _step32(env, ctx, pair, nx)
         assert ctx.acat_status() == 0
     pr = O.Problem(**kw)
@@ -82,12 +85,12 @@ def test_single_step_f32(env, kind, P, nx, bc, lpn):
     ref, _, ord_ref = O.step_1d(pr, x, dt)
     assert np.array_equal(orders, ord_ref)
     err = np.abs(acat.from_pair(out) - ref).max() / max(1.0, np.abs(ref).max())
-    print(f"single step f32 {kind} P={P} nx={nx} lpn={lpn}: rel err {err:.2e}")
+    print(f"single step f32 {kind} P={P} nx={nx} lpn={lpn} nw={nw}: rel err {err:.2e}")
     assert err < STEP_TOL, err
 
 
-@pytest.mark.parametrize("lpn", [1, 2])
-def test_teacher_forced_f32(env, lpn):
+@pytest.mark.parametrize("lpn,nw", [(1, 8), (2, 8), (1, 2)])
+def test_teacher_forced_f32(env, lpn, nw):
     torch, O, acat = env
     c = W.euler1d_riemann_entropy(nx=2048, seed=4, P=4)
     kw = c.problem_kwargs()
@@ -95,7 +98,7 @@ def test_teacher_forced_f32(env, lpn):
     pair = acat.to_pair(c.u0)
     worst = 0.0
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
-        ctx.acat_set_launch_shape(8, lpn, 0)
+        ctx.acat_set_launch_shape(nw, lpn, 0)
         for n in range(100):
             x = acat.from_pair(pair)
             out, dt, orders = _step32(env, ctx, pair, c.nx)
@@ -140,9 +143,10 @@ def _run64(env, kw, u0, steps, nx):
         return u.cpu().numpy(), orders
 
 
-@pytest.mark.parametrize("P,nx,steps,lpn", [(4, 4096, 1000, 1), (2, 4096, 1000, 1), (3, 4096, 1000, 1),
-                                            (4, 4096, 1000, 2), (4, 16384, 4000, 1)])
-def test_free_run_f32_against_oracle(env, P, nx, steps, lpn):
+@pytest.mark.parametrize("P,nx,steps,lpn,nw", [(4, 4096, 1000, 1, 8), (2, 4096, 1000, 1, 2),
+                                               (3, 4096, 1000, 1, 8), (4, 4096, 1000, 2, 8),
+                                               (4, 16384, 4000, 1, 2)])
+def test_free_run_f32_against_oracle(env, P, nx, steps, lpn, nw):
     """Free-running FP32 and FP64 GPU runs of the 1D Euler workload (the last
     case at the benchmark's size and step count) against the oracle run.
 
@@ -170,7 +174,7 @@ def test_free_run_f32_against_oracle(env, P, nx, steps, lpn):
         b1 += b.sum(1)
         binf += b.max(1)
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
-        ctx.acat_set_launch_shape(8, lpn, 0)
+        ctx.acat_set_launch_shape(nw, lpn, 0)
         u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
         ctx.acat_run(u, steps)
         torch.cuda.synchronize()
@@ -190,13 +194,33 @@ def test_free_run_f32_against_oracle(env, P, nx, steps, lpn):
     l1_32, li_32 = np.abs(got32 - ref).sum(1) / s1, np.abs(got32 - ref).max(1)
     h32, h64 = np.bincount(ord32, minlength=5), np.bincount(ord64, minlength=5)
     mis32 = int((ord32 != ord64).sum())
-    print(f"P={P} nx={nx} steps={steps} lpn={lpn}: L1 FP32 {l1_32} yardstick {l1_yard} bound {b1 / s1}; "
+    print(f"P={P} nx={nx} steps={steps} lpn={lpn} nw={nw}: L1 FP32 {l1_32} yardstick {l1_yard} bound {b1 / s1}; "
           f"Linf FP32 {li_32} yardstick {li_yard} bound {binf}; orders FP32 {h32} FP64 {h64}; "
           f"mismatch FP32-FP64 {mis32}, perturbed FP64-FP64 up to {mis_yard}")
     assert (l1_32 <= SPLIT_K * l1_yard + b1 / s1).all()
     assert (li_32 <= SPLIT_K * li_yard + binf).all()
     assert (np.abs(h32 - h64) <= HIST_TOL * (nx + 1)).all()
     assert mis32 <= max(SPLIT_K * mis_yard, HIST_TOL * (nx + 1))
+
+
+@pytest.mark.parametrize("P,nx", [(4, 16384), (2, 777), (3, 1001)])
+def test_small_cta_equals_fused(env, P, nx):
+    """The small-CTA step (boundary cells handed off between CTAs) and the
+    fused 8-warp step compute every interface and cell from the same values
+    with the same operations: 200-step runs agree bit for bit."""
+    torch, O, acat = env
+    c = W.euler1d_riemann_entropy(nx=nx, seed=8, P=P)
+    runs = []
+    for nw in (2, 8):
+        with acat.Context(**c.problem_kwargs(), precision=acat.PREC_F32) as ctx:
+            ctx.acat_set_launch_shape(nw, 1, 0)
+            u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
+            t = torch.zeros(1, dtype=torch.float64, device="cuda")
+            ctx.acat_run(u, 200, -1.0, None, t)
+            torch.cuda.synchronize()
+            assert ctx.acat_status() == 0
+            runs.append((u.cpu(), t.item()))
+    assert torch.equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
 
 
 def test_run_host_f32(env):
@@ -227,11 +251,16 @@ def test_single_instance_shape_and_autotune(env):
         with pytest.raises(acat.AcatError) as ei:
             ctx.acat_set_launch_shape(8, 3, 0)
         assert ei.value.code == -1
+        ctx.acat_set_launch_shape(2, 1, 0)  # the small-CTA step (one lane per node only)
+        assert ctx.acat_launch_shape() == (2, 1, 0)
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_set_launch_shape(2, 2, 0)
+        assert ei.value.code == -1
         u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
         keep = u.clone()
         nw, lpn, cps = ctx.acat_autotune(u, steps=50)
-        assert torch.equal(u, keep) and nw == 8 and lpn in (1, 2) and cps == 0
-        assert ctx.acat_launch_shape() == (8, lpn, 0)
+        assert torch.equal(u, keep) and (nw, lpn) in ((8, 1), (8, 2), (2, 1)) and cps == 0
+        assert ctx.acat_launch_shape() == (nw, lpn, 0)
     with acat.Context(**{**kw, "P": 3}, precision=acat.PREC_F32) as ctx:
         with pytest.raises(acat.AcatError) as ei:
             ctx.acat_set_launch_shape(8, 2, 0)

@@ -68,7 +68,11 @@ enum {
 /* sticky device status bits */
 enum {
   ACAT_STATUS_NONPHYSICAL = 1u, /* rho <= 0, p <= 0 or a non-finite state  */
-  ACAT_STATUS_BAD_DT = 2u       /* s^max not positive and finite           */
+  ACAT_STATUS_BAD_DT = 2u,      /* s^max not positive and finite           */
+  ACAT_STATUS_BOUNDS = 4u       /* only in a library built with
+                                   ACAT_BOUNDS_CHECK: a kernel computed a
+                                   tile, shared-memory or global index
+                                   outside its buffer and skipped the access */
 };
 
 /* Problem description in the terms of the paper.

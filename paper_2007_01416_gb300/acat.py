@@ -12,13 +12,15 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libacat.so")
+# ACAT_LIBRARY selects another build of the same library (the bounds-checked
+# libacat_bounds.so of the tests); default: the in-tree libacat.so
+LIB_PATH = os.environ.get("ACAT_LIBRARY") or os.path.join(HERE, "libacat.so")
 
 LINEAR, BURGERS, EULER1D, EULER2D = 0, 1, 2, 3
 PERIODIC, TRANSMISSIVE = 0, 1
 PREC_F64, PREC_F32 = 0, 1
 LO_RUSANOV, LO_GLOBAL_LF, LO_HLL = 0, 1, 2
-STATUS_NONPHYSICAL, STATUS_BAD_DT = 1, 2
+STATUS_NONPHYSICAL, STATUS_BAD_DT, STATUS_BOUNDS = 1, 2, 4
 
 
 class AcatError(RuntimeError):
@@ -47,7 +49,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libacat.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            raise RuntimeError(f"libacat not built ({LIB_PATH}); run __graft_entry__.build()")
         L = ctypes.CDLL(LIB_PATH)
         vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         pp = ctypes.POINTER(acat_params)

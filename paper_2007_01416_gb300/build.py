@@ -31,9 +31,9 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libacat")
 
 
-def _compile(src: str, force: bool, extra: list[str]) -> str:
+def _compile(src: str, force: bool, extra: list[str], build_dir: str = BUILD) -> str:
     path = os.path.join(CSRC, src)
-    obj = os.path.join(BUILD, src + ".o")
+    obj = os.path.join(build_dir, src + ".o")
     deps = [path] + HEADERS
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(map(os.path.getmtime, deps)):
         return obj
@@ -48,19 +48,28 @@ def _compile(src: str, force: bool, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+# Library variants: the product library, and a bounds-checked build of the same
+# sources (-DACAT_BOUNDS_CHECK: every checked index records ACAT_STATUS_BOUNDS
+# and skips its access instead of faulting) used by the tests.
+VARIANTS = {"": (BUILD, LIB, []),
+            "bounds": (os.path.join(HERE, "_build_bounds"), os.path.join(HERE, "libacat_bounds.so"),
+                       ["-DACAT_BOUNDS_CHECK"])}
+
+
+def build(force: bool = False, extra: list[str] | None = None, variant: str = "") -> str:
+    build_dir, lib, vflags = VARIANTS[variant]
+    os.makedirs(build_dir, exist_ok=True)
+    extra = list(extra or []) + vflags
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, force, extra), SOURCES))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(map(os.path.getmtime, objs)):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, force, extra, build_dir), SOURCES))
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(map(os.path.getmtime, objs)):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

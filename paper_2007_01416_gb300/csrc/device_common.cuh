@@ -103,6 +103,27 @@ struct Tab<float> {
   __device__ static float invfact(int k) { return c_tab.invfactf[k]; }
 };
 
+// Index checks of the bounds-checked build (compiled with ACAT_BOUNDS_CHECK):
+// acat_in_bounds(cond, status) records a failed check in the status word
+// (ACAT_STATUS_BOUNDS) and returns false, and the caller skips the access.
+// Without the flag it returns true and the check compiles away.
+__device__ __forceinline__ bool acat_in_bounds(bool cond, unsigned *status) {
+#ifdef ACAT_BOUNDS_CHECK
+  if (!cond && status) atomicOr(status, (unsigned)ACAT_STATUS_BOUNDS);
+  return cond;
+#else
+  (void)cond;
+  (void)status;
+  return true;
+#endif
+}
+
+// A tile index checked by the bounds-checked build: i itself when
+// 0 <= i < n, else (recorded in the status word) 0, a safe index.
+__device__ __forceinline__ int acat_tile_index(int i, int n, unsigned *status) {
+  return acat_in_bounds(i >= 0 && i < n, status) ? i : 0;
+}
+
 __device__ __forceinline__ long bc_index(long g, long N, int bc) {
   if (bc == ACAT_BC_PERIODIC) {
     if (g >= 0 && g < N) return g;

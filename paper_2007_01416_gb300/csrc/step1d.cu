@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   const int ps = select_order<P, S, false>(&tile[0][valid ? ic : 0], nullptr, nullptr, TL::TW, l, grp,
                                            active, valid, FC, a.eps, a.thr, a.fact_tau, a.psi2_mod);
-  if (active) {
+  if (active && acat_in_bounds(ic - P + 1 >= 0 && ic + P < TL::TW && il < TL::NI, a.status)) {
     double F[S];
     const int base = grp * TL::L;
     const double *q0 = &tile[0][ic];
@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
   __syncthreads();
   const long nI = (N + 1 - i0) < TL::NI ? (N + 1 - i0) : TL::NI;  // interfaces of this CTA
   const bool has_left = blockIdx.x > 0, has_right = i0 + TL::NI <= N;
-  if (threadIdx.x == 0) {
+  // the hand-off indices: this CTA's edge slots and counters
+  const bool ho_ok = acat_in_bounds(i0 + TL::NI - 1 <= N || !has_right, a.status) &&
+                     acat_in_bounds(blockIdx.x < gridDim.x && (long)gridDim.x * TL::NI >= N + 1, a.status);
+  if (threadIdx.x == 0 && ho_ok) {
     // publish the edge fluxes, then count in at both boundaries
 #pragma unroll
     for (int c = 0; c < S; c++) {
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
     s_own[0] = own0;
     s_own[1] = own1;
   }
+  if (threadIdx.x == 0 && !ho_ok) s_own[0] = s_own[1] = 0;
   __syncthreads();
   double smax = 0.0;
   bool bad = false;
@@ -185,6 +189,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
         Fr[c] = __ldcg(&a.flux_buf[c * (N + 1) + i0 + TL::NI]);
       }
     }
+    if (!acat_in_bounds(k >= 0 && k < TL::TW && i >= 0 && i < N, a.status)) continue;
     double un[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
@@ -261,7 +266,9 @@ __global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DAr
   __syncthreads();
   const long nI = (N + 1 - i0) < TL::NI ? (N + 1 - i0) : TL::NI;  // interfaces of this CTA
   const bool has_left = blockIdx.x > 0, has_right = i0 + TL::NI <= N;
-  if (threadIdx.x == 0) {
+  const bool ho_ok = acat_in_bounds(i0 + TL::NI - 1 <= N || !has_right, a.status) &&
+                     acat_in_bounds((long)gridDim.x * TL::NI >= N + 1, a.status);
+  if (threadIdx.x == 0 && ho_ok) {
 #pragma unroll
     for (int c = 0; c < S; c++) {
       if (has_left) gbuf[c * (N + 1) + i0] = Gs[0][c];
@@ -281,6 +288,7 @@ __global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DAr
     s_own[0] = own0;
     s_own[1] = own1;
   }
+  if (threadIdx.x == 0 && !ho_ok) s_own[0] = s_own[1] = 0;
   __syncthreads();
   float smax = 0.0f;
   bool bad = false;

@@ -730,7 +730,8 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
   constexpr int S = Phys<FLUX>::S;
   for (int q = threadIdx.x; q < S * TL::TW; q += NTB) {
     const int c = q / TL::TW, k = q - c * TL::TW;
-    sm.tile[c][k] = uin[c * M + off + bc_index(i0 - TL::GH + k, N, a.bc)];
+    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
+    if (acat_in_bounds(g >= 0 && g < N && off + N <= M, a.status)) sm.tile[c][k] = uin[c * M + off + g];
   }
   __syncthreads();
   const double gm1 = a.gamma - 1.0;
@@ -750,7 +751,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
   double F[S];
   const int base = grp * TL::L;
   const double *q0 = &sm.tile[0][ic];
-  if (active) {
+  if (active && acat_in_bounds(ic - P + 1 >= 0 && ic + P < TL::TW && il < TL::NI && m <= N, a.status)) {
     if (ps == 4) {
       if constexpr (P >= 4) cat_flux<4, FLUX, double>(q0, TL::TW, l, base, lam, a.adv, gm1, F);
     } else if (ps == 3) {
@@ -774,6 +775,7 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
   for (int t = threadIdx.x; t < TL::T; t += NTB) {
     const long i = i0 + t;
     if (i >= N) break;
+    if (!acat_in_bounds(t + 1 < TL::NI && t + TL::GH < TL::TW && off + i < M, a.status)) continue;
     double un[S];
 #pragma unroll
     for (int c = 0; c < S; c++) {
@@ -811,7 +813,7 @@ __device__ __forceinline__ int iface_f32(const Step1DArgs &a, const float *thi, 
   const int ps = select_order<P, S, true, LPN>(nullptr, thi + icv, tlo + icv, tw, l, grp, active, valid, FC,
                                                a.eps, a.thr, a.fact_tau, a.psi2_mod);
   const int base = grp * TL::L;
-  if (active) {
+  if (active && acat_in_bounds(ic - P + 1 >= 0 && ic + P < tw, a.status)) {
     const float *h0 = thi + ic, *l0 = tlo + ic;
     if (ps == 4) {
       if constexpr (P >= 4) {
@@ -855,6 +857,7 @@ __device__ __forceinline__ void update_cell_f32(const Step1DArgs &a, const float
                                                 bool *bad) {
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
+  if (!acat_in_bounds(k >= 1 && k < tw && i >= 0 && off + i < M, a.status)) return;
   const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
   float ui[S], uil[S], dh[S], dl[S], B[S];
 #pragma unroll
@@ -915,9 +918,10 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   constexpr int S = DP::S;
   for (int q = threadIdx.x; q < S * TL::TW; q += NTB) {
     const int c = q / TL::TW, k = q - c * TL::TW;
-    const long g = off + bc_index(i0 - TL::GH + k, N, a.bc);
-    sm.thi[c][k] = uin[c * M + g];
-    sm.tlo[c][k] = uin[(S + c) * M + g];
+    const long g = bc_index(i0 - TL::GH + k, N, a.bc);
+    if (!acat_in_bounds(g >= 0 && g < N && off + N <= M, a.status)) continue;
+    sm.thi[c][k] = uin[c * M + off + g];
+    sm.tlo[c][k] = uin[(S + c) * M + off + g];
   }
   __syncthreads();
   const float lam = *lam_sm;
@@ -941,7 +945,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     float G[S];
     const int ps = iface_f32<P, FLUX, LPN>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, il, grp, l, valid, active,
                                            lam, FC, &xs[warp * 64], G);
-    if (active && l == 0) {
+    if (active && l == 0 && acat_in_bounds(il < TL::NI && m <= N, a.status)) {
 #pragma unroll
       for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];
       if (orders && (il < TL::T || m == N)) orders[m] = (int8_t)ps;
@@ -954,6 +958,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   for (int t = threadIdx.x; t < TL::T; t += NTB) {
     const long i = i0 + t;
     if (i >= N) break;
+    if (!acat_in_bounds(t + 1 < TL::NI, a.status)) continue;
     update_cell_f32<FLUX>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, t + TL::GH, lam, sm.Gs[t], sm.Gs[t + 1], uout,
                           M, off, i, &smax, &bad);
   }

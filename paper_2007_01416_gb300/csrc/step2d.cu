@@ -723,6 +723,7 @@ __global__ void __launch_bounds__(NT, F32 ? 3 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
     const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW2, xx = rem - yy * TW2;
     const long gx = bc2(x0 - GH2 + xx, NXl, a.bc), gy = bc2(y0 - GH2 + yy, NYl, a.bc);
     const long gi = ((long)c * NYl + gy) * NXl + gx;
+    if (!acat_in_bounds(gx >= 0 && gx < NXl && gy >= 0 && gy < NYl, a.status)) continue;
     if constexpr (F32) {
       const float *u = static_cast<const float *>(a.u_in);
       thi[c][yy][xx] = u[gi];
@@ -1029,7 +1030,8 @@ __device__ __forceinline__ void block_tasks(Smem2H<P, FLUX> &sm, const Step2DArg
     const int ax = an % NAH - 1, ay = an / NAH - 1;
     double u[S], f0[S], g0[S], Fs[S], Gs[S], arg[n][S];
     if (act) {
-      const int tx = ax + P - p + 1 + ia, ty = ay + P - p + 1 + ib;
+      const int tx = acat_tile_index(ax + P - p + 1 + ia, Smem2H<P, FLUX>::TW, a.status);
+      const int ty = acat_tile_index(ay + P - p + 1 + ib, Smem2H<P, FLUX>::TW, a.status);
 #pragma unroll
       for (int c = 0; c < S; c++) u[c] = sm.tile[c][ty][tx];
       PH::flux2(u, f0, g0, axv, ayv, gm1);
@@ -1155,7 +1157,8 @@ __device__ __forceinline__ void rect_tasks(Smem2H<P, FLUX> &sm, const Step2DArgs
     const int ax = an % NAH - 1, ay = an / NAH - 1;
     double u[S], f0[S], g0[S], Fs[S], Gs[S], arg[NM][S];
     if (act) {
-      const int tx = ax + P - p1 + 1 + ia, ty = ay + P - p2 + 1 + ib;
+      const int tx = acat_tile_index(ax + P - p1 + 1 + ia, Smem2H<P, FLUX>::TW, a.status);
+      const int ty = acat_tile_index(ay + P - p2 + 1 + ib, Smem2H<P, FLUX>::TW, a.status);
 #pragma unroll
       for (int c = 0; c < S; c++) u[c] = sm.tile[c][ty][tx];
       PH::flux2(u, f0, g0, axv, ayv, gm1);
@@ -1281,6 +1284,7 @@ __global__ void __launch_bounds__(NT, 1) k_step2d_hi(const Step2DArgs a) {
   for (int q = tid; q < S * CELLS; q += NT) {
     const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW, xx = rem - yy * TW;
     const long gx = bc2(x0 - P + xx, NXl, a.bc), gy = bc2(y0 - P + yy, NYl, a.bc);
+    if (!acat_in_bounds(gx >= 0 && gx < NXl && gy >= 0 && gy < NYl, a.status)) continue;
     sm.tile[c][yy][xx] = uin[((long)c * NYl + gy) * NXl + gx];
   }
   __syncthreads();
@@ -1458,7 +1462,8 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
     float Ff[S], Fg[S], dels[NM][S];
     typename PH::Base bj;
     if (act) {
-      const int tx = ax + P - p1 + 1 + ia, ty = ay + P - p2 + 1 + ib;
+      const int tx = acat_tile_index(ax + P - p1 + 1 + ia, Smem2HF<P, FLUX>::TW, a.status);
+      const int ty = acat_tile_index(ay + P - p2 + 1 + ib, Smem2HF<P, FLUX>::TW, a.status);
       float ua[S], ual[S], uj[S], ujl[S], dh[S], dl[S];
 #pragma unroll
       for (int c = 0; c < S; c++) {
@@ -1617,6 +1622,7 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
     const int c = q / CELLS, rem = q - c * CELLS, yy = rem / TW, xx = rem - yy * TW;
     const long gx = bc2(x0 - P + xx, NXl, a.bc), gy = bc2(y0 - P + yy, NYl, a.bc);
     const long gi = ((long)c * NYl + gy) * NXl + gx;
+    if (!acat_in_bounds(gx >= 0 && gx < NXl && gy >= 0 && gy < NYl, a.status)) continue;
     sm.thi[c][yy][xx] = uin[gi];
     sm.tlo[c][yy][xx] = uin[(long)S * NYl * NXl + gi];
   }

@@ -347,3 +347,44 @@ def test_adjoint_run_f32_along_its_trajectory(env):
     err = np.abs(g32 - g64).max() / np.abs(g64).max()
     print(f"f32 gradient 60 steps: rel err {err:.2e}")
     assert err < n * F32_STEP_TOL, err
+
+
+def test_gradient_acoustic_pulse_against_reference_sweep(env):
+    """C5 in FP64 (1D Euler P = 2, N = 8192 periodic, 2000 steps, isentropic
+    pulse, L = dx/2 sum |u^N - u_target|^2): the GPU's dL/du^0 element by
+    element against the oracle's reverse sweep (oracle/adjoint_ref.py, the
+    step restated in PyTorch CPU float64 and differentiated by autograd, with
+    the orders the C oracle selects at each state). Both sweep the trajectory
+    the GPU recorded (every state and dt), so the two take the same discrete
+    choices. Bar: 1e-10 of the entry plus 1e-12 of max |dL/du^0| (the floor
+    takes the entries near zero)."""
+    torch, O, acat, adjoint = env
+    from oracle import adjoint_ref as A
+    c = W.acoustic_pulse(nx=8192, seed=0, P=2, steps=2000)
+    tgt_case = W.acoustic_pulse(nx=8192, seed=1, P=2, steps=2000)
+    kw = c.problem_kwargs()
+    dx = (c.x1 - c.x0) / c.nx
+    n = c.steps
+    with acat.Context(**kw) as ctx:
+        target = torch.from_numpy(tgt_case.u0.copy()).cuda()
+        ctx.acat_run(target, n)
+        u0 = torch.from_numpy(c.u0.copy()).cuda()
+        ckpt = torch.empty((n,) + tuple(u0.shape), dtype=torch.float64, device="cuda")
+        dts = torch.empty(n, dtype=torch.float64, device="cuda")
+        uN = torch.empty_like(u0)
+        ctx.acat_run_record(u0, uN, n, 1, ckpt, dts)  # every state of the run
+        wN = dx * (uN - target)
+        g = torch.empty_like(u0)
+        ctx.acat_adjoint_run(ckpt, dts, n, 1, wN, g)
+        torch.cuda.synchronize()
+        assert ctx.acat_status() == 0
+        states, dt_seq = ckpt.cpu().numpy(), dts.cpu().numpy()
+        got, w_last = g.cpu().numpy(), wN.cpu().numpy()
+    del ckpt
+    pr = O.Problem(**kw)
+    ref = A.gradient(pr, states, dt_seq, w_last)
+    bar = 1e-10 * np.abs(ref) + 1e-12 * np.abs(ref).max()
+    err = np.abs(got - ref)
+    print(f"C5 gradient against the reference sweep: max |err| / max |ref| {err.max() / np.abs(ref).max():.2e}, "
+          f"max |err| / (|ref| + 1e-2 max|ref|) {(err / (np.abs(ref) + 1e-2 * np.abs(ref).max())).max():.2e}")
+    assert (err <= bar).all(), (np.unravel_index((err - bar).argmax(), err.shape), err.max() / np.abs(ref).max())

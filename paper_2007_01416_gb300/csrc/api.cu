@@ -1,5 +1,5 @@
 // api.cu -- the C ABI of libacat (declared in include/acat.h): context
-// lifetime, argument checks, the step and run drivers (CUDA-graph replay of
+// lifetime, argument checks, the step and run entry points (CUDA-graph replay of
 // the time loop with the dt reduction kept on the device), status words.
 #include <cuda_runtime.h>
 

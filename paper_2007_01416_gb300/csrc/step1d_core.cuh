@@ -699,6 +699,7 @@ template <int P, int S, int NW = NT / 32, int LPN = 1, int R = 1>
 struct Smem32 {
   float thi[S][Tiling<P, NW, LPN, R>::TW], tlo[S][Tiling<P, NW, LPN, R>::TW];
   float Gs[Tiling<P, NW, LPN, R>::NI][S];
+  unsigned char rej[S][Tiling<P, NW, LPN, R>::NI];  // rejected orders per (component, interface)
   float redf[NW];
 };
 
@@ -800,18 +801,35 @@ __device__ __forceinline__ void tile_f64(const Step1DArgs &a, Smem64<P, Phys<FLU
 // il - 1 + GH and il + GH. xw: the warp's exchange slots. Every lane of an
 // active group returns the code p_s and G (lanes beyond the selected order's
 // 2p return G unset).
+// rej (nullable): the tile's rejected orders per (component, interface), from
+// reject_pass_f32; the group then ORs its interface's bits instead of
+// deciding in select_order.
 template <int P, int FLUX, int LPN>
 __device__ __forceinline__ int iface_f32(const Step1DArgs &a, const float *thi, const float *tlo, int tw,
                                          int il, int grp, int l, bool valid, bool active, float lam,
-                                         const FiltConst &FC, float4 *xw, float *G) {
+                                         const FiltConst &FC, float4 *xw, float *G,
+                                         const unsigned char *rej = nullptr, int ni = 0) {
   using TL = Tiling<P, NT / 32, LPN>;
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
   const float adv = a.advf, gam = a.gammaf, gm1 = a.gm1f;
   const int ic = il - 1 + TL::GH;
   const int icv = valid ? ic : 0;
-  const int ps = select_order<P, S, true, LPN>(nullptr, thi + icv, tlo + icv, tw, l, grp, active, valid, FC,
-                                               a.eps, a.thr, a.fact_tau, a.psi2_mod);
+  int ps = 1;
+  if (rej) {
+    if constexpr (P >= 2) {
+      unsigned r = 0;
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < S; c++) r |= rej[c * ni + il];
+      }
+      const unsigned accept = ~r & ((1u << (P - 1)) - 1u);
+      ps = accept ? (32 - __clz(accept)) + 1 : 1;
+    }
+  } else {
+    ps = select_order<P, S, true, LPN>(nullptr, thi + icv, tlo + icv, tw, l, grp, active, valid, FC, a.eps,
+                                       a.thr, a.fact_tau, a.psi2_mod);
+  }
   const int base = grp * TL::L;
   if (active && acat_in_bounds(ic - P + 1 >= 0 && ic + P < tw, a.status)) {
     const float *h0 = thi + ic, *l0 = tlo + ic;
@@ -842,6 +860,30 @@ __device__ __forceinline__ int iface_f32(const Step1DArgs &a, const float *thi, 
     }
   }
   return ps;
+}
+
+// The order decisions of a staged FP32 tile, spread over all nthreads
+// threads: for every (component c, interface il < ni) with i0 + il <= N, the
+// rejected orders of component c (reject_set32: the filtered decision with its
+// literal FP64 fallback on hi + lo, as select_order takes it), written to
+// rej[c ni + il]. Component-major, so that the threads of a warp read
+// consecutive cells. Interfaces beyond the instance get 0 (never used).
+template <int P, int S, int GH>
+__device__ __forceinline__ void reject_pass_f32(const Step1DArgs &a, const float *thi, const float *tlo, int tw,
+                                                int ni, long i0, long N, const FiltConst &FC, unsigned char *rej,
+                                                int nthreads) {
+  if constexpr (P >= 2) {
+    for (int q = threadIdx.x; q < S * ni; q += nthreads) {
+      const int c = q / ni, il = q - c * ni;
+      unsigned r = 0;
+      if (i0 + il <= N && acat_in_bounds(il - 1 + GH - P + 1 >= 0 && il - 1 + GH + P < tw, a.status)) {
+        const int ic = il - 1 + GH;
+        r = reject_set32<P>(thi + c * tw + ic, tlo + c * tw + ic, 1, c == 0, FC, a.eps, a.thr, a.fact_tau,
+                            a.psi2_mod);
+      }
+      rej[q] = (unsigned char)r;
+    }
+  }
 }
 
 // Conservative update (Eq. 2.12) of the cell at tile index k of an FP32 tile
@@ -901,9 +943,9 @@ __device__ __forceinline__ void update_cell_f32(const Step1DArgs &a, const float
 }
 
 // One FP32 tile on the compensated state [hi(s x M); lo(s x M)].
-// Two CTA barriers per tile: after staging (which also publishes *lam_sm,
-// written by the caller before the call) and between the flux and update
-// phases. There is none at the end: a caller that loops over tiles
+// Three CTA barriers per tile: after staging (which also publishes *lam_sm,
+// written by the caller before the call), after the order decisions, and
+// between the flux and update phases. There is none at the end: a caller that loops over tiles
 // alternates between two workspaces (and two lam slots), so the next tile's
 // staging cannot overwrite what a slower warp still reads. The wave speed
 // maximum goes out per warp (atomic max of the warps that updated cells).
@@ -933,8 +975,12 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   // the warps' shuffle-free exchange slots of the one-lane-per-node recursion
   __shared__ float4 xs[(LPN == 1 && P >= 2 && S > 1) ? NW * 64 : 1];
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  // every order decision of the tile first, over all threads (a group's
+  // lanes beyond its S components would otherwise wait through them)
+  reject_pass_f32<P, S, TL::GH>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, TL::NI, i0, N, FC, &sm.rej[0][0], NTB);
+  if (P >= 2) __syncthreads();
   // R rounds: round rnd takes the interfaces (rnd NW + warp) GPW + grp, so
-  // each round covers NW GPW consecutive interfaces; the tile's two barriers
+  // each round covers NW GPW consecutive interfaces; the tile's barriers
   // serve all R rounds
 #pragma unroll 1
   for (int rnd = 0; rnd < R; rnd++) {
@@ -944,7 +990,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     const bool active = valid && m <= N;
     float G[S];
     const int ps = iface_f32<P, FLUX, LPN>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, il, grp, l, valid, active,
-                                           lam, FC, &xs[warp * 64], G);
+                                           lam, FC, &xs[warp * 64], G, &sm.rej[0][0], TL::NI);
     if (active && l == 0 && acat_in_bounds(il < TL::NI && m <= N, a.status)) {
 #pragma unroll
       for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];

@@ -738,10 +738,31 @@ __global__ void __launch_bounds__(NT, F32 ? 3 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
   const int grp = lane >> 4, l = lane & 15, base = grp * 16;
   // the warps' exchange slots of the FP32 block recursion of systems
   __shared__ float4 xs2[(F32 && S > 1 && P >= 2) ? (NT / 32) * 128 : 1];
-  const unsigned gmask = 0xffffu << base;
   constexpr int CS = TW2 * TW2, RS = TW2;
-  constexpr int NPAIR = 2 * S;  // (direction, component): every order p = 2..P at once
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
+  // --- dimension-by-dimension order decisions of every anchor first, one
+  // (direction, component, anchor) per thread and pass: rejected orders
+  // (Eqs. 3.2-3.3 on the row through the anchor for x, its column for y)
+  __shared__ unsigned char rej2[P >= 2 ? 2 * S * NA * NA : 1];
+  if constexpr (P >= 2) {
+    for (int q = threadIdx.x; q < 2 * S * NA * NA; q += NT) {
+      const int dc = q / (NA * NA), an = q - dc * NA * NA, dir = dc / S, c = dc - dir * S;
+      const int ax = an % NA - 1, ay = an / NA - 1;
+      const bool inside = x0 + ax < NXl && y0 + ay < NYl;
+      unsigned r = 0;
+      if (inside && (dir == 0 ? ay >= 0 : ax >= 0)) {
+        const int tx = ax + GH2, ty = ay + GH2;
+        if constexpr (F32)
+          r = reject_set32<P>(&thi[c][ty][tx], &tlo[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr,
+                              a.fact_tau, a.psi2_mod);
+        else
+          r = reject_set64<P>(&tile[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau,
+                              a.psi2_mod);
+      }
+      rej2[q] = (unsigned char)r;
+    }
+    __syncthreads();
+  }
 
   for (int round = 0; round < NA * NA / 16; round++) {
     const int an = round * 16 + warp * 2 + grp;
@@ -752,24 +773,13 @@ __global__ void __launch_bounds__(NT, F32 ? 3 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 
     const bool needG = inside && ax >= 0;
     const int tx = ax + GH2, ty = ay + GH2;
     const double *q64 = F32 ? nullptr : &tile[0][F32 ? 0 : ty][F32 ? 0 : tx];
-    // --- dimension-by-dimension order selection -------------------------------
     unsigned rej = 0;
-    if (P >= 2) {
-      for (int qq = l; qq < NPAIR; qq += 16) {
-        const int dir = qq / S, c = qq - dir * S;
-        if (dir == 0 ? !needF : !needG) continue;
-        unsigned r = 0;
-        if constexpr (P >= 2) {
-          if constexpr (F32)
-            r = reject_set32<P>(&thi[c][ty][tx], &tlo[c][ty][tx], dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr,
-                                a.fact_tau, a.psi2_mod);
-          else
-            r = reject_set64<P>(q64 + c * CS, dir == 0 ? 1 : RS, c == 0, FC, a.eps, a.thr, a.fact_tau,
-                                a.psi2_mod);
-        }
-        rej |= r << (dir * (P - 1));
+    if constexpr (P >= 2) {
+#pragma unroll
+      for (int c = 0; c < S; c++) {
+        rej |= rej2[c * NA * NA + an];
+        rej |= (unsigned)rej2[(S + c) * NA * NA + an] << (P - 1);
       }
-      rej = __reduce_or_sync(gmask, rej);
     }
     int px = 1, py = 1;
     if (P >= 2) {

@@ -1421,13 +1421,25 @@ struct TabSF {
   float invfact[ACAT_MAXN + 1];
 };
 
+// Tiles of the FP32 high-order step: TXF x TXF cells and their (TXF+1)^2
+// anchors. Below P = 4 they are larger than the FP64 kernel's (its double
+// tiles fill the shared memory at TXH): fewer of the anchors on a tile's left
+// column and bottom row, whose block recursions the neighbouring CTA repeats.
+// At P = 4 the larger tile measured slower (fewer CTAs per SM) and TXH is kept.
+// Task words: anchor in bits 0-9, the wanted fluxes in bits 10-11, p1 and p2
+// from bits 12 and 15.
+template <int P>
+constexpr int TXF = P >= 4 ? TXH : 16;
+template <int P>
+constexpr int NAF = TXF<P> + 1;
+constexpr unsigned WF32 = 1u << 10, WG32 = 1u << 11;
 template <int P, int FLUX>
 struct Smem2HF {
   static constexpr int S = Phys2<FLUX>::S;
-  static constexpr int TW = TXH + 2 * P;
+  static constexpr int TW = TXF<P> + 2 * P;
   float thi[S][TW][TW], tlo[S][TW][TW];
-  float Fx[TXH][TXH + 1][S];
-  float Gy[TXH + 1][TXH][S];
+  float Fx[TXF<P>][TXF<P> + 1][S];
+  float Gy[TXF<P> + 1][TXF<P>][S];
   // F^(k), G^(k) increments of the nodes of a round, a task's 2P x 2P nodes
   // by rows (X) and by columns (Y). At P = 2, 4 each row (column) is padded to
   // 2P + 1 slots, so that the loads of node r of a warp's rows (columns) fall
@@ -1441,8 +1453,8 @@ struct Smem2HF {
   static constexpr int YC = PAD ? RW : 1, YS = PAD ? 1 : 2 * P;
   static constexpr int XS = (NT / (4 * P * P) + 1) * TS;
   float X[XS][S], Y[XS][S];
-  unsigned rej[NAH * NAH];    // rejected orders: bit dir * (P - 1) + (p - 2)
-  unsigned task[2 * NAH * NAH];  // anchor | wants | p1 << 10 | p2 << 13
+  unsigned rej[NAF<P> * NAF<P>];    // rejected orders: bit dir * (P - 1) + (p - 2)
+  unsigned task[2 * NAF<P> * NAF<P>];  // anchor | wants | p1 << 12 | p2 << 15
   int ntask;
   float lx, ly;
   TabSF tab;
@@ -1464,11 +1476,11 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
   for (int base = 0; base < nt; base += per) {
     const bool slot_ok = ti < per && base + ti < nt;
     const unsigned tk = slot_ok ? sm.task[base + ti] : 0u;
-    const int an = (int)(tk & 0xffu);
-    const int p1 = slot_ok ? (int)((tk >> 10) & 7u) : 1, p2 = slot_ok ? (int)((tk >> 13) & 7u) : 1;
+    const int an = (int)(tk & 0x3ffu);
+    const int p1 = slot_ok ? (int)((tk >> 12) & 7u) : 1, p2 = slot_ok ? (int)((tk >> 15) & 7u) : 1;
     const int n1 = 2 * p1, n2 = 2 * p2, pm = p1 > p2 ? p1 : p2, n = 2 * pm, zt = pm - 1;
     const bool act = slot_ok && ia < n1 && ib < n2;
-    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    const int ax = an % NAF<P> - 1, ay = an / NAF<P> - 1;
     float Ff[S], Fg[S], dels[NM][S];
     typename PH::Base bj;
     if (act) {
@@ -1580,14 +1592,14 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
     }
     __syncthreads();
     if (slot_ok && node == 0) {
-      if (tk & WANT_F)
+      if (tk & WF32)
 #pragma unroll
         for (int c = 0; c < S; c++) {
           float t = 0.0f;
           for (int r = 0; r < n1; r++) t += sm.X[ti * SM::TS + (p2 - 1) * SM::RW + r][c];
           sm.Fx[ay][ax + 1][c] = t;
         }
-      if (tk & WANT_G)
+      if (tk & WG32)
 #pragma unroll
         for (int c = 0; c < S; c++) {
           float t = 0.0f;
@@ -1609,14 +1621,14 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
   __shared__ double s_red[2][NT / 32];
   const int tid = threadIdx.x;
   const long NXl = a.NX, NYl = a.NY;
-  const long x0 = (long)blockIdx.x * TXH, y0 = (long)blockIdx.y * TXH;
+  const long x0 = (long)blockIdx.x * TXF<P>, y0 = (long)blockIdx.y * TXF<P>;
   if (tid == 0) {
     const double dt = step_dt2(a);
     sm.lx = (float)(dt / a.dx);
     sm.ly = (float)(dt / a.dy);
     sm.ntask = 0;
   }
-  for (int q = tid; q < NAH * NAH; q += NT) sm.rej[q] = 0u;
+  for (int q = tid; q < NAF<P> * NAF<P>; q += NT) sm.rej[q] = 0u;
   {
     constexpr int NW3 = (ACAT_MAXP + 1) * ACAT_MAXN * ACAT_MAXN;
     for (int q = tid; q < NW3; q += NT) {
@@ -1641,10 +1653,10 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
   // --- order decisions: every (anchor, direction, component), all orders at once
   constexpr int NPAIR = 2 * S;
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
-  for (int q = tid; q < NAH * NAH * NPAIR; q += NT) {
+  for (int q = tid; q < NAF<P> * NAF<P> * NPAIR; q += NT) {
     const int an = q / NPAIR, pr = q - an * NPAIR;
     const int dir = pr / S, c = pr - dir * S;
-    const int ax = an % NAH - 1, ay = an / NAH - 1;
+    const int ax = an % NAF<P> - 1, ay = an / NAF<P> - 1;
     const bool inside = x0 + ax < NXl && y0 + ay < NYl;
     const bool skip = a.rect_2d ? (ax < 0 && ay < 0) : (dir == 0 ? ay < 0 : ax < 0);
     if (!inside || skip) continue;
@@ -1654,8 +1666,8 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
   }
   __syncthreads();
   // --- orders, block tasks, FL-CAT2 directions
-  for (int an = tid; an < NAH * NAH; an += NT) {
-    const int ax = an % NAH - 1, ay = an / NAH - 1;
+  for (int an = tid; an < NAF<P> * NAF<P>; an += NT) {
+    const int ax = an % NAF<P> - 1, ay = an / NAF<P> - 1;
     const long gxa = x0 + ax, gya = y0 + ay;
     const bool inside = gxa < NXl && gya < NYl;
     const bool needF = inside && ay >= 0, needG = inside && ax >= 0;
@@ -1667,13 +1679,13 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
     const bool bF = needF && px >= 2, bG = needG && py >= 2;
     const unsigned ua = (unsigned)an;
     if (a.rect_2d) {
-      const unsigned want = (bF ? WANT_F : 0u) | (bG ? WANT_G : 0u);
-      if (want) sm.task[atomicAdd(&sm.ntask, 1)] = ua | want | ((unsigned)px << 10) | ((unsigned)py << 13);
+      const unsigned want = (bF ? WF32 : 0u) | (bG ? WG32 : 0u);
+      if (want) sm.task[atomicAdd(&sm.ntask, 1)] = ua | want | ((unsigned)px << 12) | ((unsigned)py << 15);
     } else if (bF && bG && px == py) {
-      sm.task[atomicAdd(&sm.ntask, 1)] = ua | WANT_F | WANT_G | ((unsigned)px << 10) | ((unsigned)px << 13);
+      sm.task[atomicAdd(&sm.ntask, 1)] = ua | WF32 | WG32 | ((unsigned)px << 12) | ((unsigned)px << 15);
     } else {
-      if (bF) sm.task[atomicAdd(&sm.ntask, 1)] = ua | WANT_F | ((unsigned)px << 10) | ((unsigned)px << 13);
-      if (bG) sm.task[atomicAdd(&sm.ntask, 1)] = ua | WANT_G | ((unsigned)py << 10) | ((unsigned)py << 13);
+      if (bF) sm.task[atomicAdd(&sm.ntask, 1)] = ua | WF32 | ((unsigned)px << 12) | ((unsigned)px << 15);
+      if (bG) sm.task[atomicAdd(&sm.ntask, 1)] = ua | WG32 | ((unsigned)py << 12) | ((unsigned)py << 15);
     }
     const bool flF = needF && px < 2, flG = needG && py < 2;
     if (flF || flG) {
@@ -1693,8 +1705,8 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
   float mx = 0.0f, my = 0.0f;
   bool bad = false;
   float *uo = static_cast<float *>(a.u_out);
-  for (int t = tid; t < TXH * TXH; t += NT) {
-    const int cy = t / TXH, cx = t - cy * TXH;
+  for (int t = tid; t < TXF<P> * TXF<P>; t += NT) {
+    const int cy = t / TXF<P>, cx = t - cy * TXF<P>;
     const long gx = x0 + cx, gy = y0 + cy;
     if (gx >= NXl || gy >= NYl) continue;
     const int tx = cx + P, ty = cy + P;
@@ -1770,7 +1782,7 @@ __global__ void __launch_bounds__(NT, 2) k_step2d_hi_f32(const Step2DArgs a) {
 
 template <int P, int FLUX>
 int launch2_hi_f32(const Step2DArgs &a, cudaStream_t st) {
-  dim3 grid((unsigned)((a.NX + TXH - 1) / TXH), (unsigned)((a.NY + TXH - 1) / TXH));
+  dim3 grid((unsigned)((a.NX + TXF<P> - 1) / TXF<P>), (unsigned)((a.NY + TXF<P> - 1) / TXF<P>));
   k_step2d_hi_f32<P, FLUX><<<grid, NT, 0, st>>>(a);
   return (int)cudaGetLastError();
 }

@@ -124,6 +124,17 @@ __device__ __forceinline__ int acat_tile_index(int i, int n, unsigned *status) {
   return acat_in_bounds(i >= 0 && i < n, status) ? i : 0;
 }
 
+// Node-exchange slots of the FP32 1D recursion. A lane stores its F^(k-2) in
+// a 16-byte slot that the other lanes of its group read back by broadcast. In
+// tiles of P >= 3 the slots of the group whose first lane is b start at
+// xslot(b) = b + (b >> 3): the groups of a warp, 6 or 8 lanes apart, then
+// start in distinct 16-byte bank quads, and each broadcast load is one
+// shared-memory wavefront instead of two (P = 3) or four (P = 4). At P = 2
+// (4 lanes apart) the same padding also removes four-way conflicts but
+// measured slower, and the slots start at b. A warp holds two sets of XSET.
+constexpr int XSET = 36;
+__device__ __forceinline__ int xslot(int b) { return b + (b >> 3); }
+
 __device__ __forceinline__ long bc_index(long g, long N, int bc) {
   if (bc == ACAT_BC_PERIODIC) {
     if (g >= 0 && g < N) return g;

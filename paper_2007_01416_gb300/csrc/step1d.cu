@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DAr
   __shared__ float thi[S][TL::TW], tlo[S][TL::TW];
   __shared__ float Gs[TL::NI][S];
   __shared__ unsigned char rej[S][TL::NI];
-  __shared__ float4 xs[(P >= 2 && S > 1) ? NWF * 64 : 1];
+  __shared__ float4 xs[(P >= 2 && S > 1) ? NWF * 2 * XSET : 1];
   __shared__ float s_lam;
   __shared__ int s_own[2];
   const long N = a.N, i0 = (long)blockIdx.x * TL::NI;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DAr
   if (P >= 2) __syncthreads();
   float G[S];
   const int ps = iface_f32<P, FLUX, 1>(a, &thi[0][0], &tlo[0][0], TL::TW, il, grp, l, valid, active, lam, FC,
-                                       &xs[warp * 64], G, &rej[0][0], TL::NI);
+                                       &xs[warp * 2 * XSET], G, &rej[0][0], TL::NI);
   if (active && l == 0) {
 #pragma unroll
     for (int c = 0; c < S; c++) Gs[il][c] = G[c];

@@ -298,14 +298,14 @@ struct DPhys<ACAT_FLUX_EULER1D> {
 
 // CAT2p increment G of one interface by a group of 2p lanes (lane l <-> node
 // j = l - p + 1). hi/lo point at cell i of component 0 of the compensated
-// tile, components `cs` apart. xw: the warp's 64 exchange slots in shared
-// memory (two sets of 32 used alternately by k), through which the lanes of
-// the group read the F^(k-2) of all nodes of a system: one 16-byte store and
-// 2p 16-byte broadcast loads per lane and order instead of 2p s shuffles
-// (scalar laws shuffle). Every lane returns G.
+// tile, components `cs` apart. xg: the group's exchange slots in shared
+// memory (node r at xg[r], two sets XSET apart used alternately by k),
+// through which the lanes of the group read the F^(k-2) of all nodes of a
+// system: one 16-byte store and 2p 16-byte broadcast loads per lane and order
+// instead of 2p s shuffles (scalar laws shuffle). Every lane returns G.
 template <int p, int FLUX>
 __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int cs, int l, int base,
-                                          float lam, float adv, float gm1, float4 *xw, float *Gout) {
+                                          float lam, float adv, float gm1, float4 *xg, float *Gout) {
   using TB = Tab<float>;
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
@@ -356,13 +356,13 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
       // lane of the group passed the barrier of order k - 1. At p >= 3
       // components 0 and 1 of the sum run packed in float2 lanes (each
       // rounded as the scalar FMA); at p = 2 the scalar form is faster.
-      float4 *xb = xw + (k & 1) * 32;
-      xb[base + l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
+      float4 *xb = xg + (k & 1) * XSET;
+      xb[l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
       __syncwarp(mask);
       float2 u01 = make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int r = 0; r < n; r++) {
-        const float4 f = xb[base + r];
+        const float4 f = xb[r];
         u01 = f2fma(f2dup(g1r[r]), make_float2(f.x, f.y), u01);
         U[S > 2 ? 2 : 0] = fmaf(g1r[r], f.z, U[S > 2 ? 2 : 0]);
       }
@@ -371,12 +371,12 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
       U[1] = u01.y;
       U[S > 2 ? 2 : 0] *= -lam;
     } else if constexpr (S > 1) {
-      float4 *xb = xw + (k & 1) * 32;
-      xb[base + l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
+      float4 *xb = xg + (k & 1) * XSET;
+      xb[l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
       __syncwarp(mask);
 #pragma unroll
       for (int r = 0; r < n; r++) {
-        const float4 f = xb[base + r];
+        const float4 f = xb[r];
         const float fr[3] = {f.x, f.y, f.z};
 #pragma unroll
         for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], fr[c], U[c]);
@@ -831,19 +831,20 @@ __device__ __forceinline__ int iface_f32(const Step1DArgs &a, const float *thi, 
                                        a.thr, a.fact_tau, a.psi2_mod);
   }
   const int base = grp * TL::L;
+  float4 *const xg = xw + (P >= 3 ? xslot(base) : base);
   if (active && acat_in_bounds(ic - P + 1 >= 0 && ic + P < tw, a.status)) {
     const float *h0 = thi + ic, *l0 = tlo + ic;
     if (ps == 4) {
       if constexpr (P >= 4) {
         if constexpr (LPN == 2) cat_delta2<4, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, G);
-        else cat_delta<4, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xw, G);
+        else cat_delta<4, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xg, G);
       }
     } else if (ps == 3) {
       if constexpr (P >= 3) {
         if constexpr (LPN == 2) {
           if (l < 12) cat_delta2<3, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, G);
         } else if (l < 6) {
-          cat_delta<3, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xw, G);
+          cat_delta<3, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xg, G);
         }
       }
     } else if (ps == 2) {
@@ -851,7 +852,7 @@ __device__ __forceinline__ int iface_f32(const Step1DArgs &a, const float *thi, 
         if constexpr (LPN == 2) {
           if (l < 8) cat_delta2<2, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, G);
         } else if (l < 4) {
-          cat_delta<2, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xw, G);
+          cat_delta<2, FLUX>(h0, l0, tw, l, base, lam, adv, gm1, xg, G);
         }
       }
     } else {
@@ -973,7 +974,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
   const bool valid = grp < TL::GPW;
 
   // the warps' shuffle-free exchange slots of the one-lane-per-node recursion
-  __shared__ float4 xs[(LPN == 1 && P >= 2 && S > 1) ? NW * 64 : 1];
+  __shared__ float4 xs[(LPN == 1 && P >= 2 && S > 1) ? NW * 2 * XSET : 1];
   const FiltConst FC = filt_const(a.epsf, a.rf, a.factf);
   // every order decision of the tile first, over all threads (a group's
   // lanes beyond its S components would otherwise wait through them)
@@ -990,7 +991,7 @@ __device__ __forceinline__ void tile_f32(const Step1DArgs &a, Smem32<P, DPhys<FL
     const bool active = valid && m <= N;
     float G[S];
     const int ps = iface_f32<P, FLUX, LPN>(a, &sm.thi[0][0], &sm.tlo[0][0], TL::TW, il, grp, l, valid, active,
-                                           lam, FC, &xs[warp * 64], G, &sm.rej[0][0], TL::NI);
+                                           lam, FC, &xs[warp * 2 * XSET], G, &sm.rej[0][0], TL::NI);
     if (active && l == 0 && acat_in_bounds(il < TL::NI && m <= N, a.status)) {
 #pragma unroll
       for (int c = 0; c < S; c++) sm.Gs[il][c] = G[c];

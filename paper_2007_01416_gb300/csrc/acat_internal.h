@@ -77,6 +77,7 @@ struct BatchArgs {
   double *dt_out;             // B (nullable)
   double *lam;                // B: dt / dx of each instance for this step (k_batch_dt)
   float *lamf;                // B: the same rounded to float (FP32 path)
+  int *next;                  // tile queue of the step kernel (k_batch_dt sets it to 0)
   int8_t *orders;             // M + B order codes (nullable), instance b at offs[b] + b
   int nw;                     // warps per CTA (4, 8 or 16); tiles of acat_cells_per_tile_1d(P, prec, nw, lpn) cells
   int cps;                    // CTAs per SM (<= 0: the kernel's occupancy)

@@ -46,6 +46,7 @@ struct acat_ctx {
   double *d_tb = nullptr;                 // 3 x B
   double *d_lamb = nullptr;               // B: dt / dx of each instance for the current step
   float *d_lambf = nullptr;               // B: the same in float
+  int *d_next = nullptr;                  // batched: the step kernel's tile queue counter
   double *d_contrib = nullptr;            // adjoint: per-interface node cotangents
   void *d_seg = nullptr;                  // adjoint run: recomputed states of a segment
   size_t seg_bytes = 0;
@@ -198,6 +199,7 @@ BatchArgs batch_args(acat_ctx *c) {
   bt.t = c->d_tb;
   bt.lam = c->d_lamb;
   bt.lamf = c->d_lambf;
+  bt.next = c->d_next;
   bt.nw = c->bnw;
   bt.cps = c->bcps;
   bt.lpn = c->lpn;
@@ -452,6 +454,7 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
   if (e == cudaSuccess) e = cudaMalloc(&c->d_tb, 3 * sizeof(double) * (size_t)n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_lamb, sizeof(double) * (size_t)n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_lambf, sizeof(float) * (size_t)n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_next, sizeof(int));
   if (e == cudaSuccess)
     e = cudaMemcpy(c->d_offs, offs.data(), sizeof(long long) * (size_t)(n_inst + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_smaxb, 0, 3 * sizeof(unsigned long long) * (size_t)n_inst);
@@ -615,6 +618,7 @@ int acat_destroy(acat_ctx *c) {
   cudaFree(c->d_tb);
   cudaFree(c->d_lamb);
   cudaFree(c->d_lambf);
+  cudaFree(c->d_next);
   cudaFree(c->d_contrib);
   cudaFree(c->d_seg);
   cudaFree(c->d_bar);

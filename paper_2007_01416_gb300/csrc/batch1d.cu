@@ -44,6 +44,7 @@ __device__ double batch_dt(const Step1DArgs &a, const BatchArgs &bt, int b, bool
 // divisions are done once per instance, not once per tile (in the tile they
 // held the whole CTA at its staging barrier behind one thread).
 __global__ void __launch_bounds__(NT) k_batch_dt(const Step1DArgs a, const BatchArgs bt) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *bt.next = 0;  // the step kernel's tile queue
   for (long b = (long)blockIdx.x * NT + threadIdx.x; b < bt.B; b += (long)gridDim.x * NT) {
     const long N = bt.offs[b + 1] - bt.offs[b];
     const double dx = bt.xlen / (double)N;
@@ -62,12 +63,17 @@ struct RoundsB32 {
   static constexpr int value = NW >= 16 ? 2 : 4;
 };
 
-// Persistent batched step: CTAs of NW warps stride over the (instance,
-// first cell) work list, whose tiles are Tiling<P, NW, LPN, R>::T cells wide
-// (R = RoundsB32<NW> in FP32, 1 in FP64);
-// every instance is advanced with its own dt (lambda from k_batch_dt). The
-// register cap per thread is that of the 8-warp kernels (MinCtas x 8 / NW
-// resident CTAs).
+// Persistent batched step: CTAs of NW warps take the tiles of the (instance,
+// first cell) work list, Tiling<P, NW, LPN, R>::T cells wide (R =
+// RoundsB32<NW> in FP32, 1 in FP64), from a queue: CTA c starts with tile c,
+// and each further tile is claimed with one atomic on the queue counter
+// (set to 0 by k_batch_dt), issued before the current tile so that its
+// latency hides behind the tile's work. Tiles cost unevenly (FL-CAT2
+// interfaces, the order decisions left to the FP64 fallback, partial last
+// tiles), and the queue keeps the CTAs busy to the end. Results do not
+// depend on which CTA takes a tile. Every instance is advanced with its own
+// dt (lambda from k_batch_dt). The register cap per thread is that of the
+// 8-warp kernels (MinCtas x 8 / NW resident CTAs).
 template <int P, int FLUX, bool F32, int NW, int LPN>
 __global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
     k_batch1d(const Step1DArgs a, const BatchArgs bt) {
@@ -76,8 +82,13 @@ __global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
       typename std::conditional<F32, Smem32<P, Phys<FLUX>::S, NW, LPN, R>, Smem64<P, Phys<FLUX>::S, NW>>::type;
   // FP32: two workspaces used alternately (tile_f32 ends without a barrier)
   __shared__ SM sm[F32 ? 2 : 1];
+  // the next tile of this CTA, claimed by thread 0 before the current one and
+  // read after it: the tile's staging barrier publishes it, and the two slots
+  // alternate, so a claim never overwrites a slot another thread still reads
+  __shared__ long long s_next[2];
   int par = 0;
-  for (long w = blockIdx.x; w < bt.ntiles; w += gridDim.x) {
+  for (long w = blockIdx.x; w < bt.ntiles; par ^= 1) {
+    if (threadIdx.x == 0) s_next[par] = (long long)gridDim.x + atomicAdd(bt.next, 1);
     const int b = bt.tiles[w].b;
     const long i0 = (long)bt.tiles[w].tile * Tiling<P, NW, LPN, R>::T;
     const long off = bt.offs[b], N = bt.offs[b + 1] - off;
@@ -86,11 +97,11 @@ __global__ void __launch_bounds__(NW * 32, MinCtas<P, F32>::value * 8 / NW)
     if constexpr (F32) {
       tile_f32<P, FLUX, NW, LPN, R>(a, sm[par], static_cast<const float *>(a.u_in),
                                     static_cast<float *>(a.u_out), off, bt.M, N, i0, &bt.lamf[b], ord, so);
-      par ^= 1;
     } else {
       tile_f64<P, FLUX, NW>(a, sm[0], static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out),
                             off, bt.M, N, i0, bt.lam[b], ord, so);
     }
+    w = (long)s_next[par];
   }
 }
 

@@ -166,17 +166,21 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
  *     R = 4 interface rounds per lane group in FP32 (2 at nw = 16), 1 in
  *     FP64 (P = 3, nw = 8, lpn = 1: 159 in FP32, 39 in FP64); one CTA of nw
  *     warps per tile at a time,
- *     on a grid of (SM count) x cps CTAs that stride over the tile list
+ *     on a grid of (SM count) x cps CTAs that take the tiles from a queue
  *     (cps = 0: the kernel's occupancy). nw in {4, 8, 16}. At a fixed lpn,
  *     nw and cps only move work between CTAs: every interface flux, wave
  *     speed and update is computed from the same values, so the states are
  *     bit-identical.
  *   - Single-instance contexts: cps is 0. FP64: nw is fixed (8; 2 for the
  *     small-CTA step of large grids). FP32: nw = 8 (the fused step, lpn 1
- *     or 2) or nw = 2 (the small-CTA step with the boundary hand-off,
- *     lpn = 1); both compute every interface and cell from the same values,
- *     so at lpn = 1 they are bit-identical.
- * Defaults: nw = 8, lpn = 1, cps = 0.
+ *     or 2), nw = 7 (the fused step in tiles of 7 floor(32 / 2P) - 1
+ *     cells, lpn = 1: a grid of a few waves then fills every SM with the
+ *     same number of CTAs) or nw = 2 (the small-CTA step with the boundary
+ *     hand-off, lpn = 1); all compute every interface and cell from the
+ *     same values, so at lpn = 1 they are bit-identical.
+ * Defaults: nw = 8, lpn = 1, cps = 0; a single 1D FP32 instance starts with
+ * nw = 7 where that leaves the busiest SM fewer warps of work
+ * (ceil(ceil(N / T) / SMs) x nw against the same at nw = 8).
  * acat_launch_shape returns the current shape (cps resolved to a number for
  * a batch). acat_set_launch_shape sets one; for a batch, changing nw or lpn
  * rebuilds the tile list (a device allocation and a device synchronisation);
@@ -191,7 +195,7 @@ int acat_set_launch_shape(acat_ctx *ctx, int nw, int lpn, int cps);
  * FP32 contexts). Times `steps` steps (acat_run) from u_dev for every
  * candidate shape: batched: nw in {8, 4, 16} x lpn in {1, 2 where it exists}
  * x cps in {occupancy, occupancy / 2}; single FP32: (nw, lpn) in {(8, 1),
- * (8, 2) where it exists, (2, 1)}. Each candidate runs on a context-allocated copy of u_dev (u_dev is
+ * (8, 2) where it exists, (7, 1), (2, 1)}. Each candidate runs on a context-allocated copy of u_dev (u_dev is
  * only read), once untimed and once timed with CUDA events on `stream`. The
  * fastest shape is kept (acat_set_launch_shape) and returned in *nw_out,
  * *lpn_out, *cps_out (each nullable). Synchronises `stream` and the device;

@@ -39,6 +39,7 @@ struct Step1DArgs {
   int lo_flux;                // F^lo: ACAT_LO_*
   int slot;                   // step index mod 3 (dt-reduction slots)
   int lpn;                    // FP32 1D: lanes per stencil node (1, or 2 for P = 2, 4)
+  int nw;                     // FP32 1D fused step: warps per CTA (8, or 7; 0 reads as 8)
   double dx, cfl;
   double dt_fixed;            // > 0: imposed dt
   const double *dt_in;        // device: imposed dt (nullable; takes precedence)

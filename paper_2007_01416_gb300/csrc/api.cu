@@ -53,7 +53,7 @@ struct acat_ctx {
   void *d_bar = nullptr;                  // adjoint run: second cotangent buffer
   double *d_flux = nullptr;               // 1D: CTA-edge fluxes (FP32: increments) of the small-CTA step
   int *d_cnt = nullptr;                   // 1D: its boundary hand-off counters
-  int snw = 8;                            // 1D FP32 single instance: warps per CTA (8 fused, 2 small-CTA)
+  int snw = 8;                            // 1D FP32 single instance: warps per CTA (8 or 7 fused, 2 small-CTA)
 };
 
 namespace {
@@ -141,6 +141,7 @@ Step1DArgs base_args(acat_ctx *c) {
   a.flux_buf = fine ? c->d_flux : nullptr;
   a.cnt = fine ? c->d_cnt : nullptr;
   a.lpn = c->lpn;
+  a.nw = p.precision == ACAT_PREC_F32 && c->snw == 7 ? 7 : 0;
   return a;
 }
 
@@ -402,6 +403,20 @@ int acat_create(const acat_params *p, acat_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cnt, nc * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, nc * sizeof(int));
   }
+  // 1D FP32, fused step: 8 or 7 warps per CTA, whichever leaves the busiest
+  // SM the fewer warps of work: ceil(CTAs / SMs) x warps per CTA, with
+  // CTAs = ceil(N / T) and T = warps x floor(32 / 2P) - 1 cells per tile
+  // (N = 16384: 7 at P = 2 and 4, 8 at P = 3; ties keep 8)
+  if (e == cudaSuccess && c->dim == 1 && p->precision == ACAT_PREC_F32 && sms > 0) {
+    long load[2] = {0, 0};
+    const int nws[2] = {8, 7};
+    for (int q = 0; q < 2; q++) {
+      const long T = (long)nws[q] * (32 / (2 * p->P)) - 1;
+      const long ctas = (p->nx + T - 1) / T;
+      load[q] = (ctas + sms - 1) / sms * nws[q];
+    }
+    c->snw = load[1] < load[0] ? 7 : 8;
+  }
   if (e == cudaSuccess) e = cudaMemset(c->d_smax, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_t, 0, 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
@@ -496,9 +511,11 @@ int acat_set_launch_shape(acat_ctx *c, int nw, int lpn, int cps) {
       if (nw != w0) return ACAT_ERR_UNSUPPORTED;
       return lpn == c->lpn ? ACAT_OK : ACAT_ERR_UNSUPPORTED;
     }
-    // FP32: the fused 8-warp step (one or two lanes per node) or the small-CTA step
-    if (nw != 8 && !(nw == NWF_API && c->d_flux)) return ACAT_ERR_UNSUPPORTED;
-    if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || (nw == NWF_API && lpn != 1)) return ACAT_ERR_INVALID_ARG;
+    // FP32: the fused step of 8 warps (one or two lanes per node) or 7 warps (one
+    // lane per node), or the small-CTA step
+    if (nw != 8 && nw != 7 && !(nw == NWF_API && c->d_flux)) return ACAT_ERR_UNSUPPORTED;
+    if (!acat_lpn_ok(c->p.P, c->p.precision, lpn) || ((nw == NWF_API || nw == 7) && lpn != 1))
+      return ACAT_ERR_INVALID_ARG;
     if (lpn == c->lpn && nw == c->snw) return ACAT_OK;
     if (c->chain) {
       if (cudaDeviceSynchronize() != cudaSuccess) return ACAT_ERR_CUDA;
@@ -541,6 +558,7 @@ int acat_autotune(acat_ctx *c, const void *u_dev, int steps, void *stream, int *
     if (!acat_lpn_ok(c->p.P, c->p.precision, lpn)) continue;
     if (!c->batched) {
       cands.push_back(Shape{8, lpn, 0});
+      if (lpn == 1) cands.push_back(Shape{7, 1, 0});
       if (lpn == 1 && c->d_flux) cands.push_back(Shape{NWF_API, 1, 0});
       continue;
     }

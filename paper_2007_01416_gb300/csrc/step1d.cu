@@ -53,14 +53,18 @@ __global__ void __launch_bounds__(NT, MinCtas<P, false>::value) k_step1d_f64(con
                     &a.smax[(a.slot + 1) % 3]);
 }
 
-template <int P, int FLUX, int LPN>
-__global__ void __launch_bounds__(NT, MinCtas<P, true>::value) k_step1d_f32(const Step1DArgs a) {
-  __shared__ Smem32<P, DPhys<FLUX>::S, NT / 32, LPN> sm;
+// The fused FP32 step in CTAs of NW warps: 8, or 7, whose tiles of 7 GPW - 1
+// cells let a step of a few waves fill every SM with the same number of CTAs
+// (N = 16384 at P = 4: 607 CTAs, 4 on every SM, against 529 of 8 warps, 4 on
+// some SMs and 3 on the others); the same register cap per thread.
+template <int P, int FLUX, int LPN, int NW = NT / 32>
+__global__ void __launch_bounds__(NW * 32, MinCtas<P, true>::value) k_step1d_f32(const Step1DArgs a) {
+  __shared__ Smem32<P, DPhys<FLUX>::S, NW, LPN> sm;
   __shared__ float s_lam;
   if (threadIdx.x == 0) s_lam = (float)(step_dt(a) / a.dx);
-  tile_f32<P, FLUX, NT / 32, LPN>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0,
-                                  a.N, a.N, (long)blockIdx.x * Tiling<P, NT / 32, LPN>::T, &s_lam, a.orders,
-                                  &a.smax[(a.slot + 1) % 3]);
+  tile_f32<P, FLUX, NW, LPN>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0, a.N,
+                             a.N, (long)blockIdx.x * Tiling<P, NW, LPN>::T, &s_lam, a.orders,
+                             &a.smax[(a.slot + 1) % 3]);
 }
 
 // FP64 step in small CTAs (NWF warps): CTA b computes the NI interfaces
@@ -396,6 +400,12 @@ int launch_p(const Step1DArgs &a, cudaStream_t st) {
       }
     }
     if (a.lpn != 1) return (int)cudaErrorInvalidValue;
+    if (a.nw == 7) {
+      using T7 = Tiling<P, 7>;
+      k_step1d_f32<P, FLUX, 1, 7><<<(unsigned)((a.N + T7::T - 1) / T7::T), 7 * 32, 0, st>>>(a);
+      return (int)cudaGetLastError();
+    }
+    if (a.nw != 0 && a.nw != NT / 32) return (int)cudaErrorInvalidValue;
   }
   const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
   if constexpr (F32) k_step1d_f32<P, FLUX, 1><<<grid, NT, 0, st>>>(a);

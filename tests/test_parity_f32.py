@@ -59,10 +59,13 @@ def _step32(env, ctx, pair, nx):
     ("burgers", 2, 400, 0, 2, 8), ("burgers", 4, 513, 1, 2, 8), ("linear", 4, 300, 0, 2, 8),
     # the small-CTA step with the boundary hand-off; the last CTA holds 1, 2 and 10 interfaces
     ("euler", 4, 16384, 1, 1, 2), ("euler", 3, 1001, 0, 1, 2), ("euler", 2, 777, 1, 1, 2),
-    ("burgers", 4, 513, 1, 1, 2), ("euler", 1, 64, 1, 1, 2), ("linear", 4, 300, 0, 1, 2)])
+    ("burgers", 4, 513, 1, 1, 2), ("euler", 1, 64, 1, 1, 2), ("linear", 4, 300, 0, 1, 2),
+    # the fused step in 7-warp tiles
+    ("euler", 4, 16384, 1, 1, 7), ("euler", 3, 1001, 0, 1, 7), ("euler", 2, 777, 1, 1, 7),
+    ("burgers", 2, 400, 0, 1, 7), ("euler", 1, 64, 1, 1, 7)])
 def test_single_step_f32(env, kind, P, nx, bc, lpn, nw):
     """lpn = 2: two lanes per stencil node (the node's sums split in two);
-    nw = 2: the small-CTA step."""
+    nw = 2: the small-CTA step; nw = 7: the fused step in 7-warp tiles."""
     torch, O, acat = env
     if kind == "linear":
         c = W.burgers_sine(nx=nx, seed=2, P=P)
@@ -206,12 +209,13 @@ def test_free_run_f32_against_oracle(env, P, nx, steps, lpn, nw):
 @pytest.mark.parametrize("P,nx", [(4, 16384), (2, 777), (3, 1001)])
 def test_small_cta_equals_fused(env, P, nx):
     """The small-CTA step (boundary cells handed off between CTAs) and the
-    fused 8-warp step compute every interface and cell from the same values
-    with the same operations: 200-step runs agree bit for bit."""
+    fused step in 8- and 7-warp tiles compute every interface and cell from
+    the same values with the same operations: 200-step runs agree bit for
+    bit."""
     torch, O, acat = env
     c = W.euler1d_riemann_entropy(nx=nx, seed=8, P=P)
     runs = []
-    for nw in (2, 8):
+    for nw in (2, 8, 7):
         with acat.Context(**c.problem_kwargs(), precision=acat.PREC_F32) as ctx:
             ctx.acat_set_launch_shape(nw, 1, 0)
             u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
@@ -220,7 +224,8 @@ def test_small_cta_equals_fused(env, P, nx):
             torch.cuda.synchronize()
             assert ctx.acat_status() == 0
             runs.append((u.cpu(), t.item()))
-    assert torch.equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
+    for r in runs[1:]:
+        assert torch.equal(runs[0][0], r[0]) and runs[0][1] == r[1]
 
 
 def test_run_host_f32(env):
@@ -236,6 +241,29 @@ def test_run_host_f32(env):
         assert torch.equal(out, u.cpu())
 
 
+def _default_nw_f32(torch, nx, P):
+    """Warps per CTA a single FP32 context starts with: 8 or 7, whichever
+    leaves the busiest SM the fewer warps of work (ties keep 8)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    load = {}
+    for nw in (8, 7):
+        T = nw * (32 // (2 * P)) - 1
+        load[nw] = -(-(-(-nx // T)) // sms) * nw
+    return 7 if load[7] < load[8] else 8
+
+
+@pytest.mark.parametrize("nx,P", [(4096, 4), (16384, 4), (16384, 3), (16384, 2), (777, 1)])
+def test_default_shape_f32(env, nx, P):
+    """The default warps per CTA of a single FP32 context follow the load
+    rule (at N = 16384 on 152 SMs: 7 at P = 2 and 4, 8 at P = 3)."""
+    torch, O, acat = env
+    kw = W.euler1d_riemann_entropy(nx=nx, seed=1, P=P).problem_kwargs()
+    with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
+        assert ctx.acat_launch_shape() == (_default_nw_f32(torch, nx, P), 1, 0)
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152 and nx == 16384:
+        assert _default_nw_f32(torch, nx, P) == {2: 7, 3: 8, 4: 7}[P]
+
+
 def test_single_instance_shape_and_autotune(env):
     """Single-instance shapes: FP32 may switch lanes per node (P = 2, 4); the
     tile width and grid are fixed; FP64 and lpn = 2 at P = 3 are refused.
@@ -244,7 +272,7 @@ def test_single_instance_shape_and_autotune(env):
     c = W.euler1d_riemann_entropy(nx=4096, seed=1, P=4)
     kw = c.problem_kwargs()
     with acat.Context(**kw, precision=acat.PREC_F32) as ctx:
-        assert ctx.acat_launch_shape() == (8, 1, 0)
+        assert ctx.acat_launch_shape() == (_default_nw_f32(torch, 4096, 4), 1, 0)
         with pytest.raises(acat.AcatError) as ei:
             ctx.acat_set_launch_shape(4, 1, 0)
         assert ei.value.code == -5
@@ -256,10 +284,15 @@ def test_single_instance_shape_and_autotune(env):
         with pytest.raises(acat.AcatError) as ei:
             ctx.acat_set_launch_shape(2, 2, 0)
         assert ei.value.code == -1
+        ctx.acat_set_launch_shape(7, 1, 0)  # the fused step in 7-warp tiles (one lane per node only)
+        assert ctx.acat_launch_shape() == (7, 1, 0)
+        with pytest.raises(acat.AcatError) as ei:
+            ctx.acat_set_launch_shape(7, 2, 0)
+        assert ei.value.code == -1
         u = torch.from_numpy(acat.to_pair(c.u0)).cuda()
         keep = u.clone()
         nw, lpn, cps = ctx.acat_autotune(u, steps=50)
-        assert torch.equal(u, keep) and (nw, lpn) in ((8, 1), (8, 2), (2, 1)) and cps == 0
+        assert torch.equal(u, keep) and (nw, lpn) in ((8, 1), (8, 2), (7, 1), (2, 1)) and cps == 0
         assert ctx.acat_launch_shape() == (nw, lpn, 0)
     with acat.Context(**{**kw, "P": 3}, precision=acat.PREC_F32) as ctx:
         with pytest.raises(acat.AcatError) as ei:

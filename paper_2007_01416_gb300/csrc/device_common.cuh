@@ -124,6 +124,20 @@ __device__ __forceinline__ int acat_tile_index(int i, int n, unsigned *status) {
   return acat_in_bounds(i >= 0 && i < n, status) ? i : 0;
 }
 
+// Programmatic dependent launch of the 1D step kernels. They are launched
+// with programmatic stream serialization, so that the next step's launch
+// overlaps the end of the current step. acat_pdl_wait() is the first
+// statement of such a kernel: it waits until the previous kernel of the
+// stream has completed and its memory is visible (no memory access of the
+// step comes before). acat_pdl_release() is its last: the next launch begins
+// once every CTA of this grid has passed it, when nearly every SM is free, so
+// the next grid's CTAs spread over the SMs as a plain launch spreads them.
+// (Released at the start of the kernel, the next grid's CTAs took the first
+// SMs to free up, and steps of one uneven wave lost their balance.) In a
+// kernel launched without the attribute both instructions return at once.
+__device__ __forceinline__ void acat_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void acat_pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Node-exchange slots of the FP32 1D recursion. A lane stores its F^(k-2) in
 // a 16-byte slot that the other lanes of its group read back by broadcast. In
 // tiles of P >= 3 the slots of the group whose first lane is b start at

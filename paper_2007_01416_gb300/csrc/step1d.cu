@@ -44,6 +44,7 @@ namespace {
 
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NT, MinCtas<P, false>::value) k_step1d_f64(const Step1DArgs a) {
+  acat_pdl_wait();
   __shared__ Smem64<P, Phys<FLUX>::S> sm;
   __shared__ double s_lam;
   if (threadIdx.x == 0) s_lam = step_dt(a) / a.dx;
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(NT, MinCtas<P, false>::value) k_step1d_f64(con
   tile_f64<P, FLUX>(a, sm, static_cast<const double *>(a.u_in), static_cast<double *>(a.u_out), 0,
                     a.N, a.N, (long)blockIdx.x * Tiling<P>::T, s_lam, a.orders,
                     &a.smax[(a.slot + 1) % 3]);
+  acat_pdl_release();
 }
 
 // The fused FP32 step in CTAs of NW warps: 8, or 7, whose tiles of 7 GPW - 1
@@ -59,12 +61,14 @@ __global__ void __launch_bounds__(NT, MinCtas<P, false>::value) k_step1d_f64(con
 // some SMs and 3 on the others); the same register cap per thread.
 template <int P, int FLUX, int LPN, int NW = NT / 32>
 __global__ void __launch_bounds__(NW * 32, MinCtas<P, true>::value) k_step1d_f32(const Step1DArgs a) {
+  acat_pdl_wait();
   __shared__ Smem32<P, DPhys<FLUX>::S, NW, LPN> sm;
   __shared__ float s_lam;
   if (threadIdx.x == 0) s_lam = (float)(step_dt(a) / a.dx);
   tile_f32<P, FLUX, NW, LPN>(a, sm, static_cast<const float *>(a.u_in), static_cast<float *>(a.u_out), 0, a.N,
                              a.N, (long)blockIdx.x * Tiling<P, NW, LPN>::T, &s_lam, a.orders,
                              &a.smax[(a.slot + 1) % 3]);
+  acat_pdl_release();
 }
 
 // FP64 step in small CTAs (NWF warps): CTA b computes the NI interfaces
@@ -78,6 +82,7 @@ __global__ void __launch_bounds__(NW * 32, MinCtas<P, true>::value) k_step1d_f32
 // interface is computed twice.
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1DArgs a) {
+  acat_pdl_wait();
   using TL = Tiling<P, NWF>;
   constexpr int S = Phys<FLUX>::S;
   constexpr int NTF = NWF * 32;
@@ -215,6 +220,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
     for (int w = 1; w < NWF; w++) v = fmax(v, red[w]);
     atomic_max_pos(&a.smax[(a.slot + 1) % 3], v);
   }
+  acat_pdl_release();
 }
 
 // FP32 step in small CTAs (NWF warps), the boundary hand-off of
@@ -230,6 +236,7 @@ __global__ void __launch_bounds__(NWF * 32, 16 / NWF) k_step1d_fine(const Step1D
 // so this is a selectable launch shape (nw = 2), not the default.
 template <int P, int FLUX>
 __global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DArgs a) {
+  acat_pdl_wait();
   using TL = Tiling<P, NWF>;
   using DP = DPhys<FLUX>;
   constexpr int S = DP::S;
@@ -338,6 +345,7 @@ __global__ void __launch_bounds__(NWF * 32, 16) k_step1d_fine_f32(const Step1DAr
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
   if (lane == 0) atomic_max_pos(&a.smax[(a.slot + 1) % 3], (double)smax);
+  acat_pdl_release();
 }
 
 // Wave speed of a state into smax[slot]; block 0 also sets tslot[slot] = 0.
@@ -376,41 +384,49 @@ __global__ void __launch_bounds__(NT) k_smax1d(const Step1DArgs a) {
   }
 }
 
+// A step kernel launched with programmatic stream serialization (see
+// acat_pdl_enter): its launch overlaps the end of the previous kernel.
+int launch_dep(void (*kernel)(const Step1DArgs), unsigned grid, unsigned block, cudaStream_t st,
+               const Step1DArgs &a) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <int P, int FLUX, bool F32>
 int launch_p(const Step1DArgs &a, cudaStream_t st) {
   using TL = Tiling<P>;
   if constexpr (!F32) {
-    if (a.flux_buf && a.cnt) {  // small-CTA step with boundary hand-off
-      const unsigned g = (unsigned)acat_fine_ctas_1d(P, a.N);
-      k_step1d_fine<P, FLUX><<<g, NWF * 32, 0, st>>>(a);
-      return (int)cudaGetLastError();
-    }
+    if (a.flux_buf && a.cnt)  // small-CTA step with boundary hand-off
+      return launch_dep(k_step1d_fine<P, FLUX>, (unsigned)acat_fine_ctas_1d(P, a.N), NWF * 32, st, a);
   }
   if constexpr (F32) {
-    if (a.flux_buf && a.cnt && a.lpn == 1) {  // small-CTA step with boundary hand-off
-      const unsigned g = (unsigned)acat_fine_ctas_1d(P, a.N);
-      k_step1d_fine_f32<P, FLUX><<<g, NWF * 32, 0, st>>>(a);
-      return (int)cudaGetLastError();
-    }
+    if (a.flux_buf && a.cnt && a.lpn == 1)  // small-CTA step with boundary hand-off
+      return launch_dep(k_step1d_fine_f32<P, FLUX>, (unsigned)acat_fine_ctas_1d(P, a.N), NWF * 32, st, a);
     if constexpr (P == 2 || P == 4) {
       if (a.lpn == 2) {
         using T2 = Tiling<P, NT / 32, 2>;
-        k_step1d_f32<P, FLUX, 2><<<(unsigned)((a.N + T2::T - 1) / T2::T), NT, 0, st>>>(a);
-        return (int)cudaGetLastError();
+        return launch_dep(k_step1d_f32<P, FLUX, 2>, (unsigned)((a.N + T2::T - 1) / T2::T), NT, st, a);
       }
     }
     if (a.lpn != 1) return (int)cudaErrorInvalidValue;
     if (a.nw == 7) {
       using T7 = Tiling<P, 7>;
-      k_step1d_f32<P, FLUX, 1, 7><<<(unsigned)((a.N + T7::T - 1) / T7::T), 7 * 32, 0, st>>>(a);
-      return (int)cudaGetLastError();
+      return launch_dep(k_step1d_f32<P, FLUX, 1, 7>, (unsigned)((a.N + T7::T - 1) / T7::T), 7 * 32, st, a);
     }
     if (a.nw != 0 && a.nw != NT / 32) return (int)cudaErrorInvalidValue;
   }
   const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
-  if constexpr (F32) k_step1d_f32<P, FLUX, 1><<<grid, NT, 0, st>>>(a);
-  else k_step1d_f64<P, FLUX><<<grid, NT, 0, st>>>(a);
-  return (int)cudaGetLastError();
+  if constexpr (F32) return launch_dep(k_step1d_f32<P, FLUX, 1>, grid, NT, st, a);
+  else return launch_dep(k_step1d_f64<P, FLUX>, grid, NT, st, a);
 }
 
 template <int FLUX, bool F32>

@@ -434,8 +434,8 @@ __device__ void flcat2_adj(const double *q, int cs, double lam, double adv, doub
 // Per-interface cotangents of the stencil nodes: contrib[(m * NS + s) * S + c],
 // node j = s - NS/2 + 1.
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NWF * 32) k_adj1d(const Step1DArgs a, const double *__restrict__ ubar1,
-                                                    double *__restrict__ contrib) {
+__device__ __forceinline__ void adj1d_body(const Step1DArgs a, const double *__restrict__ ubar1,
+                                           double *__restrict__ contrib) {
   using TL = Tiling<P, NWF>;
   constexpr int S = Phys<FLUX>::S;
   constexpr int NS = 2 * P > 4 ? 2 * P : 4;
@@ -521,12 +521,23 @@ __global__ void __launch_bounds__(NWF * 32) k_adj1d(const Step1DArgs a, const do
   }
 }
 
+// The launched kernel: the programmatic-launch wait, adj1d_body, the
+// release (acat_pdl_wait, acat_pdl_release); the body's early returns
+// still reach the release.
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NWF * 32) k_adj1d(const Step1DArgs a, const double *__restrict__ ubar1,
+                                                    double *__restrict__ contrib) {
+  acat_pdl_wait();
+  adj1d_body<P, FLUX>(a, ubar1, contrib);
+  acat_pdl_release();
+}
+
 // ubar^n_i = ubar^{n+1}_i + the contributions of every (interface, node)
 // whose position maps to cell i through the boundary condition.
 template <int P, int S>
-__global__ void __launch_bounds__(NT) k_adj_gather(const Step1DArgs a, const double *__restrict__ ubar1,
-                                                   const double *__restrict__ contrib,
-                                                   double *__restrict__ ubar0) {
+__device__ __forceinline__ void adj_gather_body(const Step1DArgs a, const double *__restrict__ ubar1,
+                                                const double *__restrict__ contrib,
+                                                double *__restrict__ ubar0) {
   constexpr int NS = 2 * P > 4 ? 2 * P : 4;
   constexpr int GA = P > 2 ? P : 2;
   const long N = a.N;
@@ -561,6 +572,18 @@ __global__ void __launch_bounds__(NT) k_adj_gather(const Step1DArgs a, const dou
   }
 }
 
+// The launched kernel: the programmatic-launch wait, adj_gather_body, the
+// release (acat_pdl_wait, acat_pdl_release); the body's early returns
+// still reach the release.
+template <int P, int S>
+__global__ void __launch_bounds__(NT) k_adj_gather(const Step1DArgs a, const double *__restrict__ ubar1,
+                                                   const double *__restrict__ contrib,
+                                                   double *__restrict__ ubar0) {
+  acat_pdl_wait();
+  adj_gather_body<P, S>(a, ubar1, contrib, ubar0);
+  acat_pdl_release();
+}
+
 // FP32 adjoint step on the compensated state [hi(S x N); lo(S x N)] with a
 // compensated cotangent of the same layout. The order decisions are the FP32
 // forward's (taken on hi + lo); Fbar_m = lambda (ubar_m - ubar_{m-1}) is
@@ -570,8 +593,8 @@ __global__ void __launch_bounds__(NT) k_adj_gather(const Step1DArgs a, const dou
 // differentiated in FP64 on hi + lo. Per-interface node cotangents go to a
 // float scratch array.
 template <int P, int FLUX>
-__global__ void __launch_bounds__(NWF * 32) k_adj1d_f32(const Step1DArgs a, const float *__restrict__ ubar1,
-                                                        float *__restrict__ contrib) {
+__device__ __forceinline__ void adj1d_f32_body(const Step1DArgs a, const float *__restrict__ ubar1,
+                                               float *__restrict__ contrib) {
   using TL = Tiling<P, NWF>;
   constexpr int S = Phys<FLUX>::S;
   constexpr int NS = 2 * P > 4 ? 2 * P : 4;
@@ -669,12 +692,23 @@ __global__ void __launch_bounds__(NWF * 32) k_adj1d_f32(const Step1DArgs a, cons
   }
 }
 
+// The launched kernel: the programmatic-launch wait, adj1d_f32_body, the
+// release (acat_pdl_wait, acat_pdl_release); the body's early returns
+// still reach the release.
+template <int P, int FLUX>
+__global__ void __launch_bounds__(NWF * 32) k_adj1d_f32(const Step1DArgs a, const float *__restrict__ ubar1,
+                                                        float *__restrict__ contrib) {
+  acat_pdl_wait();
+  adj1d_f32_body<P, FLUX>(a, ubar1, contrib);
+  acat_pdl_release();
+}
+
 // Compensated gather: ubar^n = ubar^{n+1} + the float sum of the contributions
 // that map to the cell, added to the pair with TwoSum and renormalised.
 template <int P, int S>
-__global__ void __launch_bounds__(NT) k_adj_gather_f32(const Step1DArgs a, const float *__restrict__ ubar1,
-                                                       const float *__restrict__ contrib,
-                                                       float *__restrict__ ubar0) {
+__device__ __forceinline__ void adj_gather_f32_body(const Step1DArgs a, const float *__restrict__ ubar1,
+                                                    const float *__restrict__ contrib,
+                                                    float *__restrict__ ubar0) {
   constexpr int NS = 2 * P > 4 ? 2 * P : 4;
   constexpr int GA = P > 2 ? P : 2;
   const long N = a.N;
@@ -717,6 +751,18 @@ __global__ void __launch_bounds__(NT) k_adj_gather_f32(const Step1DArgs a, const
   }
 }
 
+// The launched kernel: the programmatic-launch wait, adj_gather_f32_body, the
+// release (acat_pdl_wait, acat_pdl_release); the body's early returns
+// still reach the release.
+template <int P, int S>
+__global__ void __launch_bounds__(NT) k_adj_gather_f32(const Step1DArgs a, const float *__restrict__ ubar1,
+                                                       const float *__restrict__ contrib,
+                                                       float *__restrict__ ubar0) {
+  acat_pdl_wait();
+  adj_gather_f32_body<P, S>(a, ubar1, contrib, ubar0);
+  acat_pdl_release();
+}
+
 template <int FLUX>
 int launch_adj_f32(int P, const Step1DArgs &a, const float *ub1, float *contrib, float *ub0, cudaStream_t st) {
   constexpr int S = Phys<FLUX>::S;
@@ -726,9 +772,9 @@ int launch_adj_f32(int P, const Step1DArgs &a, const float *ub1, float *contrib,
 #define ACAT_ADJ32_CASE(PP)                                                                       \
   case PP: {                                                                                      \
     const unsigned grid = (unsigned)((a.N + Tiling<PP, NWF>::NI) / Tiling<PP, NWF>::NI);          \
-    k_adj1d_f32<PP, FLUX><<<grid, NWF * 32, 0, st>>>(a, ub1, contrib);                            \
-    k_adj_gather_f32<PP, S><<<g2, NT, 0, st>>>(a, ub1, contrib, ub0);                             \
-  } break;
+    if (int e = acat_launch_dep(k_adj1d_f32<PP, FLUX>, grid, NWF * 32, st, a, ub1, contrib)) return e;  \
+    return acat_launch_dep(k_adj_gather_f32<PP, S>, g2, NT, st, a, ub1, (const float *)contrib, ub0); \
+  }
     ACAT_ADJ32_CASE(1)
     ACAT_ADJ32_CASE(2)
     ACAT_ADJ32_CASE(3)
@@ -749,9 +795,9 @@ int launch_adj_f(int P, const Step1DArgs &a, const double *ub1, double *contrib,
 #define ACAT_ADJ_CASE(PP)                                                                         \
   case PP: {                                                                                      \
     const unsigned grid = (unsigned)((a.N + Tiling<PP, NWF>::NI) / Tiling<PP, NWF>::NI);          \
-    k_adj1d<PP, FLUX><<<grid, NWF * 32, 0, st>>>(a, ub1, contrib);                                \
-    k_adj_gather<PP, S><<<g2, NT, 0, st>>>(a, ub1, contrib, ub0);                                 \
-  } break;
+    if (int e = acat_launch_dep(k_adj1d<PP, FLUX>, grid, NWF * 32, st, a, ub1, contrib)) return e;     \
+    return acat_launch_dep(k_adj_gather<PP, S>, g2, NT, st, a, ub1, (const double *)contrib, ub0);   \
+  }
     ACAT_ADJ_CASE(1)
     ACAT_ADJ_CASE(2)
     ACAT_ADJ_CASE(3)

@@ -2,6 +2,7 @@
 // Each translation unit that includes it gets its own copy of the weight
 // tables in constant memory; acat_upload_tables_current_device fills all.
 #pragma once
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -137,6 +138,23 @@ __device__ __forceinline__ int acat_tile_index(int i, int n, unsigned *status) {
 // kernel launched without the attribute both instructions return at once.
 __device__ __forceinline__ void acat_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void acat_pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Host side: launch a kernel of that form with programmatic stream
+// serialization (returns 0 or a cudaError_t value).
+template <typename... Params, typename... Args>
+int acat_launch_dep(void (*kernel)(Params...), unsigned grid, unsigned block, cudaStream_t st, Args &&...args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Node-exchange slots of the FP32 1D recursion. A lane stores its F^(k-2) in
 // a 16-byte slot that the other lanes of its group read back by broadcast. In

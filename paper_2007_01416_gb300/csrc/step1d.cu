@@ -384,49 +384,32 @@ __global__ void __launch_bounds__(NT) k_smax1d(const Step1DArgs a) {
   }
 }
 
-// A step kernel launched with programmatic stream serialization (see
-// acat_pdl_enter): its launch overlaps the end of the previous kernel.
-int launch_dep(void (*kernel)(const Step1DArgs), unsigned grid, unsigned block, cudaStream_t st,
-               const Step1DArgs &a) {
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return (int)cudaLaunchKernelEx(&cfg, kernel, a);
-}
-
 template <int P, int FLUX, bool F32>
 int launch_p(const Step1DArgs &a, cudaStream_t st) {
   using TL = Tiling<P>;
   if constexpr (!F32) {
     if (a.flux_buf && a.cnt)  // small-CTA step with boundary hand-off
-      return launch_dep(k_step1d_fine<P, FLUX>, (unsigned)acat_fine_ctas_1d(P, a.N), NWF * 32, st, a);
+      return acat_launch_dep(k_step1d_fine<P, FLUX>, (unsigned)acat_fine_ctas_1d(P, a.N), NWF * 32, st, a);
   }
   if constexpr (F32) {
     if (a.flux_buf && a.cnt && a.lpn == 1)  // small-CTA step with boundary hand-off
-      return launch_dep(k_step1d_fine_f32<P, FLUX>, (unsigned)acat_fine_ctas_1d(P, a.N), NWF * 32, st, a);
+      return acat_launch_dep(k_step1d_fine_f32<P, FLUX>, (unsigned)acat_fine_ctas_1d(P, a.N), NWF * 32, st, a);
     if constexpr (P == 2 || P == 4) {
       if (a.lpn == 2) {
         using T2 = Tiling<P, NT / 32, 2>;
-        return launch_dep(k_step1d_f32<P, FLUX, 2>, (unsigned)((a.N + T2::T - 1) / T2::T), NT, st, a);
+        return acat_launch_dep(k_step1d_f32<P, FLUX, 2>, (unsigned)((a.N + T2::T - 1) / T2::T), NT, st, a);
       }
     }
     if (a.lpn != 1) return (int)cudaErrorInvalidValue;
     if (a.nw == 7) {
       using T7 = Tiling<P, 7>;
-      return launch_dep(k_step1d_f32<P, FLUX, 1, 7>, (unsigned)((a.N + T7::T - 1) / T7::T), 7 * 32, st, a);
+      return acat_launch_dep(k_step1d_f32<P, FLUX, 1, 7>, (unsigned)((a.N + T7::T - 1) / T7::T), 7 * 32, st, a);
     }
     if (a.nw != 0 && a.nw != NT / 32) return (int)cudaErrorInvalidValue;
   }
   const unsigned grid = (unsigned)((a.N + TL::T - 1) / TL::T);
-  if constexpr (F32) return launch_dep(k_step1d_f32<P, FLUX, 1>, grid, NT, st, a);
-  else return launch_dep(k_step1d_f64<P, FLUX>, grid, NT, st, a);
+  if constexpr (F32) return acat_launch_dep(k_step1d_f32<P, FLUX, 1>, grid, NT, st, a);
+  else return acat_launch_dep(k_step1d_f64<P, FLUX>, grid, NT, st, a);
 }
 
 template <int FLUX, bool F32>

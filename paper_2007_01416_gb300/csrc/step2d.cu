@@ -695,7 +695,7 @@ __device__ double step_dt2(const Step2DArgs &a) {
 __device__ __forceinline__ long bc2(long g, long n, int bc) { return bc_index(g, n, bc); }
 
 template <int P, int FLUX, bool F32>
-__global__ void __launch_bounds__(NT, F32 ? 3 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 1)) k_step2d(const Step2DArgs a) {
+__global__ void __launch_bounds__(NT, F32 ? 3 : (FLUX == ACAT_FLUX_LINEAR ? 3 : 2)) k_step2d(const Step2DArgs a) {
   using PH = Phys2<FLUX>;
   constexpr int S = PH::S;
   using R = typename std::conditional<F32, float, double>::type;

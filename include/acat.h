@@ -163,8 +163,8 @@ int acat_create_batched(const acat_params *p, int n_inst, const int32_t *n_per_i
  *     bit for bit.
  *   - Batched contexts: the batch is cut into tiles of
  *     T = R nw floor(32 / (2P lpn)) - 1 consecutive cells of one instance,
- *     R = 4 interface rounds per lane group in FP32 (2 at nw = 16), 1 in
- *     FP64 (P = 3, nw = 8, lpn = 1: 159 in FP32, 39 in FP64); one CTA of nw
+ *     R = 8 interface rounds per lane group in FP32 (2 at nw = 16), 1 in
+ *     FP64 (P = 3, nw = 8, lpn = 1: 319 in FP32, 39 in FP64); one CTA of nw
  *     warps per tile at a time,
  *     on a grid of (SM count) x cps CTAs that take the tiles from a queue
  *     (cps = 0: the kernel's occupancy). nw in {4, 8, 16}. At a fixed lpn,

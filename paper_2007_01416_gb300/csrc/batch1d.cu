@@ -54,13 +54,13 @@ __global__ void __launch_bounds__(NT) k_batch_dt(const Step1DArgs a, const Batch
   }
 }
 
-// Interface rounds per lane group in a tile of the FP32 batched step: four
+// Interface rounds per lane group in a tile of the FP32 batched step: eight
 // rounds (two at 16 warps, within 48 KB of static shared memory) make tiles
-// of R NW GPW interfaces, so the tile's two CTA barriers and its update phase
-// are shared by R times the flux work.
+// of R NW GPW interfaces, so the tile's CTA barriers, order-decision pass and
+// update phase are shared by R times the flux work.
 template <int NW>
 struct RoundsB32 {
-  static constexpr int value = NW >= 16 ? 2 : 4;
+  static constexpr int value = NW >= 16 ? 2 : 8;
 };
 
 // Persistent batched step: CTAs of NW warps take the tiles of the (instance,

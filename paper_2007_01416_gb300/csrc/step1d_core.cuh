@@ -25,9 +25,11 @@ __device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R 
   constexpr int n = 2 * p;
   const unsigned mask = ((1u << n) - 1u) << base;
   const int j = l - p + 1;
+  // the node's derivative weights scaled by -lambda once, so that each order's
+  // U^(k-1)_j = -lambda sum_r g1[j][r] F_r needs no multiply per component
   R g1r[n];
 #pragma unroll
-  for (int r = 0; r < n; r++) g1r[r] = TB::g1(p, l, r);
+  for (int r = 0; r < n; r++) g1r[r] = TB::g1(p, l, r) * -lam;
   R f0[S], Fsum[S], Fprev[S], arg[n][S];
   {
     R u[S];
@@ -55,10 +57,7 @@ __device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R 
       for (int c = 0; c < S; c++) U[c] = fma(g1r[r], __shfl_sync(mask, Fprev[c], base + r), U[c]);
     R acc[S];
 #pragma unroll
-    for (int c = 0; c < S; c++) {
-      U[c] *= -lam;
-      acc[c] = TB::gk(p, k - 1, p - 1) * f0[c];
-    }
+    for (int c = 0; c < S; c++) acc[c] = TB::gk(p, k - 1, p - 1) * f0[c];
 #pragma unroll
     for (int rr = 0; rr < n; rr++) {
       if (rr == p - 1) continue;  // r = 0: f(u_j) itself
@@ -80,9 +79,9 @@ __device__ __forceinline__ void cat_flux(const R *q, int cs, int l, int base, R 
 #pragma unroll
   for (int c = 0; c < S; c++) {
     const R v = w * Fsum[c];
-    R t = R(0);
+    R t = __shfl_sync(mask, v, base);
 #pragma unroll
-    for (int r = 0; r < n; r++) t += __shfl_sync(mask, v, base + r);
+    for (int r = 1; r < n; r++) t += __shfl_sync(mask, v, base + r);
     Fout[c] = t;
   }
 }

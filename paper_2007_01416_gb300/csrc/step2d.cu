@@ -240,11 +240,14 @@ __device__ __forceinline__ void cat2d_f64(const double *q, int cs, int rs, int l
   constexpr int n = 2 * p;
   const unsigned mask = ((1u << (n * n)) - 1u) << base;
   const int a1 = l % n, b1 = l / n;
+  // the node's row and column weights scaled by -lambda_x and -lambda_y once:
+  // each order's U = -lambda_x sum_r gx_r F_r - lambda_y sum_r gy_r G_r is then
+  // one accumulation over both directions
   double gx[n], gy[n];
 #pragma unroll
   for (int r = 0; r < n; r++) {
-    gx[r] = TB::g1(p, a1, r);
-    gy[r] = TB::g1(p, b1, r);
+    gx[r] = TB::g1(p, a1, r) * -lx;
+    gy[r] = TB::g1(p, b1, r) * -ly;
   }
   double f0[S], g0[S], Ff[S], Fg[S], Pf[S], Pg[S], arg[n][S];
   {
@@ -264,20 +267,19 @@ __device__ __forceinline__ void cat2d_f64(const double *q, int cs, int rs, int l
   }
 #pragma unroll
   for (int k = 2; k <= n; k++) {
-    double Ux[S], Uy[S];
+    double U[S], af[S], ag[S];
 #pragma unroll
-    for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0;
+    for (int c = 0; c < S; c++) U[c] = 0.0;
 #pragma unroll
     for (int r = 0; r < n; r++)
 #pragma unroll
-      for (int c = 0; c < S; c++) {
-        Ux[c] = fma(gx[r], __shfl_sync(mask, Pf[c], base + b1 * n + r), Ux[c]);
-        Uy[c] = fma(gy[r], __shfl_sync(mask, Pg[c], base + r * n + a1), Uy[c]);
-      }
-    double U[S], af[S], ag[S];
+      for (int c = 0; c < S; c++) U[c] = fma(gx[r], __shfl_sync(mask, Pf[c], base + b1 * n + r), U[c]);
+#pragma unroll
+    for (int r = 0; r < n; r++)
+#pragma unroll
+      for (int c = 0; c < S; c++) U[c] = fma(gy[r], __shfl_sync(mask, Pg[c], base + r * n + a1), U[c]);
 #pragma unroll
     for (int c = 0; c < S; c++) {
-      U[c] = -(lx * Ux[c]) - ly * Uy[c];
       af[c] = TB::gk(p, k - 1, p - 1) * f0[c];
       ag[c] = TB::gk(p, k - 1, p - 1) * g0[c];
     }
@@ -1027,11 +1029,13 @@ __device__ __forceinline__ void block_tasks(Smem2H<P, FLUX> &sm, const Step2DArg
   const int nt = sm.ntask[p];
   const int tid = threadIdx.x, ti = tid / nn, node = tid - ti * nn;
   const int ia = node % n, ib = node / n;
+  // row and column weights scaled by -lambda_x, -lambda_y once (one
+  // accumulation of U over both directions per order)
   double gx[n], gy[n];
 #pragma unroll
   for (int r = 0; r < n; r++) {
-    gx[r] = TB::g1(p, ia, r);
-    gy[r] = TB::g1(p, ib, r);
+    gx[r] = TB::g1(p, ia, r) * -lx;
+    gy[r] = TB::g1(p, ib, r) * -ly;
   }
   for (int base = 0; base < nt; base += per) {
     const bool act = ti < per && base + ti < nt;
@@ -1065,18 +1069,16 @@ __device__ __forceinline__ void block_tasks(Smem2H<P, FLUX> &sm, const Step2DArg
       __syncthreads();
       double U[S];
       if (act) {
-        double Ux[S], Uy[S];
 #pragma unroll
-        for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0;
+        for (int c = 0; c < S; c++) U[c] = 0.0;
 #pragma unroll
         for (int r = 0; r < n; r++)
 #pragma unroll
-          for (int c = 0; c < S; c++) {
-            Ux[c] = fma(gx[r], sm.X[ti * nn + ib * n + r][c], Ux[c]);
-            Uy[c] = fma(gy[r], sm.Y[ti * nn + r * n + ia][c], Uy[c]);
-          }
+          for (int c = 0; c < S; c++) U[c] = fma(gx[r], sm.X[ti * nn + ib * n + r][c], U[c]);
 #pragma unroll
-        for (int c = 0; c < S; c++) U[c] = -(lx * Ux[c]) - ly * Uy[c];
+        for (int r = 0; r < n; r++)
+#pragma unroll
+          for (int c = 0; c < S; c++) U[c] = fma(gy[r], sm.Y[ti * nn + r * n + ia][c], U[c]);
       }
       __syncthreads();
       if (act) {

@@ -311,9 +311,11 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
   constexpr int n = 2 * p;
   const unsigned mask = ((1u << n) - 1u) << base;
   const int j = l - p + 1;
+  // the node's derivative weights scaled by -lambda once (no multiply per
+  // component and order)
   float g1r[n];
 #pragma unroll
-  for (int r = 0; r < n; r++) g1r[r] = TB::g1(p, l, r);
+  for (int r = 0; r < n; r++) g1r[r] = __fmul_rn(TB::g1(p, l, r), -lam);
   float ui[S], uil[S], uj[S], ujl[S], dh[S], dl[S];
 #pragma unroll
   for (int c = 0; c < S; c++) {
@@ -365,10 +367,8 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
         u01 = f2fma(f2dup(g1r[r]), make_float2(f.x, f.y), u01);
         U[S > 2 ? 2 : 0] = fmaf(g1r[r], f.z, U[S > 2 ? 2 : 0]);
       }
-      u01 = f2mul(u01, f2dup(-lam));
       U[0] = u01.x;
       U[1] = u01.y;
-      U[S > 2 ? 2 : 0] *= -lam;
     } else if constexpr (S > 1) {
       float4 *xb = xg + (k & 1) * XSET;
       xb[l] = make_float4(Fprev[0], Fprev[1], Fprev[S > 2 ? 2 : 0], 0.0f);
@@ -380,12 +380,9 @@ __device__ __forceinline__ void cat_delta(const float *hi, const float *lo, int 
 #pragma unroll
         for (int c = 0; c < S; c++) U[c] = fmaf(g1r[r], fr[c], U[c]);
       }
-#pragma unroll
-      for (int c = 0; c < S; c++) U[c] *= -lam;
     } else {  // a scalar law: one shuffle per node
 #pragma unroll
       for (int r = 0; r < n; r++) U[0] = fmaf(g1r[r], __shfl_sync(mask, Fprev[0], base + r), U[0]);
-      U[0] *= -lam;
     }
     float acc[S];
     float2 acc2[S];

@@ -1522,9 +1522,9 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
     float wx[HW ? NM : 1], wy[HW ? NM : 1];
     if constexpr (HW) {
 #pragma unroll
-      for (int r = 0; r < NM; r++) {
-        wx[r] = act && r < n1 ? TB.g1[p1][ia][r] : 0.0f;
-        wy[r] = act && r < n2 ? TB.g1[p2][ib][r] : 0.0f;
+      for (int r = 0; r < NM; r++) {  // scaled by -lambda_x, -lambda_y once
+        wx[r] = act && r < n1 ? __fmul_rn(TB.g1[p1][ia][r], -lx) : 0.0f;
+        wy[r] = act && r < n2 ? __fmul_rn(TB.g1[p2][ib][r], -ly) : 0.0f;
       }
     }
 #pragma unroll 1
@@ -1533,28 +1533,40 @@ __device__ __forceinline__ void block_tasks_f32(Smem2HF<P, FLUX> &sm, const Step
       const bool go = act && k <= n;
       float U[S];
       if (go) {
-        float Ux[S], Uy[S];
+        if constexpr (HW) {  // the scaled weights: one accumulation over row and column
 #pragma unroll
-        for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0f;
+          for (int c = 0; c < S; c++) U[c] = 0.0f;
 #pragma unroll
-        for (int r = 0; r < NM; r++) {
-          if (r < n1) {
-            float w;
-            if constexpr (HW) w = wx[r];
-            else w = TB.g1[p1][ia][r];
+          for (int r = 0; r < NM; r++) {
+            if (r < n1) {
 #pragma unroll
-            for (int c = 0; c < S; c++) Ux[c] = fmaf(w, sm.X[xrow + r][c], Ux[c]);
+              for (int c = 0; c < S; c++) U[c] = fmaf(wx[r], sm.X[xrow + r][c], U[c]);
+            }
+            if (r < n2) {
+#pragma unroll
+              for (int c = 0; c < S; c++) U[c] = fmaf(wy[r], sm.Y[ycol + r * SM::YS][c], U[c]);
+            }
           }
-          if (r < n2) {
-            float w;
-            if constexpr (HW) w = wy[r];
-            else w = TB.g1[p2][ib][r];
+        } else {
+          float Ux[S], Uy[S];
 #pragma unroll
-            for (int c = 0; c < S; c++) Uy[c] = fmaf(w, sm.Y[ycol + r * SM::YS][c], Uy[c]);
+          for (int c = 0; c < S; c++) Ux[c] = Uy[c] = 0.0f;
+#pragma unroll
+          for (int r = 0; r < NM; r++) {
+            if (r < n1) {
+              const float w = TB.g1[p1][ia][r];
+#pragma unroll
+              for (int c = 0; c < S; c++) Ux[c] = fmaf(w, sm.X[xrow + r][c], Ux[c]);
+            }
+            if (r < n2) {
+              const float w = TB.g1[p2][ib][r];
+#pragma unroll
+              for (int c = 0; c < S; c++) Uy[c] = fmaf(w, sm.Y[ycol + r * SM::YS][c], Uy[c]);
+            }
           }
+#pragma unroll
+          for (int c = 0; c < S; c++) U[c] = -(lx * Ux[c]) - ly * Uy[c];
         }
-#pragma unroll
-        for (int c = 0; c < S; c++) U[c] = -(lx * Ux[c]) - ly * Uy[c];
       }
       __syncthreads();
       if (go) {

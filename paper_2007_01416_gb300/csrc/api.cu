@@ -392,9 +392,9 @@ int acat_create(const acat_params *p, acat_ctx **out) {
   const long fused_ctas = (p->nx + acat_cells_per_cta_1d(p->P, ACAT_PREC_F64) - 1) /
                           acat_cells_per_cta_1d(p->P, ACAT_PREC_F64);
   // 1D FP32: the small-CTA step is available to every context through
-  // acat_set_launch_shape and the autotuner; the fused 8-warp step stays the
-  // default (at FP32 step times the hand-off's fences and the small CTAs' serial
-  // update phases cost more than their even load saves)
+  // acat_set_launch_shape and the autotuner; the fused step (8 or 7 warps, set
+  // below) stays the default (at FP32 step times the hand-off's fences and the
+  // small CTAs' serial update phases cost more than their even load saves)
   const bool f64_fine = p->precision == ACAT_PREC_F64 && 4 * fused_ctas > 3 * 2 * (long)sms;
   const bool f32_fine = p->precision == ACAT_PREC_F32;
   if (e == cudaSuccess && c->dim == 1 && (f64_fine || f32_fine)) {

@@ -1,9 +1,9 @@
 // batch1d.cu -- the batched 1D step: independent instances of ragged sizes,
 // concatenated along the cell index, advanced in one persistent launch per
-// step. CTAs stride over an (instance, tile) work list; each tile is the
-// tile of the single-instance step (step1d_core.cuh) with the instance's own
-// dt, and per-instance wave speeds are reduced into per-instance slots for
-// the next step's dt.
+// step. CTAs take the tiles of an (instance, tile) work list from a queue;
+// each tile is the tile of the single-instance step (step1d_core.cuh) with
+// the instance's own dt, and per-instance wave speeds are reduced into
+// per-instance slots for the next step's dt.
 #include "step1d_core.cuh"
 
 namespace {

@@ -162,6 +162,46 @@ def test_run_equals_repeated_steps(env, nx):
         assert torch.equal(u, v)
 
 
+@pytest.mark.parametrize("prec,nx", [(0, 3000), (0, 20001), (1, 3000), (1, 16384)])
+def test_steps_ordered_with_stream_kernels(env, prec, nx):
+    """The 1D step kernels are launched with programmatic stream serialization:
+    each waits for the previous kernel of the stream before any memory access.
+    Steps and runs interleaved with PyTorch kernels that write their input and
+    read and overwrite their output, with no synchronisation in between, give
+    the bits of the same sequence synchronised after every operation (FP64
+    fused and small-CTA grids; FP32 8- and 7-warp tiles)."""
+    torch, O, acat = env
+    c = W.euler1d_riemann_entropy(nx=nx, seed=11, P=4)
+    u0 = torch.from_numpy(acat.to_pair(c.u0) if prec else c.u0.copy()).cuda()
+
+    def sequence(sync):
+        outs = []
+        with acat.Context(**c.problem_kwargs(), precision=prec) as ctx:
+            u, w = torch.empty_like(u0), torch.empty_like(u0)
+            for k in range(12):
+                u.copy_(u0)
+                u.mul_(1.0 + 1e-3 * k)  # the step's input, written by stream kernels
+                if sync:
+                    torch.cuda.synchronize()
+                if k % 3 == 2:
+                    ctx.acat_run(u, 5)  # graph replay, in place
+                    res = u
+                else:
+                    ctx.acat_step(u, w)
+                    res = w
+                if sync:
+                    torch.cuda.synchronize()
+                outs.append(res.clone())  # read by a stream kernel
+                res.fill_(float("nan"))  # and overwritten before the next step
+            torch.cuda.synchronize()
+            assert ctx.acat_status() == 0
+        return outs
+
+    fast, slow = sequence(False), sequence(True)
+    for x, y in zip(fast, slow):
+        assert torch.equal(x, y)
+
+
 @pytest.mark.parametrize("nx,t_end", [(1024, 0.01), (30001, 0.002)])
 def test_t_end_clipping(env, nx, t_end):
     torch, O, acat = env
